@@ -1,0 +1,260 @@
+"""CPU oracle (plain FP64) for the subdomain-wise ILU0 BiCGSTAB hot path.
+
+TEST INFRASTRUCTURE ONLY.  The test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only users.  The CUDA library never
+imports, links or calls anything here, and the two share no code; both take
+their inputs from :mod:`synth`.
+
+The arithmetic lives in ``oracle.c`` (plain loops, one function per step of
+the paper, each citing its passage).  This module compiles it with the system
+C compiler on first use and wraps it with numpy arrays.
+
+Paper map:
+  partition            Algorithm 2 (geometric cuts)
+  permutation/reorder  Section 3.1, Algorithm 3
+  drop                 Section 3.2
+  ilu0                 Algorithm 7 (ILU0 part), block form
+  levels_lower/upper   Algorithm 5 (level sets of the subdomain DAGs)
+  apply                Section 4.2.2 / 4.4 result: z = U^-1 L^-1 r
+  spmv, dot            the products inside Algorithm 1
+  bicgstab             Algorithm 1 (right-preconditioned reading)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ZERO_PIVOT, BREAKDOWN, NOT_CONVERGED = 0, 2, 5, 6
+DOT_TILE = 256
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` (O2, no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("restarts", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("rel_res_recurrence", ctypes.c_double), ("rel_res_true", ctypes.c_double)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+            f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+            vp = ctypes.c_void_p
+            I, L, D = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+            lib.oracle_partition.argtypes = [ctypes.c_int] * 6 + [i32p]
+            lib.oracle_partition.restype = None
+            lib.oracle_permutation.argtypes = [I, I, i32p, i32p, i32p, i32p]
+            lib.oracle_permutation.restype = None
+            lib.oracle_reorder.argtypes = [I, i32p, i32p, vp, i32p, i32p, i32p, i32p, vp]
+            lib.oracle_reorder.restype = None
+            lib.oracle_drop.argtypes = [I, i32p, i32p, vp, i32p, vp, vp, vp]
+            lib.oracle_drop.restype = L
+            lib.oracle_ilu0.argtypes = [I, i32p, i32p, f64p, f64p]
+            lib.oracle_ilu0.restype = ctypes.c_int
+            lib.oracle_levels_lower.argtypes = [I, i32p, i32p, i32p]
+            lib.oracle_levels_lower.restype = I
+            lib.oracle_levels_upper.argtypes = [I, i32p, i32p, i32p]
+            lib.oracle_levels_upper.restype = I
+            lib.oracle_apply.argtypes = [I, i32p, i32p, f64p, f64p, f64p]
+            lib.oracle_apply.restype = ctypes.c_int
+            lib.oracle_spmv.argtypes = [I, i32p, i32p, f64p, f64p, f64p]
+            lib.oracle_spmv.restype = None
+            lib.oracle_dot.argtypes = [I, f64p, f64p]
+            lib.oracle_dot.restype = D
+            lib.oracle_bicgstab.argtypes = [I, i32p, i32p, f64p, i32p, i32p, f64p, f64p, f64p, I, D,
+                                            ctypes.POINTER(_Info), vp]
+            lib.oracle_bicgstab.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+
+
+@dataclass
+class BSR:
+    """Block sparse rows; ``val`` has shape (nnzb, 3, 3) or is None (pattern only)."""
+
+    row_ptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray | None
+
+    @property
+    def n(self) -> int:
+        return len(self.row_ptr) - 1
+
+    @property
+    def nnzb(self) -> int:
+        return int(self.row_ptr[-1])
+
+
+def partition(grid, sub) -> np.ndarray:
+    """Algorithm 2 (ceil-division for ragged grids)."""
+    nx, ny, nz = grid
+    part = np.empty(nx * ny * nz, np.int32)
+    _load().oracle_partition(nx, ny, nz, *sub, part)
+    return part
+
+
+def nparts(grid, sub) -> int:
+    return int(np.prod([-(-g // s) for g, s in zip(grid, sub)]))
+
+
+def permutation(part_id: np.ndarray, nparts_: int):
+    """Section 3.1: returns perm (new -> old), iperm (old -> new), part_ptr."""
+    n = len(part_id)
+    perm = np.empty(n, np.int32)
+    iperm = np.empty(n, np.int32)
+    pp = np.empty(nparts_ + 1, np.int32)
+    _load().oracle_permutation(n, nparts_, np.ascontiguousarray(part_id, np.int32), perm, iperm, pp)
+    return perm, iperm, pp
+
+
+def reorder(A: BSR, perm, iperm) -> BSR:
+    """Algorithm 3 on BSR."""
+    n = A.n
+    rp = np.empty(n + 1, np.int32)
+    col = np.empty(A.nnzb, np.int32)
+    val = None if A.val is None else np.empty((A.nnzb, 3, 3), np.float64)
+    src = None if A.val is None else np.ascontiguousarray(A.val, np.float64)
+    _load().oracle_reorder(n, A.row_ptr, A.col, _ptr(src), perm, iperm, rp, col, _ptr(val))
+    return BSR(rp, col, val)
+
+
+def drop(A: BSR, label: np.ndarray) -> BSR:
+    """Section 3.2: keep blocks whose row and column carry the same label."""
+    lib = _load()
+    label = np.ascontiguousarray(label, np.int32)
+    kept = lib.oracle_drop(A.n, A.row_ptr, A.col, None, label, None, None, None)
+    rp = np.empty(A.n + 1, np.int32)
+    col = np.empty(kept, np.int32)
+    val = None if A.val is None else np.empty((kept, 3, 3), np.float64)
+    src = None if A.val is None else np.ascontiguousarray(A.val, np.float64)
+    lib.oracle_drop(A.n, A.row_ptr, A.col, _ptr(src), label, _ptr(rp), _ptr(col), _ptr(val))
+    return BSR(rp, col, val)
+
+
+def ilu0(Add: BSR):
+    """Algorithm 7 (block ILU0).  Returns (lu values, status)."""
+    lu = np.empty((Add.nnzb, 3, 3), np.float64)
+    st = _load().oracle_ilu0(Add.n, Add.row_ptr, Add.col, _f64(Add.val), lu.reshape(-1))
+    return lu, int(st)
+
+
+def levels_lower(M: BSR):
+    lev = np.empty(M.n, np.int32)
+    nl = _load().oracle_levels_lower(M.n, M.row_ptr, M.col, lev)
+    return lev, int(nl)
+
+
+def levels_upper(M: BSR):
+    lev = np.empty(M.n, np.int32)
+    nl = _load().oracle_levels_upper(M.n, M.row_ptr, M.col, lev)
+    return lev, int(nl)
+
+
+def apply(LU: BSR, r: np.ndarray) -> np.ndarray:
+    """z = U^-1 L^-1 r (sequential substitution, ILU0 form)."""
+    z = np.empty(3 * LU.n, np.float64)
+    st = _load().oracle_apply(LU.n, LU.row_ptr, LU.col, _f64(LU.val), _f64(r), z)
+    if st:
+        raise ArithmeticError(f"singular pivot block at row {-st - 1}")
+    return z
+
+
+def spmv(A: BSR, x: np.ndarray) -> np.ndarray:
+    y = np.empty(3 * A.n, np.float64)
+    _load().oracle_spmv(A.n, A.row_ptr, A.col, _f64(A.val), _f64(x), y)
+    return y
+
+
+def dot(x: np.ndarray, y: np.ndarray) -> float:
+    """Dot product in the project's fixed order (block rows, 256-row tiles, halving sums)."""
+    x = _f64(x)
+    y = _f64(y)
+    assert len(x) == len(y) and len(x) % 3 == 0
+    return float(_load().oracle_dot(len(x) // 3, x, y))
+
+
+@dataclass
+class SolveResult:
+    x: np.ndarray
+    status: int
+    iterations: int
+    restarts: int
+    rel_res_recurrence: float
+    rel_res_true: float
+    history: np.ndarray
+
+
+def bicgstab(A: BSR, LU: BSR, b: np.ndarray, maxit: int = 10000, rtol: float = 1e-8) -> SolveResult:
+    """Algorithm 1 with M = LU; vectors in the reordered numbering."""
+    x = np.empty(3 * A.n, np.float64)
+    hist = np.zeros(maxit + 1, np.float64)
+    info = _Info()
+    _load().oracle_bicgstab(A.n, A.row_ptr, A.col, _f64(A.val), LU.row_ptr, LU.col, _f64(LU.val),
+                            _f64(b), x, maxit, rtol, ctypes.byref(info), _ptr(hist))
+    it = info.iterations
+    return SolveResult(x, info.status, it, info.restarts, info.rel_res_recurrence,
+                       info.rel_res_true, hist[: it + 1].copy())
+
+
+@dataclass
+class Decomposition:
+    """Everything the method derives from A before the solve (Sections 3 and 4.3)."""
+
+    grid: tuple
+    sub: tuple
+    part_id: np.ndarray
+    perm: np.ndarray
+    iperm: np.ndarray
+    part_ptr: np.ndarray
+    Ap: BSR          # reordered full matrix (SpMV operand)
+    Add: BSR         # reordered matrix without inter-subdomain blocks
+    LU: BSR          # ILU0 factors of Add, same pattern
+    status: int
+
+
+def decompose(row_ptr, col, val, grid, sub, factor: bool = True) -> Decomposition:
+    """Partition (Alg. 2), reorder (Alg. 3), drop (Section 3.2), ILU0 (Alg. 7)."""
+    part = partition(grid, sub)
+    np_ = nparts(grid, sub)
+    perm, iperm, pp = permutation(part, np_)
+    A = BSR(np.ascontiguousarray(row_ptr, np.int32), np.ascontiguousarray(col, np.int32),
+            None if val is None else np.ascontiguousarray(val, np.float64).reshape(-1, 3, 3))
+    Ap = reorder(A, perm, iperm)
+    label = part[perm]
+    Add = drop(Ap, label)
+    LU, st = BSR(Add.row_ptr, Add.col, None), 0
+    if factor and Add.val is not None:
+        lu, st = ilu0(Add)
+        LU = BSR(Add.row_ptr, Add.col, lu)
+    return Decomposition(tuple(grid), tuple(sub), part, perm, iperm, pp, Ap, Add, LU, st)

@@ -1,0 +1,444 @@
+/*
+ * CPU oracle for subdomain-wise ILU0-preconditioned BiCGSTAB on 3x3 BSR
+ * matrices (arXiv 2508.04917). TEST INFRASTRUCTURE ONLY: the test suite, the
+ * smoke check and the benchmark's CPU-baseline leg are its only callers. The
+ * CUDA library never links, loads or calls it, and it shares no code with it.
+ *
+ * Plain FP64 loops, written for reading, not for speed. Every function says
+ * which part of the paper it follows. Indices are int32 (rows, columns) and
+ * int64 (block positions). Blocks are 3x3 row-major, nine doubles each.
+ *
+ * Readings of passages the paper leaves open (the same list is kept with the
+ * design notes of the project):
+ *  - Algorithm 2 with ceil-division: edge subdomains may be smaller.
+ *  - Algorithm 3 permutation semantics: perm[new] = old, iperm[old] = new.
+ *    Rows of one subdomain keep ascending natural order (stable grouping).
+ *  - Section 3.2 drop: keep block (i, j) iff rows i and j carry the same label.
+ *  - Algorithm 7, block form: L unit block-lower with L_ij = W_ij * U_jj^-1,
+ *    U keeps full 3x3 diagonal blocks; the update loop runs over k > j.
+ *  - 3x3 solves: Gaussian elimination with partial pivoting.
+ *  - Algorithm 1 with K1 = I, K2 = M = LU (right preconditioning), x0 = 0,
+ *    stop when ||r||_2 / ||b||_2 < rtol (checked on r_{j+1} only), then one
+ *    restart from the true residual if the true residual misses rtol.
+ *  - Dot products follow one fixed order (oracle_dot) that the GPU library
+ *    implements independently; vector updates use the fused multiply-adds
+ *    written below.
+ *
+ * Parity pins for every function are in the CPU test suite. Nothing in this
+ * file is "parity unpinned".
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Decomposition: Algorithm 2, Algorithm 3, Section 3.2                      */
+/* ------------------------------------------------------------------------ */
+
+static int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+/* Algorithm 2: label of every cell from the grid and subdomain dimensions. */
+void oracle_partition(int nx, int ny, int nz, int sx, int sy, int sz, int32_t* part_id) {
+  int bx = ceil_div(nx, sx), by = ceil_div(ny, sy);
+  for (int i = 0; i < nx; ++i)
+    for (int j = 0; j < ny; ++j)
+      for (int k = 0; k < nz; ++k) {
+        int64_t gidx = (int64_t)i + (int64_t)nx * (j + (int64_t)ny * k);
+        part_id[gidx] = (i / sx) + bx * ((j / sy) + by * (k / sz));
+      }
+}
+
+/*
+ * Section 3.1: rows grouped by label, in label order; inside a label the
+ * original order is kept. perm[new] = old, iperm[old] = new, and
+ * part_ptr[p] .. part_ptr[p+1] is the new row range of label p.
+ */
+void oracle_permutation(int32_t n, int32_t nparts, const int32_t* part_id, int32_t* perm,
+                        int32_t* iperm, int32_t* part_ptr) {
+  for (int32_t p = 0; p <= nparts; ++p) part_ptr[p] = 0;
+  for (int32_t r = 0; r < n; ++r) part_ptr[part_id[r] + 1] += 1;
+  for (int32_t p = 0; p < nparts; ++p) part_ptr[p + 1] += part_ptr[p];
+  int32_t* next = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nparts > 0 ? nparts : 1));
+  for (int32_t p = 0; p < nparts; ++p) next[p] = part_ptr[p];
+  for (int32_t r = 0; r < n; ++r) {
+    int32_t newr = next[part_id[r]]++;
+    perm[newr] = r;
+    iperm[r] = newr;
+  }
+  free(next);
+}
+
+/*
+ * Algorithm 3 on BSR: new row i is old row perm[i]; its blocks move with
+ * their columns renamed by iperm and are then sorted by new column.
+ * val may be NULL (pattern only).
+ */
+void oracle_reorder(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* val,
+                    const int32_t* perm, const int32_t* iperm, int32_t* out_row_ptr,
+                    int32_t* out_col, double* out_val) {
+  out_row_ptr[0] = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t k = perm[i];
+    out_row_ptr[i + 1] = row_ptr[k + 1] - row_ptr[k];
+  }
+  for (int32_t i = 0; i < n; ++i) out_row_ptr[i + 1] += out_row_ptr[i];
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t m = perm[i];
+    int64_t dst = out_row_ptr[i];
+    for (int64_t q = row_ptr[m]; q < row_ptr[m + 1]; ++q, ++dst) {
+      out_col[dst] = iperm[col[q]];
+      if (val) memcpy(out_val + 9 * dst, val + 9 * q, 9 * sizeof(double));
+    }
+    /* sort the row by new column (insertion sort; rows are short) */
+    int64_t lo = out_row_ptr[i], hi = out_row_ptr[i + 1];
+    for (int64_t a = lo + 1; a < hi; ++a) {
+      int32_t c = out_col[a];
+      double blk[9];
+      if (val) memcpy(blk, out_val + 9 * a, sizeof blk);
+      int64_t b = a - 1;
+      while (b >= lo && out_col[b] > c) {
+        out_col[b + 1] = out_col[b];
+        if (val) memcpy(out_val + 9 * (b + 1), out_val + 9 * b, sizeof blk);
+        --b;
+      }
+      out_col[b + 1] = c;
+      if (val) memcpy(out_val + 9 * (b + 1), blk, sizeof blk);
+    }
+  }
+}
+
+/*
+ * Section 3.2: keep only blocks whose row and column lie in the same
+ * subdomain. label[i] is the subdomain of (new) row i. With out_col == NULL
+ * only the number of kept blocks is returned.
+ */
+int64_t oracle_drop(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* val,
+                    const int32_t* label, int32_t* out_row_ptr, int32_t* out_col, double* out_val) {
+  int64_t kept = 0;
+  if (out_row_ptr) out_row_ptr[0] = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+      if (label[col[q]] != label[i]) continue;
+      if (out_col) {
+        out_col[kept] = col[q];
+        if (val && out_val) memcpy(out_val + 9 * kept, val + 9 * q, 9 * sizeof(double));
+      }
+      ++kept;
+    }
+    if (out_row_ptr) out_row_ptr[i + 1] = (int32_t)kept;
+  }
+  return kept;
+}
+
+/* ------------------------------------------------------------------------ */
+/* 3x3 dense helpers                                                         */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Solve M y = f for a 3x3 row-major M by Gaussian elimination with partial
+ * pivoting. Returns 0, or -1 for a zero or non-finite pivot.
+ */
+static int solve3(const double* M, const double* f, double* y) {
+  double a[3][4];
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) a[r][c] = M[3 * r + c];
+    a[r][3] = f[r];
+  }
+  for (int c = 0; c < 3; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < 3; ++r)
+      if (fabs(a[r][c]) > fabs(a[piv][c])) piv = r;
+    if (!(fabs(a[piv][c]) > 0.0) || !isfinite(a[piv][c])) return -1;
+    if (piv != c)
+      for (int q = 0; q < 4; ++q) {
+        double t = a[c][q];
+        a[c][q] = a[piv][q];
+        a[piv][q] = t;
+      }
+    for (int r = c + 1; r < 3; ++r) {
+      double m = a[r][c] / a[c][c];
+      for (int q = c; q < 4; ++q) a[r][q] = a[r][q] - m * a[c][q];
+    }
+  }
+  for (int r = 2; r >= 0; --r) {
+    double s = a[r][3];
+    for (int q = r + 1; q < 3; ++q) s = s - a[r][q] * y[q];
+    y[r] = s / a[r][r];
+  }
+  return 0;
+}
+
+/* X = W * U^-1, i.e. solve X U = W row by row: U^T x_r = w_r. */
+static int right_divide3(const double* W, const double* U, double* X) {
+  double Ut[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) Ut[3 * r + c] = U[3 * c + r];
+  for (int r = 0; r < 3; ++r)
+    if (solve3(Ut, W + 3 * r, X + 3 * r)) return -1;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 7 (ILU0, block form) and the level sets of Algorithm 5         */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Block ILU0 in IKJ order (Algorithm 7, upper half) on the dropped matrix.
+ * lu receives L (strictly lower blocks; unit block diagonal implied) and U
+ * (diagonal and upper blocks) in the pattern of the input. Returns 0, or
+ * -(row+1) for a singular pivot block.
+ */
+int oracle_ilu0(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* val, double* lu) {
+  int64_t nnzb = row_ptr[n];
+  memcpy(lu, val, (size_t)nnzb * 9 * sizeof(double));
+  int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  int64_t* diag = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int32_t c = 0; c < n; ++c) pos[c] = -1;
+  int status = 0;
+  for (int32_t i = 0; i < n && status == 0; ++i) {
+    diag[i] = -1;
+    for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+      pos[col[q]] = q;
+      if (col[q] == i) diag[i] = q;
+    }
+    if (diag[i] < 0) { status = -(i + 1); break; }
+    for (int64_t q = row_ptr[i]; q < row_ptr[i + 1] && col[q] < i; ++q) {
+      int32_t j = col[q];
+      double Lij[9];
+      if (right_divide3(lu + 9 * q, lu + 9 * diag[j], Lij)) { status = -(j + 1); break; }
+      memcpy(lu + 9 * q, Lij, sizeof Lij);
+      /* W_ik -= L_ij U_jk for every k > j present in both rows i and j */
+      for (int64_t t = row_ptr[j]; t < row_ptr[j + 1]; ++t) {
+        int32_t k = col[t];
+        if (k <= j || pos[k] < 0) continue;
+        double* W = lu + 9 * pos[k];
+        const double* Ujk = lu + 9 * t;
+        for (int a = 0; a < 3; ++a)
+          for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int b = 0; b < 3; ++b) s = s + Lij[3 * a + b] * Ujk[3 * b + c];
+            W[3 * a + c] = W[3 * a + c] - s;
+          }
+      }
+    }
+    for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) pos[col[q]] = -1;
+    if (status == 0) {
+      /* the pivot block of row i must be invertible for later rows */
+      double probe[9], eye[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+      if (right_divide3(eye, lu + 9 * diag[i], probe)) status = -(i + 1);
+    }
+  }
+  free(pos);
+  free(diag);
+  return status;
+}
+
+/*
+ * Level of every row in the lower-triangular DAG: 0 without a strictly-lower
+ * block, else one more than the deepest strictly-lower neighbour (the fixed
+ * point that Algorithm 5 reaches). Returns the number of levels.
+ */
+int32_t oracle_levels_lower(int32_t n, const int32_t* row_ptr, const int32_t* col, int32_t* lev) {
+  int32_t nlev = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t l = 0;
+    for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q)
+      if (col[q] < i && lev[col[q]] + 1 > l) l = lev[col[q]] + 1;
+    lev[i] = l;
+    if (l + 1 > nlev) nlev = l + 1;
+  }
+  return nlev;
+}
+
+/* Same on the upper-triangular DAG, solved from the last row backwards. */
+int32_t oracle_levels_upper(int32_t n, const int32_t* row_ptr, const int32_t* col, int32_t* lev) {
+  int32_t nlev = 0;
+  for (int32_t i = n - 1; i >= 0; --i) {
+    int32_t l = 0;
+    for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q)
+      if (col[q] > i && lev[col[q]] + 1 > l) l = lev[col[q]] + 1;
+    lev[i] = l;
+    if (l + 1 > nlev) nlev = l + 1;
+  }
+  return nlev;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Preconditioner apply, SpMV, dot                                           */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * z = U^-1 L^-1 r by plain sequential substitution over all rows (Section
+ * 4.2.2 computes the same result level by level). L has a unit block
+ * diagonal; each U diagonal block is applied through a 3x3 solve. Within a
+ * row, blocks are taken in ascending column order and, per output entry,
+ * block entries c = 0..2 with a fused multiply-add.
+ */
+int oracle_apply(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* lu,
+                 const double* r, double* z) {
+  double* y = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+  for (int32_t i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a) {
+      double acc = r[3 * (int64_t)i + a];
+      for (int64_t q = row_ptr[i]; q < row_ptr[i + 1] && col[q] < i; ++q)
+        for (int c = 0; c < 3; ++c) acc = fma(-lu[9 * q + 3 * a + c], y[3 * (int64_t)col[q] + c], acc);
+      y[3 * (int64_t)i + a] = acc;
+    }
+  int status = 0;
+  for (int32_t i = n - 1; i >= 0; --i) {
+    double w[3];
+    int64_t d = -1;
+    for (int a = 0; a < 3; ++a) {
+      double acc = y[3 * (int64_t)i + a];
+      for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+        if (col[q] == i) d = q;
+        if (col[q] <= i) continue;
+        for (int c = 0; c < 3; ++c) acc = fma(-lu[9 * q + 3 * a + c], z[3 * (int64_t)col[q] + c], acc);
+      }
+      w[a] = acc;
+    }
+    if (d < 0 || solve3(lu + 9 * d, w, z + 3 * (int64_t)i)) status = -(i + 1);
+  }
+  free(y);
+  return status;
+}
+
+/* y = A x: per scalar row, blocks in ascending column order, c = 0..2, FMA from 0. */
+void oracle_spmv(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* val,
+                 const double* x, double* y) {
+  for (int32_t i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a) {
+      double acc = 0.0;
+      for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q)
+        for (int c = 0; c < 3; ++c) acc = fma(val[9 * q + 3 * a + c], x[3 * (int64_t)col[q] + c], acc);
+      y[3 * (int64_t)i + a] = acc;
+    }
+}
+
+/* Block rows per tile of the fixed dot order. */
+#define DOT_TILE 256
+
+/* In place pairwise (halving) sum of s[0..m), m a power of two: s[i] += s[i+h]. */
+static double halving_sum(double* s, int64_t m) {
+  for (int64_t h = m / 2; h >= 1; h /= 2)
+    for (int64_t i = 0; i < h; ++i) s[i] = s[i] + s[i + h];
+  return s[0];
+}
+
+/*
+ * x . y over n block rows (3n scalars) in one fixed order:
+ *  1. per block row: q_i = fma(x2, y2, fma(x1, y1, x0 * y0));
+ *  2. per tile of 256 block rows (missing rows count as 0): halving sum;
+ *  3. over the tile sums, padded with zeros to a power of two: halving sum.
+ */
+double oracle_dot(int32_t n, const double* x, const double* y) {
+  int64_t ntiles = (n + DOT_TILE - 1) / DOT_TILE;
+  if (ntiles == 0) return 0.0;
+  int64_t m = 1;
+  while (m < ntiles) m *= 2;
+  double* tile = (double*)calloc((size_t)m, sizeof(double));
+  double q[DOT_TILE];
+  for (int64_t t = 0; t < ntiles; ++t) {
+    for (int r = 0; r < DOT_TILE; ++r) {
+      int64_t i = t * DOT_TILE + r;
+      q[r] = 0.0;
+      if (i < n) q[r] = fma(x[3 * i + 2], y[3 * i + 2], fma(x[3 * i + 1], y[3 * i + 1], x[3 * i] * y[3 * i]));
+    }
+    tile[t] = halving_sum(q, DOT_TILE);
+  }
+  double s = halving_sum(tile, m);
+  free(tile);
+  return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1: preconditioned BiCGSTAB                                      */
+/* ------------------------------------------------------------------------ */
+
+enum {
+  ORC_OK = 0,
+  ORC_BREAKDOWN = 5,
+  ORC_NOT_CONVERGED = 6,
+  ORC_ZERO_PIVOT = 2,
+};
+
+typedef struct {
+  int32_t status, iterations, restarts, pad;
+  double rel_res_recurrence, rel_res_true;
+} oracle_info;
+
+static double rel_of(double rr, double bb) { return sqrt(rr) / sqrt(bb); }
+
+/*
+ * Solve A x = b with M = LU (right preconditioning), x0 = 0. A is the full
+ * reordered matrix, (lrp, lcol, lu) the ILU0 factors of the dropped one. All
+ * vectors are in the reordered numbering. hist (optional, maxit + 1 entries)
+ * receives ||r_j|| / ||b|| with hist[0] = 1.
+ */
+int oracle_bicgstab(int32_t n, const int32_t* arp, const int32_t* acol, const double* aval,
+                    const int32_t* lrp, const int32_t* lcol, const double* lu, const double* b,
+                    double* x, int32_t maxit, double rtol, oracle_info* info, double* hist) {
+  size_t m = 3 * (size_t)(n > 0 ? n : 1);
+  double *r = calloc(m, 8), *rh = calloc(m, 8), *p = calloc(m, 8), *v = calloc(m, 8);
+  double *s = calloc(m, 8), *t = calloc(m, 8), *ph = calloc(m, 8), *sh = calloc(m, 8);
+  int64_t len = 3 * (int64_t)n;
+  memset(info, 0, sizeof *info);
+  for (int64_t e = 0; e < len; ++e) x[e] = 0.0;
+  double bb = oracle_dot(n, b, b);
+  int status = ORC_NOT_CONVERGED;
+  if (!(bb > 0.0)) {
+    status = ORC_OK; /* b = 0: x = 0 is exact */
+    goto done;
+  }
+  for (int64_t e = 0; e < len; ++e) r[e] = b[e];
+  if (hist) hist[0] = 1.0;
+  int j = 0;
+  for (int restart = 0; restart < 2; ++restart) {
+    for (int64_t e = 0; e < len; ++e) rh[e] = r[e], p[e] = r[e];
+    double rho = oracle_dot(n, rh, r);
+    int converged = 0;
+    for (; j < maxit; ++j) {
+      if (oracle_apply(n, lrp, lcol, lu, p, ph)) { status = ORC_ZERO_PIVOT; goto done; }
+      oracle_spmv(n, arp, acol, aval, ph, v);
+      double rv = oracle_dot(n, rh, v);
+      if (rv == 0.0 || !isfinite(rv)) { status = ORC_BREAKDOWN; goto done; }
+      double alpha = rho / rv;
+      for (int64_t e = 0; e < len; ++e) s[e] = fma(-alpha, v[e], r[e]);
+      if (oracle_apply(n, lrp, lcol, lu, s, sh)) { status = ORC_ZERO_PIVOT; goto done; }
+      oracle_spmv(n, arp, acol, aval, sh, t);
+      double ts = oracle_dot(n, t, s);
+      double tt = oracle_dot(n, t, t);
+      double omega = tt == 0.0 ? 0.0 : ts / tt;
+      for (int64_t e = 0; e < len; ++e) {
+        x[e] = fma(omega, sh[e], fma(alpha, ph[e], x[e]));
+        r[e] = fma(-omega, t[e], s[e]);
+      }
+      double rr = oracle_dot(n, r, r);
+      double rel = rel_of(rr, bb);
+      info->rel_res_recurrence = rel;
+      if (hist) hist[j + 1] = rel;
+      if (!isfinite(rel)) { status = ORC_BREAKDOWN; goto done; }
+      if (rel < rtol) { ++j; converged = 1; break; }
+      double rho_new = oracle_dot(n, rh, r);
+      if (rho_new == 0.0 || omega == 0.0 || !isfinite(rho_new)) { status = ORC_BREAKDOWN; goto done; }
+      double beta = (alpha / omega) * (rho_new / rho);
+      for (int64_t e = 0; e < len; ++e) p[e] = fma(beta, fma(-omega, v[e], p[e]), r[e]);
+      rho = rho_new;
+    }
+    info->iterations = j;
+    if (!converged) { status = ORC_NOT_CONVERGED; goto done; }
+    /* true residual r = b - A x */
+    oracle_spmv(n, arp, acol, aval, x, t);
+    for (int64_t e = 0; e < len; ++e) r[e] = b[e] - t[e];
+    double rel_true = rel_of(oracle_dot(n, r, r), bb);
+    info->rel_res_true = rel_true;
+    if (rel_true < rtol) { status = ORC_OK; goto done; }
+    if (restart == 0) info->restarts = 1;
+  }
+  status = ORC_NOT_CONVERGED;
+done:
+  info->status = status;
+  free(r); free(rh); free(p); free(v); free(s); free(t); free(ph); free(sh);
+  return status;
+}

@@ -1,0 +1,168 @@
+/*
+ * Seeded synthetic inputs: 3D 7-point stencils with 3 unknowns per cell,
+ * stored as BSR with 3x3 row-major blocks in natural cell order
+ * gidx = i + nx*(j + ny*k) (the ordering the geometric-cut partition of
+ * Algorithm 2 assumes).
+ *
+ * This file holds no arithmetic of the solver or of the preconditioner. It is
+ * the common input source of the CPU oracle and of the CUDA library; both
+ * consume the arrays it writes.
+ *
+ * Random numbers: a counter-based generator. Each draw is the SplitMix64
+ * output function (Steele, Lea and Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014) applied to a counter derived from
+ * (seed, stream, index), so any entry can be recomputed on its own.
+ *
+ * Two coefficient models:
+ *  - "laplace": off-diagonal block of each existing face = -I + U(-0.1,0.1)
+ *    per entry; diagonal block = 6.5*I + U(-0.1,0.1) per entry.
+ *  - "layered": cell coefficient kappa = exp(2*g), g ~ N(0,1) drawn once per
+ *    (i, j, floor(k/8)); face coupling c_ab = H(kappa_a, kappa_b)*(I + P_ab)
+ *    with H the harmonic mean and P_ab a 3x3 U(-0.1,0.1) perturbation drawn per
+ *    directed face; off-diagonal block = -c_ab; diagonal block = sum of the
+ *    cell's face couplings + 0.01*I.
+ * x* ~ U(-1,1) per unknown; b = A x* (per scalar row, blocks in ascending
+ * column order, entries c = 0..2, fused multiply-add from 0).
+ *
+ * Build: gcc -O2 -ffp-contract=off -shared -fPIC (no fast-math), so the same
+ * source gives the same bits on x86-64 and aarch64 apart from libm's exp,
+ * log and cos (used by the layered model only).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+enum { STREAM_DIAG = 1, STREAM_OFF = 2, STREAM_XSTAR = 3, STREAM_FIELD = 4, STREAM_SIDES = 5 };
+
+static inline uint64_t sm64_out(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+/* Counter -> 64 random bits. */
+uint64_t synth_bits(uint64_t seed, uint64_t stream, uint64_t index) {
+  uint64_t key = sm64_out(seed * 0x9E3779B97F4A7C15ULL + stream);
+  return sm64_out(key + (index + 1) * 0x9E3779B97F4A7C15ULL);
+}
+
+/* Uniform double in [0, 1) with 53 random bits. */
+double synth_unit(uint64_t seed, uint64_t stream, uint64_t index) {
+  return (double)(synth_bits(seed, stream, index) >> 11) * 0x1.0p-53;
+}
+
+static inline double unif(uint64_t seed, uint64_t stream, uint64_t index, double lo, double hi) {
+  return lo + (hi - lo) * synth_unit(seed, stream, index);
+}
+
+/* Face directions of a cell: 0:-x 1:+x 2:-y 3:+y 4:-z 5:+z. */
+static inline int64_t nbr(int nx, int ny, int nz, int i, int j, int k, int dir) {
+  switch (dir) {
+    case 0: return i > 0 ? (int64_t)(i - 1) + (int64_t)nx * (j + (int64_t)ny * k) : -1;
+    case 1: return i + 1 < nx ? (int64_t)(i + 1) + (int64_t)nx * (j + (int64_t)ny * k) : -1;
+    case 2: return j > 0 ? (int64_t)i + (int64_t)nx * ((j - 1) + (int64_t)ny * k) : -1;
+    case 3: return j + 1 < ny ? (int64_t)i + (int64_t)nx * ((j + 1) + (int64_t)ny * k) : -1;
+    case 4: return k > 0 ? (int64_t)i + (int64_t)nx * (j + (int64_t)ny * (k - 1)) : -1;
+    default: return k + 1 < nz ? (int64_t)i + (int64_t)nx * (j + (int64_t)ny * (k + 1)) : -1;
+  }
+}
+
+/* Number of stored blocks: one diagonal block per cell plus two per interior face. */
+int64_t synth_nnzb(int nx, int ny, int nz) {
+  int64_t n = (int64_t)nx * ny * nz;
+  int64_t faces = (int64_t)(nx - 1) * ny * nz + (int64_t)nx * (ny - 1) * nz + (int64_t)nx * ny * (nz - 1);
+  return n + 2 * faces;
+}
+
+/* Row order of a cell's blocks in ascending column: -z, -y, -x, self, +x, +y, +z. */
+static const int k_order[7] = {4, 2, 0, -1, 1, 3, 5};
+
+/* Sparsity pattern only (row_ptr[N+1], col[nnzb]). */
+void synth_pattern(int nx, int ny, int nz, int32_t* row_ptr, int32_t* col) {
+  int64_t p = 0;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        int64_t g = (int64_t)i + (int64_t)nx * (j + (int64_t)ny * k);
+        row_ptr[g] = (int32_t)p;
+        for (int o = 0; o < 7; ++o) {
+          int d = k_order[o];
+          int64_t c = d < 0 ? g : nbr(nx, ny, nz, i, j, k, d);
+          if (c >= 0) col[p++] = (int32_t)c;
+        }
+      }
+  row_ptr[(int64_t)nx * ny * nz] = (int32_t)p;
+}
+
+static double layered_kappa(uint64_t seed, int nx, int ny, int i, int j, int k) {
+  uint64_t id = (uint64_t)i + (uint64_t)nx * ((uint64_t)j + (uint64_t)ny * (uint64_t)(k / 8));
+  double u1 = synth_unit(seed, STREAM_FIELD, 2 * id);
+  double u2 = synth_unit(seed, STREAM_FIELD, 2 * id + 1);
+  /* Box-Muller: 1-u1 lies in (0, 1], so the logarithm is finite. */
+  double g = sqrt(-2.0 * log(1.0 - u1)) * cos(6.283185307179586 * u2);
+  return exp(2.0 * g);
+}
+
+/*
+ * Full system. model 0 = laplace, 1 = layered. Writes row_ptr[N+1],
+ * col[nnzb], val[nnzb*9], xstar[3N], b[3N]. Returns the number of blocks.
+ */
+int64_t synth_system(int model, int nx, int ny, int nz, uint64_t seed, int32_t* row_ptr,
+                     int32_t* col, double* val, double* xstar, double* b) {
+  int64_t n = (int64_t)nx * ny * nz;
+  synth_pattern(nx, ny, nz, row_ptr, col);
+  for (int64_t g = 0; g < n; ++g)
+    for (int a = 0; a < 3; ++a) xstar[3 * g + a] = unif(seed, STREAM_XSTAR, (uint64_t)(3 * g + a), -1.0, 1.0);
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        int64_t g = (int64_t)i + (int64_t)nx * (j + (int64_t)ny * k);
+        int64_t p = row_ptr[g];
+        double diag[9];
+        double ka = model ? layered_kappa(seed, nx, ny, i, j, k) : 0.0;
+        if (model == 0) {
+          for (int e = 0; e < 9; ++e)
+            diag[e] = (e % 4 == 0 ? 6.5 : 0.0) + unif(seed, STREAM_DIAG, (uint64_t)(9 * g + e), -0.1, 0.1);
+        } else {
+          for (int e = 0; e < 9; ++e) diag[e] = (e % 4 == 0 ? 0.01 : 0.0);
+        }
+        int64_t pdiag = -1;
+        for (int o = 0; o < 7; ++o) {
+          int d = k_order[o];
+          if (d < 0) { pdiag = p++; continue; }
+          int64_t c = nbr(nx, ny, nz, i, j, k, d);
+          if (c < 0) continue;
+          double* blk = val + 9 * p;
+          uint64_t base = (uint64_t)(6 * g + d) * 9;
+          if (model == 0) {
+            for (int e = 0; e < 9; ++e)
+              blk[e] = (e % 4 == 0 ? -1.0 : 0.0) + unif(seed, STREAM_OFF, base + e, -0.1, 0.1);
+          } else {
+            int ci = (int)(c % nx), cj = (int)((c / nx) % ny), ck = (int)(c / ((int64_t)nx * ny));
+            double kb = layered_kappa(seed, nx, ny, ci, cj, ck);
+            double h = 2.0 * ka * kb / (ka + kb);
+            for (int e = 0; e < 9; ++e) {
+              double cpl = h * ((e % 4 == 0 ? 1.0 : 0.0) + unif(seed, STREAM_OFF, base + e, -0.1, 0.1));
+              blk[e] = -cpl;
+              diag[e] += cpl;
+            }
+          }
+          ++p;
+        }
+        memcpy(val + 9 * pdiag, diag, sizeof diag);
+      }
+  for (int64_t g = 0; g < n; ++g)
+    for (int a = 0; a < 3; ++a) {
+      double acc = 0.0;
+      for (int64_t p = row_ptr[g]; p < row_ptr[g + 1]; ++p)
+        for (int c = 0; c < 3; ++c) acc = fma(val[9 * p + 3 * a + c], xstar[3 * (int64_t)col[p] + c], acc);
+      b[3 * g + a] = acc;
+    }
+  return row_ptr[n];
+}
+
+/* Grid sides of one system of a ragged batch: integers uniform in [lo, hi]. */
+void synth_sides(uint64_t seed, int lo, int hi, int32_t* sides) {
+  for (int a = 0; a < 3; ++a)
+    sides[a] = lo + (int)(synth_unit(seed, STREAM_SIDES, (uint64_t)a) * (double)(hi - lo + 1));
+}
