@@ -1,0 +1,227 @@
+/*
+ * ilu0dd — subdomain-wise ILU0 preconditioning on GB300 (sm_103a).
+ *
+ * C ABI of the library built from paper_2508_04917_gb300/csrc. It implements
+ * the hot path of arXiv 2508.04917, "Mapping Sparse Triangular Solves to GPUs
+ * via Fine-grained Domain Decomposition": a 3x3-block (BSR) system A x = b
+ * from a 3D 7-point stencil is cut into box subdomains (Algorithm 2),
+ * reordered so every subdomain is a contiguous row range (Algorithm 3),
+ * stripped of inter-subdomain blocks (Section 3.2) and factored with ILU0 /
+ * ILDU0 (Algorithm 7). The preconditioner z = M^-1 r, M = LU, is then applied
+ * by one fused L -> D^-1 -> U kernel with one thread block per subdomain and
+ * the subdomain vector in shared memory, rows scheduled by level
+ * (Sections 4.2, 4.3, 4.4), inside preconditioned BiCGSTAB (Algorithm 1).
+ *
+ * Conventions of every entry point:
+ *  - Return value: ILU0DD_OK (0) or one of the ILU0DD_ERR_* codes below. No
+ *    exception crosses the ABI; nothing is printed unless opts.trace is set.
+ *  - "host" pointers are ordinary CPU memory, "device" pointers are CUDA
+ *    device memory of the current device.
+ *  - `stream` is a cudaStream_t passed as void*; 0 means the legacy default
+ *    stream.
+ *  - The library never allocates device memory. The caller allocates one
+ *    device workspace of ilu0_dd_workspace_size() bytes (256-byte aligned)
+ *    and keeps it alive for the lifetime of the context. Small host-side
+ *    bookkeeping (the context object, host copies for ilu0_dd_export) is
+ *    allocated with malloc and released by ilu0_dd_destroy.
+ *  - Vectors hold 3 doubles per block row (cell), entry 3*i + a.
+ */
+#ifndef ILU0DD_H_
+#define ILU0DD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define ILU0DD_OK 0
+#define ILU0DD_ERR_INVALID 1        /* bad pointer, size, pattern (unsorted columns, missing diagonal) */
+#define ILU0DD_ERR_ZERO_PIVOT 2     /* singular or non-finite 3x3 pivot block in ILU0 */
+#define ILU0DD_ERR_SMEM 3           /* a subdomain vector does not fit in shared memory */
+#define ILU0DD_ERR_CUDA 4           /* a CUDA call failed (see ilu0_dd_query ILU0DD_Q_CUDA_ERROR) */
+#define ILU0DD_ERR_BREAKDOWN 5      /* BiCGSTAB breakdown: (r^,v)=0, rho=0, omega=0 or non-finite */
+#define ILU0DD_ERR_NOT_CONVERGED 6  /* maxit reached, or the true residual misses rtol after a restart */
+#define ILU0DD_ERR_NONFINITE 7      /* NaN/Inf in an input vector */
+#define ILU0DD_ERR_WORKSPACE 8      /* workspace too small or misaligned */
+#define ILU0DD_ERR_DEVICE_WAIT 9    /* a device-side bounded wait expired (see ilu0_dd_device_error) */
+
+/* ---- factor storage precision (opts.factor_prec) --------------------- */
+#define ILU0DD_F64 0   /* factors and apply arithmetic in FP64 */
+#define ILU0DD_F32 1   /* factors stored in FP32, apply in FP32 */
+#define ILU0DD_BF16 2  /* factors stored in BF16, apply in FP32 */
+
+/* ---- inputs ----------------------------------------------------------- */
+
+/* 3x3-block CSR matrix in natural cell order gidx = i + nx*(j + ny*k).
+ * HOST pointers: row_ptr[n_brows+1], col_idx[nnzb] (strictly ascending per
+ * row, diagonal block present), val[9*nnzb] (row-major 3x3 blocks). */
+typedef struct {
+  int32_t n_brows;
+  int32_t reserved;
+  int64_t nnzb;
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const double* val;
+} ilu0dd_bsr;
+
+/* Grid (nx, ny, nz) and subdomain box (sx, sy, sz), the inputs of
+ * Algorithm 2. Edge subdomains are smaller when a side does not divide. */
+typedef struct {
+  int32_t nx, ny, nz;
+  int32_t sx, sy, sz;
+} ilu0dd_geom;
+
+typedef struct {
+  int32_t factor_prec;      /* ILU0DD_F64 / ILU0DD_F32 / ILU0DD_BF16 */
+  int32_t threads_per_cta;  /* apply block size; 0 = smallest multiple of 32 >= widest level (<= 512) */
+  int32_t ring_bytes;       /* apply staging ring per block (power of two); 0 = automatic */
+  int32_t maxit;            /* BiCGSTAB iteration limit; 0 = 10000 */
+  double rtol;              /* stop when ||r||_2/||b||_2 < rtol; 0 = 1e-8 */
+  int32_t check_every;      /* iterations per CUDA-graph launch between convergence polls; 0 = 8 */
+  int32_t use_graphs;       /* 1 = capture iterations as CUDA graphs (default), 0 = plain launches */
+  int32_t keep_host;        /* 1 = keep host copies of factors and levels for ilu0_dd_export */
+  int32_t trace;            /* 1 = print per-phase timings to stderr */
+} ilu0dd_opts;
+
+typedef struct {
+  int32_t status;             /* ILU0DD_OK or an error code */
+  int32_t iterations;         /* BiCGSTAB iterations (j + 1 at the stopping iteration) */
+  int32_t restarts;           /* 0 or 1: restarts from the true residual */
+  int32_t reserved;
+  double rel_res_recurrence;  /* ||r_j|| / ||b|| of the recurrence at exit */
+  double rel_res_true;        /* ||b - A x|| / ||b|| recomputed at exit */
+  double setup_s;             /* wall time of ilu0_dd_setup (host side included) */
+  double solve_s;             /* wall time of the last bicgstab_solve */
+} ilu0dd_info;
+
+typedef struct ilu0dd_ctx ilu0dd_ctx;
+
+/* Fill *opts with the defaults listed above. */
+int ilu0dd_default_opts(ilu0dd_opts* opts);
+
+/* Human-readable name of a return code (static string, never NULL). */
+const char* ilu0dd_strerror(int code);
+
+/*
+ * Device workspace bytes needed by ilu0_dd_setup for this matrix, geometry
+ * and options. Runs the structural part of the setup on the host
+ * (Algorithm 2, Algorithm 3, Section 3.2 drop, Algorithm 5 levels) without
+ * factoring. Errors: INVALID (pattern), SMEM (subdomain too large for shared
+ * memory of the current device).
+ */
+int ilu0_dd_workspace_size(const ilu0dd_bsr* A, const ilu0dd_geom* geom, const ilu0dd_opts* opts,
+                           size_t* bytes);
+
+/*
+ * Build the preconditioner and the solver state in d_workspace
+ * (ws_bytes >= ilu0_dd_workspace_size): partition (Algorithm 2), reorder
+ * (Algorithm 3), drop inter-subdomain blocks (Section 3.2), block ILU0 and
+ * ILDU0 in FP64 (Algorithm 7), level sets per subdomain (Algorithm 5), pack
+ * the factors for the fused apply in opts.factor_prec, and upload everything
+ * on `stream`. The host-side steps run on the CPU threads of the caller's
+ * process; A may be freed after return. Synchronizes `stream`.
+ * On success *out owns host memory released by ilu0_dd_destroy; it refers
+ * to d_workspace, which must outlive it.
+ */
+int ilu0_dd_setup(const ilu0dd_bsr* A, const ilu0dd_geom* geom, const ilu0dd_opts* opts,
+                  void* d_workspace, size_t ws_bytes, void* stream, ilu0dd_ctx** out);
+
+/*
+ * z = M^-1 r = U~^-1 D^-1 L^-1 r (Sections 4.3-4.4), one fused kernel launch.
+ * d_r, d_z: device, 3*N doubles each, in the reordered (subdomain-
+ * contiguous) numbering; they must not overlap. Asynchronous on `stream`.
+ * The context is only read, so concurrent applies on one context are safe.
+ */
+int ilu0_dd_apply(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream);
+
+/*
+ * y = A_p x with the full reordered matrix (all inter-subdomain blocks kept,
+ * Section 3.2 last paragraph). Device vectors in the reordered numbering,
+ * 3*N doubles each, not overlapping. Asynchronous on `stream`.
+ */
+int ilu0_dd_spmv(const ilu0dd_ctx* ctx, const double* d_x, double* d_y, void* stream);
+
+/*
+ * *d_result = x . y over 3*N doubles (device pointers) in the library's fixed
+ * summation order: per block row fma(x2,y2,fma(x1,y1,x0*y0)); halving sums in
+ * 256-row tiles; halving sum over tiles zero-padded to a power of two.
+ * Uses the context's reduction scratch: calls on one context must be
+ * serialized on one stream.
+ */
+int ilu0_dd_dot(const ilu0dd_ctx* ctx, const double* d_x, const double* d_y, double* d_result,
+                void* stream);
+
+/* Permute a device vector between numberings: dir 0 natural -> reordered,
+ * dir 1 reordered -> natural (Algorithm 3's perm/iperm). Asynchronous. */
+int ilu0_dd_permute(const ilu0dd_ctx* ctx, const double* d_in, double* d_out, int dir, void* stream);
+
+/*
+ * Preconditioned BiCGSTAB (Algorithm 1) with K1 = I, K2 = M (right
+ * preconditioning), x0 = 0, stopping when ||r_{j+1}||/||b|| < rtol, followed
+ * by a true-residual check and at most one restart. d_b and d_x are device
+ * vectors in the NATURAL numbering (3*N doubles); d_x receives the solution.
+ * Scalars stay on the device; iterations run as CUDA graphs of
+ * opts.check_every iterations. Synchronizes `stream`. The solver vectors live
+ * in the workspace: solves on one context must not overlap.
+ * Errors: BREAKDOWN, NOT_CONVERGED, NONFINITE, CUDA, DEVICE_WAIT.
+ */
+int bicgstab_solve(ilu0dd_ctx* ctx, const double* d_b, double* d_x, ilu0dd_info* info,
+                   void* stream);
+
+/* Residual history of the last solve: hist[j] = ||r_j||/||b||, j = 0..iterations
+ * (host destination of n doubles; copies min(n, iterations+1) entries). */
+int ilu0_dd_history(const ilu0dd_ctx* ctx, double* host_dst, int32_t n);
+
+/* ---- inspection ------------------------------------------------------ */
+#define ILU0DD_X_PART_ID 0   /* int32[N]   Algorithm 2 label per natural cell */
+#define ILU0DD_X_PERM 1      /* int32[N]   perm[new] = old */
+#define ILU0DD_X_IPERM 2     /* int32[N]   iperm[old] = new */
+#define ILU0DD_X_PART_PTR 3  /* int32[nsub+1] row range of each subdomain */
+#define ILU0DD_X_LEVEL_L 4   /* int32[N]   L level of each reordered row (local DAG) */
+#define ILU0DD_X_LEVEL_U 5   /* int32[N]   U level of each reordered row */
+#define ILU0DD_X_DD_ROW_PTR 6 /* int32[N+1] pattern of the dropped matrix */
+#define ILU0DD_X_DD_COL 7    /* int32[kept] */
+#define ILU0DD_X_L 8         /* double[kept*9]: L blocks at strictly-lower positions, 0 elsewhere */
+#define ILU0DD_X_UT 9        /* double[kept*9]: U~ = D^-1 U at strictly-upper positions, 0 elsewhere */
+#define ILU0DD_X_INVD 10     /* double[N*9]: D^-1 = U_ii^-1 per row */
+#define ILU0DD_X_AP_ROW_PTR 11 /* int32[N+1] reordered full matrix */
+#define ILU0DD_X_AP_COL 12   /* int32[nnzb] */
+
+/* Copy one array to host memory (`bytes` must equal its size). Arrays
+ * 4..10 need opts.keep_host = 1 at setup. */
+int ilu0_dd_export(const ilu0dd_ctx* ctx, int what, void* host_dst, size_t bytes);
+
+#define ILU0DD_Q_N 0              /* block rows */
+#define ILU0DD_Q_NNZB 1           /* blocks of A */
+#define ILU0DD_Q_KEPT 2           /* blocks kept after the drop */
+#define ILU0DD_Q_NSUB 3           /* subdomains (= apply thread blocks) */
+#define ILU0DD_Q_NL 4             /* strictly-lower blocks kept */
+#define ILU0DD_Q_NU 5             /* strictly-upper blocks kept */
+#define ILU0DD_Q_APPLY_BYTES 6    /* algorithmic bytes of one apply */
+#define ILU0DD_Q_SPMV_BYTES 7     /* algorithmic bytes of one SpMV */
+#define ILU0DD_Q_STREAM_BYTES 8   /* bytes of the packed factor stream */
+#define ILU0DD_Q_THREADS 9        /* apply threads per block */
+#define ILU0DD_Q_SMEM 10          /* apply dynamic shared memory per block */
+#define ILU0DD_Q_PIECES 11        /* barrier-separated pieces, summed over subdomains */
+#define ILU0DD_Q_CUDA_ERROR 12    /* last cudaError_t recorded by the context */
+#define ILU0DD_Q_MAX_LEVELS 13    /* max over subdomains of L levels + U levels */
+#define ILU0DD_Q_WORKSPACE 14     /* workspace bytes in use */
+#define ILU0DD_Q_APPLY_KERNELS 15 /* kernel launches per apply (always 1) */
+#define ILU0DD_Q_ITER_KERNELS 16  /* kernel launches per BiCGSTAB iteration */
+
+int ilu0_dd_query(const ilu0dd_ctx* ctx, int what, int64_t* value);
+
+/* Read (and clear) the device error word: 0, or the code of a bounded wait
+ * that expired inside a kernel. Synchronizes the device. */
+int ilu0_dd_device_error(const ilu0dd_ctx* ctx, int32_t* code);
+
+/* Release the host-side context (the caller frees the workspace). */
+void ilu0_dd_destroy(ilu0dd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ILU0DD_H_ */

@@ -1,0 +1,294 @@
+"""Thin ctypes binding of ``libilu0dd.so`` (argument marshalling only).
+
+Every step of the hot path runs in the library's CUDA kernels; PyTorch only
+provides device memory (the workspace, the vectors) and the current stream.
+There is no CPU fallback: if the library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ilu0dd.h")
+
+OK = 0
+ERR_INVALID, ERR_ZERO_PIVOT, ERR_SMEM, ERR_CUDA = 1, 2, 3, 4
+ERR_BREAKDOWN, ERR_NOT_CONVERGED, ERR_NONFINITE, ERR_WORKSPACE, ERR_DEVICE_WAIT = 5, 6, 7, 8, 9
+F64, F32, BF16 = 0, 1, 2
+PRECISIONS = {"f64": F64, "f32": F32, "bf16": BF16}
+
+X_PART_ID, X_PERM, X_IPERM, X_PART_PTR, X_LEVEL_L, X_LEVEL_U = 0, 1, 2, 3, 4, 5
+X_DD_ROW_PTR, X_DD_COL, X_L, X_UT, X_INVD, X_AP_ROW_PTR, X_AP_COL = 6, 7, 8, 9, 10, 11, 12
+
+Q = dict(n=0, nnzb=1, kept=2, nsub=3, nl=4, nu=5, apply_bytes=6, spmv_bytes=7, stream_bytes=8,
+         threads=9, smem=10, pieces=11, cuda_error=12, max_levels=13, workspace=14,
+         apply_kernels=15, iter_kernels=16)
+
+
+class Ilu0DDError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} (code {code})")
+
+
+class Bsr(ctypes.Structure):
+    _fields_ = [("n_brows", ctypes.c_int32), ("reserved", ctypes.c_int32), ("nnzb", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class Geom(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in ("nx", "ny", "nz", "sx", "sy", "sz")]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("factor_prec", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
+                ("ring_bytes", ctypes.c_int32), ("maxit", ctypes.c_int32), ("rtol", ctypes.c_double),
+                ("check_every", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
+                ("keep_host", ctypes.c_int32), ("trace", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("rel_res_recurrence", ctypes.c_double),
+                ("rel_res_true", ctypes.c_double), ("setup_s", ctypes.c_double), ("solve_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load ``libilu0dd.so`` (building it in-tree first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libilu0dd.so not found at {path}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        sig = {
+            "ilu0dd_default_opts": ([ctypes.POINTER(Opts)], ctypes.c_int),
+            "ilu0dd_strerror": ([ctypes.c_int], ctypes.c_char_p),
+            "ilu0_dd_workspace_size": ([ctypes.POINTER(Bsr), ctypes.POINTER(Geom), ctypes.POINTER(Opts),
+                                        ctypes.POINTER(sz)], ctypes.c_int),
+            "ilu0_dd_setup": ([ctypes.POINTER(Bsr), ctypes.POINTER(Geom), ctypes.POINTER(Opts), vp, sz, vp,
+                               ctypes.POINTER(vp)], ctypes.c_int),
+            "ilu0_dd_apply": ([vp, vp, vp, vp], ctypes.c_int),
+            "ilu0_dd_spmv": ([vp, vp, vp, vp], ctypes.c_int),
+            "ilu0_dd_dot": ([vp, vp, vp, vp, vp], ctypes.c_int),
+            "ilu0_dd_permute": ([vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
+            "bicgstab_solve": ([vp, vp, vp, ctypes.POINTER(Info), vp], ctypes.c_int),
+            "ilu0_dd_history": ([vp, vp, i32], ctypes.c_int),
+            "ilu0_dd_export": ([vp, ctypes.c_int, vp, sz], ctypes.c_int),
+            "ilu0_dd_query": ([vp, ctypes.c_int, ctypes.POINTER(i64)], ctypes.c_int),
+            "ilu0_dd_device_error": ([vp, ctypes.POINTER(i32)], ctypes.c_int),
+            "ilu0_dd_destroy": ([vp], None),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions declared in include/ilu0dd.h."""
+    text = open(_HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?(?:int|void|const char\s*\*)\s*\**\s*(\w+)\s*\(", text, re.M)))
+
+
+def strerror(code: int) -> str:
+    return load().ilu0dd_strerror(code).decode()
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    load().ilu0dd_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "factor_prec" and isinstance(v, str):
+            v = PRECISIONS[v]
+        setattr(o, k, v)
+    return o
+
+
+def _bsr(row_ptr, col, val):
+    rp = np.ascontiguousarray(row_ptr, np.int32)
+    ci = np.ascontiguousarray(col, np.int32)
+    va = None if val is None else np.ascontiguousarray(val, np.float64).reshape(-1)
+    b = Bsr(len(rp) - 1, 0, int(rp[-1]), rp.ctypes.data, ci.ctypes.data, None if va is None else va.ctypes.data)
+    return b, (rp, ci, va)
+
+
+def workspace_size(row_ptr, col, val, grid, sub, **opts) -> int:
+    """Structural query (host only): workspace bytes, or raises Ilu0DDError."""
+    b, keep = _bsr(row_ptr, col, val)
+    g = Geom(*grid, *sub)
+    o = default_opts(**opts)
+    n = ctypes.c_size_t(0)
+    rc = load().ilu0_dd_workspace_size(ctypes.byref(b), ctypes.byref(g), ctypes.byref(o), ctypes.byref(n))
+    del keep
+    if rc:
+        raise Ilu0DDError(rc, "ilu0_dd_workspace_size")
+    return int(n.value)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, n=None, what="vector"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{what} must be a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{what} must have {n} entries, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Ilu0DD:
+    """Subdomain ILU0 preconditioner + BiCGSTAB solver on one GPU.
+
+    ``row_ptr``, ``col``, ``val`` are host arrays of the natural-order BSR
+    matrix (``val`` of shape (nnzb, 3, 3) or flat); ``grid`` = (nx, ny, nz),
+    ``sub`` = (sx, sy, sz) are the inputs of Algorithm 2.
+    """
+
+    def __init__(self, row_ptr, col, val, grid, sub, *, device=None, stream=None, **opts):
+        import torch
+        lib = load()
+        self._lib = lib
+        self.grid, self.sub = tuple(grid), tuple(sub)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        b, keep = _bsr(row_ptr, col, val)
+        g = Geom(*grid, *sub)
+        self.opts = default_opts(**opts)
+        n = ctypes.c_size_t(0)
+        rc = lib.ilu0_dd_workspace_size(ctypes.byref(b), ctypes.byref(g), ctypes.byref(self.opts), ctypes.byref(n))
+        if rc:
+            raise Ilu0DDError(rc, "ilu0_dd_workspace_size")
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=self.device)
+            ctx = ctypes.c_void_p()
+            rc = lib.ilu0_dd_setup(ctypes.byref(b), ctypes.byref(g), ctypes.byref(self.opts),
+                                   ctypes.c_void_p(self.workspace.data_ptr()), ctypes.c_size_t(self.workspace.numel()),
+                                   _stream(stream), ctypes.byref(ctx))
+        del keep
+        if rc:
+            raise Ilu0DDError(rc, "ilu0_dd_setup")
+        self._ctx = ctx
+        self.n = self.query("n")
+        self.size = 3 * self.n
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.ilu0_dd_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc:
+            raise Ilu0DDError(rc, what)
+
+    def _new(self):
+        import torch
+        return torch.empty(self.size, dtype=torch.float64, device=self.device)
+
+    # -- hot path ---------------------------------------------------------
+    def apply(self, r, z=None, stream=None):
+        """z = M^-1 r (reordered numbering)."""
+        z = self._new() if z is None else z
+        self._check(self._lib.ilu0_dd_apply(self._ctx, _dptr(r, self.size, "r"), _dptr(z, self.size, "z"),
+                                            _stream(stream)), "ilu0_dd_apply")
+        return z
+
+    def spmv(self, x, y=None, stream=None):
+        """y = A_p x (reordered numbering, full matrix)."""
+        y = self._new() if y is None else y
+        self._check(self._lib.ilu0_dd_spmv(self._ctx, _dptr(x, self.size, "x"), _dptr(y, self.size, "y"),
+                                           _stream(stream)), "ilu0_dd_spmv")
+        return y
+
+    def dot(self, x, y, out=None, stream=None):
+        """x . y in the library's fixed order; returns a 1-element CUDA tensor."""
+        import torch
+        out = torch.empty(1, dtype=torch.float64, device=self.device) if out is None else out
+        self._check(self._lib.ilu0_dd_dot(self._ctx, _dptr(x, self.size, "x"), _dptr(y, self.size, "y"),
+                                          _dptr(out, 1, "out"), _stream(stream)), "ilu0_dd_dot")
+        return out
+
+    def permute(self, x, direction: int, out=None, stream=None):
+        """direction 0: natural -> reordered; 1: reordered -> natural."""
+        out = self._new() if out is None else out
+        self._check(self._lib.ilu0_dd_permute(self._ctx, _dptr(x, self.size, "in"), _dptr(out, self.size, "out"),
+                                              int(direction), _stream(stream)), "ilu0_dd_permute")
+        return out
+
+    def solve(self, b, x=None, stream=None, check=True):
+        """BiCGSTAB (Algorithm 1) on natural-order device vectors; returns (x, info dict)."""
+        x = self._new() if x is None else x
+        info = Info()
+        rc = self._lib.bicgstab_solve(self._ctx, _dptr(b, self.size, "b"), _dptr(x, self.size, "x"),
+                                      ctypes.byref(info), _stream(stream))
+        if rc and check:
+            raise Ilu0DDError(rc, "bicgstab_solve")
+        d = info.as_dict()
+        d["status"] = rc
+        return x, d
+
+    # -- inspection -------------------------------------------------------
+    def history(self, n=None):
+        n = (self.opts.maxit + 1) if n is None else n
+        buf = np.zeros(n, np.float64)
+        self._check(self._lib.ilu0_dd_history(self._ctx, buf.ctypes.data, n), "ilu0_dd_history")
+        return buf
+
+    def query(self, what):
+        v = ctypes.c_int64(0)
+        self._check(self._lib.ilu0_dd_query(self._ctx, Q[what] if isinstance(what, str) else what,
+                                            ctypes.byref(v)), "ilu0_dd_query")
+        return int(v.value)
+
+    def export(self, what):
+        n, kept, nsub = self.n, self.query("kept"), self.query("nsub")
+        spec = {X_PART_ID: (np.int32, n), X_PERM: (np.int32, n), X_IPERM: (np.int32, n),
+                X_PART_PTR: (np.int32, nsub + 1), X_LEVEL_L: (np.int32, n), X_LEVEL_U: (np.int32, n),
+                X_DD_ROW_PTR: (np.int32, n + 1), X_DD_COL: (np.int32, kept), X_L: (np.float64, 9 * kept),
+                X_UT: (np.float64, 9 * kept), X_INVD: (np.float64, 9 * n), X_AP_ROW_PTR: (np.int32, n + 1),
+                X_AP_COL: (np.int32, self.query("nnzb"))}
+        dt, cnt = spec[what]
+        buf = np.empty(cnt, dt)
+        self._check(self._lib.ilu0_dd_export(self._ctx, what, buf.ctypes.data, buf.nbytes), "ilu0_dd_export")
+        return buf
+
+    def device_error(self) -> int:
+        v = ctypes.c_int32(0)
+        self._check(self._lib.ilu0_dd_device_error(self._ctx, ctypes.byref(v)), "ilu0_dd_device_error")
+        return int(v.value)

@@ -1,0 +1,490 @@
+// The C ABI declared in include/ilu0dd.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.h"
+
+using namespace ilu0dd;
+
+struct ilu0dd_ctx {
+  Plan plan;
+  DevCtx dev{};
+  unsigned char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int device = 0;
+  cudaStream_t own = nullptr;       // private stream of bicgstab_solve
+  cudaGraphExec_t graph = nullptr;  // opts.check_every iterations
+  int graph_iters = 0;
+  double rtol = 1e-8;
+  int32_t maxit = 10000;
+  int check_every = 8;
+  bool use_graphs = true;
+  bool trace = false;
+  double setup_s = 0.0;
+  int last_iterations = 0;
+  cudaError_t last_cuda = cudaSuccess;
+  std::string why;
+  // host copies for ilu0_dd_export (opts.keep_host)
+  std::vector<double> F, invD;
+  bool have_factors = false;
+};
+
+namespace {
+
+int cuda_fail(ilu0dd_ctx* c, cudaError_t e, const char* what) {
+  if (c) {
+    c->last_cuda = e;
+    c->why = std::string(what) + ": " + cudaGetErrorString(e);
+    if (c->trace) std::fprintf(stderr, "[ilu0dd] %s\n", c->why.c_str());
+  }
+  return ILU0DD_ERR_CUDA;
+}
+
+#define CK(ctx, call)                                    \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+ilu0dd_opts resolved(const ilu0dd_opts* o) {
+  ilu0dd_opts r;
+  ilu0dd_default_opts(&r);
+  if (o) r = *o;
+  if (r.maxit <= 0) r.maxit = 10000;
+  if (!(r.rtol > 0.0)) r.rtol = 1e-8;
+  if (r.check_every <= 0) r.check_every = 8;
+  return r;
+}
+
+int max_smem_optin() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 232448;  // sm_103 opt-in limit: lets the structural query run without a device
+  }
+  return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ilu0dd_default_opts(ilu0dd_opts* o) {
+  if (!o) return ILU0DD_ERR_INVALID;
+  std::memset(o, 0, sizeof *o);
+  o->factor_prec = ILU0DD_F64;
+  o->threads_per_cta = 0;
+  o->ring_bytes = 0;
+  o->maxit = 10000;
+  o->rtol = 1e-8;
+  o->check_every = 8;
+  o->use_graphs = 1;
+  o->keep_host = 0;
+  o->trace = 0;
+  return ILU0DD_OK;
+}
+
+const char* ilu0dd_strerror(int code) {
+  switch (code) {
+    case ILU0DD_OK: return "ok";
+    case ILU0DD_ERR_INVALID: return "invalid argument or matrix pattern";
+    case ILU0DD_ERR_ZERO_PIVOT: return "singular or non-finite pivot block in ILU0";
+    case ILU0DD_ERR_SMEM: return "subdomain does not fit in shared memory";
+    case ILU0DD_ERR_CUDA: return "CUDA error";
+    case ILU0DD_ERR_BREAKDOWN: return "BiCGSTAB breakdown";
+    case ILU0DD_ERR_NOT_CONVERGED: return "BiCGSTAB did not converge";
+    case ILU0DD_ERR_NONFINITE: return "non-finite input";
+    case ILU0DD_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case ILU0DD_ERR_DEVICE_WAIT: return "device-side bounded wait expired";
+    default: return "unknown error code";
+  }
+}
+
+int ilu0_dd_workspace_size(const ilu0dd_bsr* A, const ilu0dd_geom* geom, const ilu0dd_opts* opts,
+                           size_t* bytes) {
+  if (!A || !geom || !bytes) return ILU0DD_ERR_INVALID;
+  ilu0dd_opts o = resolved(opts);
+  Plan p;
+  std::string why;
+  int rc = make_plan(A, geom, &o, max_smem_optin(), &p, &why);
+  if (rc) {
+    if (o.trace) std::fprintf(stderr, "[ilu0dd] workspace_size: %s\n", why.c_str());
+    return rc;
+  }
+  *bytes = p.lay.total;
+  return ILU0DD_OK;
+}
+
+int ilu0_dd_setup(const ilu0dd_bsr* A, const ilu0dd_geom* geom, const ilu0dd_opts* opts, void* d_workspace,
+                  size_t ws_bytes, void* stream, ilu0dd_ctx** out) {
+  if (!A || !geom || !out) return ILU0DD_ERR_INVALID;
+  *out = nullptr;
+  const double t0 = wall_seconds();
+  ilu0dd_opts o = resolved(opts);
+  ilu0dd_ctx* c = new (std::nothrow) ilu0dd_ctx();
+  if (!c) return ILU0DD_ERR_INVALID;
+  c->trace = o.trace != 0;
+  int rc = make_plan(A, geom, &o, max_smem_optin(), &c->plan, &c->why);
+  if (rc) {
+    if (c->trace) std::fprintf(stderr, "[ilu0dd] setup: %s\n", c->why.c_str());
+    delete c;
+    return rc;
+  }
+  Plan& p = c->plan;
+  if (!d_workspace || ws_bytes < p.lay.total || (reinterpret_cast<uintptr_t>(d_workspace) & 255)) {
+    delete c;
+    return ILU0DD_ERR_WORKSPACE;
+  }
+  const double t1 = wall_seconds();
+  int32_t bad = -1;
+  std::vector<double> F, invD;
+  rc = factor_ildu0(p, A->val, &F, &invD, &bad);
+  if (rc) {
+    if (c->trace) std::fprintf(stderr, "[ilu0dd] setup: zero pivot at reordered row %d\n", bad);
+    delete c;
+    return rc;
+  }
+  const double t2 = wall_seconds();
+  std::vector<uint8_t> sbytes;
+  pack_stream(p, F, invD, &sbytes);
+  std::vector<int32_t> sell_col;
+  std::vector<double> sell_val;
+  pack_sell(p, A->val, &sell_col, &sell_val);
+  const double t3 = wall_seconds();
+
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  c->ws = static_cast<unsigned char*>(d_workspace);
+  c->ws_bytes = ws_bytes;
+  c->rtol = o.rtol;
+  c->maxit = o.maxit;
+  c->check_every = o.check_every;
+  c->use_graphs = o.use_graphs != 0;
+  {
+    auto up = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
+      if (!bytes) return cudaSuccess;
+      return cudaMemcpyAsync(c->ws + off, src, bytes, cudaMemcpyHostToDevice, s);
+    };
+    const Plan::Layout& L = p.lay;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = up(L.stream, sbytes.data(), sbytes.size());
+    if (e == cudaSuccess) e = up(L.cta, p.cta.data(), sizeof(CtaDesc) * p.cta.size());
+    if (e == cudaSuccess) e = up(L.pieces, p.pieces.data(), sizeof(PieceDesc) * p.pieces.size());
+    if (e == cudaSuccess) e = up(L.sell_off, p.slice_off.data(), sizeof(int32_t) * p.slice_off.size());
+    if (e == cudaSuccess) e = up(L.sell_col, sell_col.data(), sizeof(int32_t) * sell_col.size());
+    if (e == cudaSuccess) e = up(L.sell_val, sell_val.data(), sizeof(double) * sell_val.size());
+    if (e == cudaSuccess) e = up(L.perm, p.perm.data(), sizeof(int32_t) * p.perm.size());
+    if (e == cudaSuccess) e = up(L.iperm, p.iperm.data(), sizeof(int32_t) * p.iperm.size());
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.partials, 0, sizeof(double) * 5 * (size_t)p.ntiles_pow2, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.counters, 0, sizeof(uint32_t) * 16, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.scal, 0, sizeof(SolverScalars), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.err, 0, sizeof(int32_t) * 4, s);
+    for (int v = 0; v < kNumVec && e == cudaSuccess; ++v)
+      e = cudaMemsetAsync(c->ws + L.vec[v], 0, sizeof(double) * 3 * (size_t)p.N, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host staging buffers die below
+    if (e != cudaSuccess) {
+      int r = cuda_fail(c, e, "setup upload");
+      delete c;
+      return r;
+    }
+    DevCtx& d = c->dev;
+    d.stream = c->ws + L.stream;
+    d.cta = reinterpret_cast<const CtaDesc*>(c->ws + L.cta);
+    d.pieces = reinterpret_cast<const PieceDesc*>(c->ws + L.pieces);
+    d.nsub = p.nsub;
+    d.threads = p.threads;
+    d.ring_bytes = p.ring_bytes;
+    d.chunk_bytes = p.chunk_bytes;
+    d.nslot = p.nslot;
+    d.vec_bytes = (int)(p.smem_bytes - (size_t)p.ring_bytes);
+    d.factor_prec = o.factor_prec;
+    d.smem_bytes = p.smem_bytes;
+    d.slice_off = reinterpret_cast<const int32_t*>(c->ws + L.sell_off);
+    d.sell_col = reinterpret_cast<const int32_t*>(c->ws + L.sell_col);
+    d.sell_val = reinterpret_cast<const double*>(c->ws + L.sell_val);
+    d.nslices = p.nslices;
+    d.perm = reinterpret_cast<const int32_t*>(c->ws + L.perm);
+    d.iperm = reinterpret_cast<const int32_t*>(c->ws + L.iperm);
+    d.N = p.N;
+    d.ntiles = p.ntiles;
+    d.ntiles_pow2 = p.ntiles_pow2;
+    for (int v = 0; v < kNumVec; ++v) d.vec[v] = reinterpret_cast<double*>(c->ws + L.vec[v]);
+    d.partials = reinterpret_cast<double*>(c->ws + L.partials);
+    d.counters = reinterpret_cast<uint32_t*>(c->ws + L.counters);
+    d.scal = reinterpret_cast<SolverScalars*>(c->ws + L.scal);
+    d.hist = reinterpret_cast<double*>(c->ws + L.hist);
+    d.err = reinterpret_cast<int32_t*>(c->ws + L.err);
+    e = apply_configure(d);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      int r = cuda_fail(c, e, "setup configure");
+      if (c->own) cudaStreamDestroy(c->own);
+      delete c;
+      return r;
+    }
+  }
+  if (o.keep_host) {
+    c->F.swap(F);
+    c->invD.swap(invD);
+    c->have_factors = true;
+  }
+  const double t4 = wall_seconds();
+  c->setup_s = t4 - t0;
+  if (c->trace)
+    std::fprintf(stderr,
+                 "[ilu0dd] setup: plan %.3fs factor %.3fs pack %.3fs upload %.3fs; N=%d nsub=%d pieces=%lld "
+                 "threads=%d smem=%zu stream=%lld B\n",
+                 t1 - t0, t2 - t1, t3 - t2, t4 - t3, p.N, p.nsub, (long long)p.n_pieces, p.threads,
+                 p.smem_bytes, (long long)p.stream_bytes);
+  *out = c;
+  return ILU0DD_OK;
+}
+
+int ilu0_dd_apply(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream) {
+  if (!ctx || (ctx->plan.N > 0 && (!d_r || !d_z))) return ILU0DD_ERR_INVALID;
+  const size_t n = 3 * (size_t)ctx->plan.N * sizeof(double);
+  const char* r = reinterpret_cast<const char*>(d_r);
+  const char* z = reinterpret_cast<const char*>(d_z);
+  if (r < z + n && z < r + n) return ILU0DD_ERR_INVALID;  // overlapping vectors
+  cudaError_t e = launch_apply(ctx->dev, kModePlain, d_r, d_z, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(const_cast<ilu0dd_ctx*>(ctx), e, "apply launch");
+  return ILU0DD_OK;
+}
+
+int ilu0_dd_spmv(const ilu0dd_ctx* ctx, const double* d_x, double* d_y, void* stream) {
+  if (!ctx || (ctx->plan.N > 0 && (!d_x || !d_y)) || d_x == d_y) return ILU0DD_ERR_INVALID;
+  cudaError_t e = launch_spmv(ctx->dev, 0, d_x, d_y, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(const_cast<ilu0dd_ctx*>(ctx), e, "spmv launch");
+  return ILU0DD_OK;
+}
+
+int ilu0_dd_dot(const ilu0dd_ctx* ctx, const double* d_x, const double* d_y, double* d_result, void* stream) {
+  if (!ctx || !d_result || (ctx->plan.N > 0 && (!d_x || !d_y))) return ILU0DD_ERR_INVALID;
+  cudaError_t e = launch_dot(ctx->dev, d_x, d_y, d_result, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(const_cast<ilu0dd_ctx*>(ctx), e, "dot launch");
+  return ILU0DD_OK;
+}
+
+int ilu0_dd_permute(const ilu0dd_ctx* ctx, const double* d_in, double* d_out, int dir, void* stream) {
+  if (!ctx || (dir != 0 && dir != 1) || (ctx->plan.N > 0 && (!d_in || !d_out)) || d_in == d_out)
+    return ILU0DD_ERR_INVALID;
+  cudaError_t e = launch_permute(ctx->dev, d_in, d_out, dir, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(const_cast<ilu0dd_ctx*>(ctx), e, "permute launch");
+  return ILU0DD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// One BiCGSTAB iteration of Algorithm 1 as five launches.
+cudaError_t launch_iteration(const DevCtx& d, cudaStream_t s) {
+  cudaError_t e;
+  // p = r + beta (p - omega v); ph = M^-1 p
+  if ((e = launch_apply(d, kModeP, d.vec[kVecR], d.vec[kVecPh], s)) != cudaSuccess) return e;
+  // v = A ph; alpha = rho / (rh . v)
+  if ((e = launch_spmv(d, 1, d.vec[kVecPh], d.vec[kVecV], s)) != cudaSuccess) return e;
+  // s = r - alpha v; sh = M^-1 s
+  if ((e = launch_apply(d, kModeS, d.vec[kVecR], d.vec[kVecSh], s)) != cudaSuccess) return e;
+  // t = A sh; omega = (t . s) / (t . t)
+  if ((e = launch_spmv(d, 2, d.vec[kVecSh], d.vec[kVecT], s)) != cudaSuccess) return e;
+  // x += alpha ph + omega sh; r = s - omega t; convergence; beta
+  return launch_update(d, s);
+}
+
+cudaError_t run_chunk(ilu0dd_ctx* c) {
+  const DevCtx& d = c->dev;
+  if (!c->use_graphs) {
+    for (int i = 0; i < c->check_every; ++i) {
+      cudaError_t e = launch_iteration(d, c->own);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  if (!c->graph) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->own, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < c->check_every && e == cudaSuccess; ++i) e = launch_iteration(d, c->own);
+    cudaError_t e2 = cudaStreamEndCapture(c->own, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return e;
+    c->graph_iters = c->check_every;
+  }
+  return cudaGraphLaunch(c->graph, c->own);
+}
+
+cudaError_t read_scalars(ilu0dd_ctx* c, SolverScalars* h) {
+  cudaError_t e = cudaMemcpyAsync(h, c->dev.scal, sizeof *h, cudaMemcpyDeviceToHost, c->own);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->own);
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bicgstab_solve(ilu0dd_ctx* c, const double* d_b, double* d_x, ilu0dd_info* info, void* stream) {
+  if (!c || (c->plan.N > 0 && (!d_b || !d_x))) return ILU0DD_ERR_INVALID;
+  const double t0 = wall_seconds();
+  const DevCtx& d = c->dev;
+  cudaStream_t us = reinterpret_cast<cudaStream_t>(stream);
+  SolverScalars h{};
+  int status = ILU0DD_OK, restarts = 0;
+  CK(c, cudaStreamSynchronize(us));
+  if (c->plan.N == 0) {
+    if (info) {
+      std::memset(info, 0, sizeof *info);
+      info->setup_s = c->setup_s;
+    }
+    return ILU0DD_OK;
+  }
+  CK(c, launch_permute(d, d_b, d.vec[kVecB], 0, c->own));
+  CK(c, launch_init(d, c->rtol, c->maxit, c->own));
+  CK(c, read_scalars(c, &h));
+  if (h.status == ILU0DD_ERR_NONFINITE) status = ILU0DD_ERR_NONFINITE;
+  while (status == ILU0DD_OK && !h.converged) {
+    while (!h.done) {
+      CK(c, run_chunk(c));
+      CK(c, read_scalars(c, &h));
+    }
+    if (h.status != ILU0DD_OK) {
+      status = h.status;
+      break;
+    }
+    // true residual r = b - A x
+    CK(c, launch_spmv(d, 0, d.vec[kVecX], d.vec[kVecT], c->own));
+    CK(c, launch_residual(d, 0, c->own));
+    CK(c, read_scalars(c, &h));
+    if (h.rel_true < c->rtol) break;
+    if (restarts == 0) {
+      restarts = 1;
+      CK(c, launch_residual(d, 1, c->own));
+      CK(c, read_scalars(c, &h));
+      continue;
+    }
+    status = ILU0DD_ERR_NOT_CONVERGED;
+    break;
+  }
+  // a device wait that expired poisons the result
+  int32_t derr = 0;
+  CK(c, cudaMemcpyAsync(&derr, d.err, sizeof derr, cudaMemcpyDeviceToHost, c->own));
+  CK(c, launch_permute(d, d.vec[kVecX], d_x, 1, c->own));
+  CK(c, cudaStreamSynchronize(c->own));
+  if (derr && status == ILU0DD_OK) status = ILU0DD_ERR_DEVICE_WAIT;
+  c->last_iterations = h.iter;
+  if (info) {
+    info->status = status;
+    info->iterations = h.iter;
+    info->restarts = restarts;
+    info->reserved = 0;
+    info->rel_res_recurrence = h.rel;
+    info->rel_res_true = h.rel_true;
+    info->setup_s = c->setup_s;
+    info->solve_s = wall_seconds() - t0;
+  }
+  if (c->trace)
+    std::fprintf(stderr, "[ilu0dd] solve: status=%d iterations=%d restarts=%d rel=%.3e true=%.3e %.4fs\n", status,
+                 h.iter, restarts, h.rel, h.rel_true, wall_seconds() - t0);
+  return status;
+}
+
+int ilu0_dd_history(const ilu0dd_ctx* c, double* host_dst, int32_t n) {
+  if (!c || !host_dst || n < 0) return ILU0DD_ERR_INVALID;
+  int32_t m = std::min(n, c->last_iterations + 1);
+  if (m <= 0) return ILU0DD_OK;
+  cudaError_t e = cudaMemcpy(host_dst, c->dev.hist, sizeof(double) * (size_t)m, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(const_cast<ilu0dd_ctx*>(c), e, "history copy");
+  return ILU0DD_OK;
+}
+
+int ilu0_dd_export(const ilu0dd_ctx* c, int what, void* dst, size_t bytes) {
+  if (!c || !dst) return ILU0DD_ERR_INVALID;
+  const Plan& p = c->plan;
+  auto put = [&](const void* src, size_t n) {
+    if (n != bytes) return ILU0DD_ERR_INVALID;
+    if (n) std::memcpy(dst, src, n);
+    return ILU0DD_OK;
+  };
+  const size_t kept = (size_t)p.dd_rp[p.N];
+  switch (what) {
+    case ILU0DD_X_PART_ID: return put(p.part_id.data(), 4 * p.part_id.size());
+    case ILU0DD_X_PERM: return put(p.perm.data(), 4 * p.perm.size());
+    case ILU0DD_X_IPERM: return put(p.iperm.data(), 4 * p.iperm.size());
+    case ILU0DD_X_PART_PTR: return put(p.part_ptr.data(), 4 * p.part_ptr.size());
+    case ILU0DD_X_LEVEL_L: return put(p.lev_l.data(), 4 * p.lev_l.size());
+    case ILU0DD_X_LEVEL_U: return put(p.lev_u.data(), 4 * p.lev_u.size());
+    case ILU0DD_X_DD_ROW_PTR: return put(p.dd_rp.data(), 4 * p.dd_rp.size());
+    case ILU0DD_X_DD_COL: return put(p.dd_col.data(), 4 * p.dd_col.size());
+    case ILU0DD_X_AP_ROW_PTR: return put(p.ap_rp.data(), 4 * p.ap_rp.size());
+    case ILU0DD_X_AP_COL: return put(p.ap_col.data(), 4 * p.ap_col.size());
+    case ILU0DD_X_INVD:
+      if (!c->have_factors) return ILU0DD_ERR_INVALID;
+      return put(c->invD.data(), 8 * c->invD.size());
+    case ILU0DD_X_L:
+    case ILU0DD_X_UT: {
+      if (!c->have_factors || bytes != 72 * kept) return ILU0DD_ERR_INVALID;
+      double* o = static_cast<double*>(dst);
+      for (int32_t i = 0; i < p.N; ++i)
+        for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1]; ++q) {
+          const bool take = what == ILU0DD_X_L ? p.dd_col[q] < i : p.dd_col[q] > i;
+          for (int e = 0; e < 9; ++e) o[9 * q + e] = take ? c->F[9 * (size_t)q + e] : 0.0;
+        }
+      return ILU0DD_OK;
+    }
+    default: return ILU0DD_ERR_INVALID;
+  }
+}
+
+int ilu0_dd_query(const ilu0dd_ctx* c, int what, int64_t* v) {
+  if (!c || !v) return ILU0DD_ERR_INVALID;
+  const Plan& p = c->plan;
+  switch (what) {
+    case ILU0DD_Q_N: *v = p.N; break;
+    case ILU0DD_Q_NNZB: *v = p.nnzb; break;
+    case ILU0DD_Q_KEPT: *v = p.dd_rp[p.N]; break;
+    case ILU0DD_Q_NSUB: *v = p.nsub; break;
+    case ILU0DD_Q_NL: *v = p.nL; break;
+    case ILU0DD_Q_NU: *v = p.nU; break;
+    case ILU0DD_Q_APPLY_BYTES: *v = p.apply_bytes; break;
+    case ILU0DD_Q_SPMV_BYTES: *v = p.spmv_bytes; break;
+    case ILU0DD_Q_STREAM_BYTES: *v = p.stream_bytes; break;
+    case ILU0DD_Q_THREADS: *v = p.threads; break;
+    case ILU0DD_Q_SMEM: *v = (int64_t)p.smem_bytes; break;
+    case ILU0DD_Q_PIECES: *v = p.n_pieces; break;
+    case ILU0DD_Q_CUDA_ERROR: *v = (int64_t)c->last_cuda; break;
+    case ILU0DD_Q_MAX_LEVELS: *v = p.max_levels; break;
+    case ILU0DD_Q_WORKSPACE: *v = (int64_t)p.lay.total; break;
+    case ILU0DD_Q_APPLY_KERNELS: *v = 1; break;
+    case ILU0DD_Q_ITER_KERNELS: *v = 5; break;
+    default: return ILU0DD_ERR_INVALID;
+  }
+  return ILU0DD_OK;
+}
+
+int ilu0_dd_device_error(const ilu0dd_ctx* c, int32_t* code) {
+  if (!c || !code) return ILU0DD_ERR_INVALID;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(code, c->dev.err, sizeof *code, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(c->dev.err, 0, sizeof *code);
+  if (e != cudaSuccess) return cuda_fail(const_cast<ilu0dd_ctx*>(c), e, "device error read");
+  return ILU0DD_OK;
+}
+
+void ilu0_dd_destroy(ilu0dd_ctx* c) {
+  if (!c) return;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->own) cudaStreamDestroy(c->own);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,189 @@
+// Device helpers: mbarrier + bulk-copy (TMA) staging, bounded waits, the fixed
+// reduction order, precision conversions. sm_103a only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace ilu0dd {
+
+// Error word codes written by kernels (device error word).
+constexpr int32_t kDevErrWaitExpired = 1;
+
+// Iteration limit of an mbarrier wait loop. Each try_wait suspends the thread
+// for a hardware-chosen interval; the limit keeps every wait finite (well
+// above any legitimate copy latency) so a lost completion ends the kernel
+// with an error word instead of a hang.
+constexpr uint32_t kWaitSpins = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the completion of phase `parity`; false if the limit expired.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kWaitSpins; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// One-dimensional bulk copy global -> shared, completing on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ float bf16_to_f32(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+
+template <typename TF>
+struct FactorLoad;
+template <>
+struct FactorLoad<double> {
+  using compute = double;
+  __device__ __forceinline__ static double get(const unsigned char* p) { return *reinterpret_cast<const double*>(p); }
+};
+template <>
+struct FactorLoad<float> {
+  using compute = float;
+  __device__ __forceinline__ static float get(const unsigned char* p) { return *reinterpret_cast<const float*>(p); }
+};
+struct bf16s {
+  uint16_t v;
+};
+template <>
+struct FactorLoad<bf16s> {
+  using compute = float;
+  __device__ __forceinline__ static float get(const unsigned char* p) {
+    return bf16_to_f32(*reinterpret_cast<const uint16_t*>(p));
+  }
+};
+
+// Fixed-order block reduction of kDotTile values, one per thread of a
+// kDotTile-thread block: halving sums s[i] += s[i + h], h = 128 .. 1. `buf`
+// holds kDotTile doubles of shared memory. Result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void tile_halving_sum(double (&q)[NV], double (*buf)[kDotTile]) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) buf[v][t] = q[v];
+  __syncthreads();
+#pragma unroll
+  for (int h = kDotTile / 2; h >= 32; h >>= 1) {
+    if (t < h) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) buf[v][t] = buf[v][t] + buf[v][t + h];
+    }
+    __syncthreads();
+  }
+  if (t < 32) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double s = buf[v][t];
+#pragma unroll
+      for (int h = 16; h >= 1; h >>= 1) {
+        double o = __shfl_down_sync(0xffffffffu, s, h);
+        s = s + o;  // lanes < h hold s[i] + s[i+h]; others are ignored
+      }
+      q[v] = s;
+    }
+  }
+}
+
+// Levels h >= kDotTile of the final halving sum for K = m / kDotTile values per
+// thread (indices t + k * kDotTile): a halving sum over k, kept in registers.
+template <int K, int NV>
+__device__ __forceinline__ void fold_strided(const double* const (&part)[NV], double (&q)[NV]) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double a[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) a[k] = __ldcg(part[v] + t + k * kDotTile);
+#pragma unroll
+    for (int h = K / 2; h >= 1; h >>= 1) {
+#pragma unroll
+      for (int k = 0; k < h; ++k) a[k] = a[k] + a[k + h];
+    }
+    q[v] = a[0];
+  }
+}
+
+// Same for larger K: the partial sums are updated in place in global memory
+// (only the block that owns the final reduction runs this).
+template <int NV>
+__device__ __forceinline__ void fold_strided_global(const double* const (&part)[NV], int64_t K, double (&q)[NV]) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double* p = const_cast<double*>(part[v]);
+    for (int64_t h = K / 2; h >= 1; h >>= 1)
+      for (int64_t k = 0; k < h; ++k)
+        p[t + k * kDotTile] = __ldcg(p + t + k * kDotTile) + __ldcg(p + t + (k + h) * kDotTile);
+    q[v] = __ldcg(p + t);
+  }
+}
+
+// Final fixed-order reduction over `m` (power of two) tile partials held in
+// global memory, by a kDotTile-thread block: halving sums from h = m/2 down to
+// 1. Levels with h >= kDotTile combine indices of equal residue mod kDotTile,
+// so each thread finishes them alone; the rest use shared memory. For
+// m < kDotTile the partials are padded with zeros to kDotTile: the extra
+// levels then add zeros and leave the sums unchanged. Result in thread 0.
+template <int NV>
+__device__ __forceinline__ void final_halving_sum(const double* const (&part)[NV], int64_t m,
+                                                  double (&out)[NV], double (*buf)[kDotTile]) {
+  const int t = threadIdx.x;
+  double q[NV];
+  if (m >= kDotTile) {
+    switch (m / kDotTile) {
+      case 1: fold_strided<1, NV>(part, q); break;
+      case 2: fold_strided<2, NV>(part, q); break;
+      case 4: fold_strided<4, NV>(part, q); break;
+      case 8: fold_strided<8, NV>(part, q); break;
+      case 16: fold_strided<16, NV>(part, q); break;
+      case 32: fold_strided<32, NV>(part, q); break;
+      case 64: fold_strided<64, NV>(part, q); break;
+      default: fold_strided_global<NV>(part, m / kDotTile, q); break;
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = t < m ? __ldcg(part[v] + t) : 0.0;
+  }
+  tile_halving_sum<NV>(q, buf);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[v] = q[v];
+}
+
+}  // namespace ilu0dd

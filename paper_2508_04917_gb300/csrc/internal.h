@@ -1,0 +1,157 @@
+// Internal layout shared by the host setup (setup.cpp), the kernels and the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ilu0dd.h"
+
+namespace ilu0dd {
+
+// ---------------------------------------------------------------------------
+// Fused-apply factor stream.
+//
+// Every subdomain owns one contiguous byte range ("its stream"), read in order
+// by its thread block through a ring of bulk copies. The stream is a sequence
+// of piece records. A piece is a set of rows of one level of the subdomain's L
+// DAG (kind 0) or U DAG (kind 1); rows of one piece are independent, pieces
+// are separated by a block barrier. Rows with no strictly-lower block (L level
+// 0) need no work in the L sweep and appear in no L piece.
+//
+// Inside a record the rows are sorted by block count, longest first, and the
+// blocks are stored slot-major ("jagged diagonal" order): slot s holds the
+// s-th block (ascending column) of the first cnt[s] rows. All arrays are
+// structure-of-arrays so consecutive threads read consecutive addresses.
+//
+//   u16 cnt[w]                 rows having more than s blocks, s = 0..w-1
+//   u16 rows[n]                local row index (0 .. nrows-1 of the subdomain)
+//   u16 cols[nb]               slot-major local column of each block
+//   pad to 16
+//   T   invD[9][n]             (kind 1 only) D^-1 = U_ii^-1, entry-major
+//   T   vals[...]              per slot s: 9 entry arrays of cnt[s] values
+//   pad to 16
+// T is the factor storage type (double, float or bf16).
+// ---------------------------------------------------------------------------
+struct PieceDesc {          // 16 bytes, one per piece, device array
+  uint32_t off;             // record start, bytes from the subdomain stream start
+  uint32_t meta;            // n | (w << 16) | (kind << 24)
+  uint32_t nb;              // blocks in the record
+  uint32_t voff;            // first value array (invD or vals), bytes from record start
+};
+
+struct CtaDesc {            // 32 bytes, one per subdomain
+  int64_t stream_off;       // bytes from the stream base, 128-aligned
+  int32_t stream_len;       // bytes, multiple of 16
+  int32_t row0;             // first reordered row
+  int32_t nrows;            // rows of the subdomain
+  int32_t piece0;           // first PieceDesc
+  int32_t npieces;
+  int32_t pad;
+};
+
+// Device-resident BiCGSTAB scalars (Algorithm 1). Written by the last block of
+// the reduction kernels, read by every kernel of the next step.
+struct SolverScalars {
+  double rho, alpha, omega, beta;
+  double bb;                // ||b||^2
+  double rv, ts, tt, rr, rhr;
+  double rel;               // ||r|| / ||b|| of the last update
+  double rel_true;          // ||b - A x|| / ||b|| of the last true-residual check
+  double rtol;
+  int32_t iter;             // completed iterations
+  int32_t done;             // 1 = stop launching work (converged or failed)
+  int32_t status;           // ILU0DD_OK / BREAKDOWN / NOT_CONVERGED / NONFINITE
+  int32_t maxit;
+  int32_t converged;        // 1 = recurrence residual reached rtol
+  int32_t pad[3];
+};
+
+// Vectors of the solver state in the workspace (3N doubles each).
+enum VecId : int { kVecB = 0, kVecX, kVecR, kVecRh, kVecP, kVecV, kVecS, kVecT, kVecPh, kVecSh, kNumVec };
+
+// Reduction counters (one per kernel kind, reset by the last block).
+enum CounterId : int { kCntInit = 0, kCntSpmvV, kCntSpmvT, kCntUpdate, kCntResid, kCntDot, kNumCounters };
+
+// Sliced-ELL copy of the full reordered matrix for the SpMV: slices of 32
+// rows, slot-major, entry-major within a slot; padding entries have value 0
+// and the row's own column.
+constexpr int kSlice = 32;
+// Block rows per tile of the fixed dot order.
+constexpr int kDotTile = 256;
+// Maximum apply ring slots.
+constexpr int kMaxSlots = 16;
+// Maximum apply threads per block.
+constexpr int kMaxApplyThreads = 512;
+
+enum ApplyMode : int {
+  kModePlain = 0,   // smem <- r
+  kModeP = 1,       // p <- r + beta (p - omega v); smem <- p
+  kModeS = 2,       // s <- r - alpha v;            smem <- s
+};
+
+// Host-side plan: everything derived from the pattern (no values).
+struct Plan {
+  int32_t N = 0;
+  int64_t nnzb = 0;
+  ilu0dd_geom geom{};
+  ilu0dd_opts opts{};
+  int32_t nsub = 0;
+  std::vector<int32_t> part_id, perm, iperm, part_ptr;
+  // reordered full matrix
+  std::vector<int32_t> ap_rp, ap_col;
+  std::vector<int64_t> ap_src;      // source block of each reordered block
+  // dropped matrix (pattern, and position of each kept block in ap)
+  std::vector<int32_t> dd_rp, dd_col;
+  std::vector<int64_t> dd_ap;       // index into ap blocks
+  int64_t nL = 0, nU = 0;
+  std::vector<int32_t> lev_l, lev_u;
+  int32_t max_levels = 0;
+  // apply packing
+  int threads = 0;
+  int ring_bytes = 0, chunk_bytes = 0, nslot = 0;
+  int vec_elem = 8, factor_elem = 8;
+  int rmax = 0, max_pieces = 0;
+  size_t smem_bytes = 0;
+  int64_t n_pieces = 0;
+  std::vector<CtaDesc> cta;
+  std::vector<PieceDesc> pieces;
+  std::vector<std::vector<int32_t>> piece_rows;   // local rows of each piece, stream order
+  std::vector<int64_t> piece_record_bytes;
+  int64_t stream_bytes = 0;
+  // SpMV packing
+  int64_t nslices = 0, sell_slots = 0;            // sell_slots = sum of slice widths
+  std::vector<int32_t> slice_off;                 // [nslices+1] prefix of widths
+  // workspace layout (byte offsets)
+  struct Layout {
+    size_t stream, cta, pieces, sell_off, sell_col, sell_val, perm, iperm;
+    size_t vec[kNumVec];
+    size_t partials, counters, scal, hist, err, total;
+  } lay{};
+  int64_t ntiles = 0, ntiles_pow2 = 0;
+  int64_t apply_bytes = 0, spmv_bytes = 0;
+};
+
+int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, int max_smem,
+              Plan* plan, std::string* why);
+
+// Numeric setup (host, FP64): block ILU0 of the dropped matrix per subdomain
+// and the ILDU0 post-processing. F is indexed like plan.dd_col: L_ij at
+// strictly-lower positions, U~_ij = D_i^-1 U_ij at strictly-upper positions,
+// zero at the diagonal; invD holds D_i^-1 = U_ii^-1 per row. `aval` is the
+// caller's matrix in natural order (reordered through plan.ap_src).
+int factor_ildu0(const Plan& plan, const double* aval, std::vector<double>* F,
+                 std::vector<double>* invD, int32_t* bad_row);
+
+// Pack the factor stream (bytes) in the plan's precision.
+void pack_stream(const Plan& plan, const std::vector<double>& F, const std::vector<double>& invD,
+                 std::vector<uint8_t>* stream);
+
+// Pack the sliced-ELL SpMV arrays of the reordered full matrix.
+void pack_sell(const Plan& plan, const double* aval, std::vector<int32_t>* cols,
+               std::vector<double>* vals);
+
+double wall_seconds();
+
+}  // namespace ilu0dd

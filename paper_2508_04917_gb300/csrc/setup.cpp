@@ -1,0 +1,567 @@
+// Host side of ilu0_dd_setup: decomposition (Algorithm 2, Algorithm 3, the drop
+// of Section 3.2), level sets (Algorithm 5), block ILU0 / ILDU0 (Algorithm 7)
+// and packing of the device layouts. FP64 throughout; compiled without FMA
+// contraction so x86-64 and aarch64 hosts produce the same bits.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <thread>
+
+#include "internal.h"
+
+namespace ilu0dd {
+
+double wall_seconds() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+namespace {
+
+inline int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// Run f(i) for i in [0, n) on the host's hardware threads.
+template <typename F>
+void parallel_for(int64_t n, F&& f) {
+  unsigned hw = std::thread::hardware_concurrency();
+  int64_t nt = std::max<int64_t>(1, std::min<int64_t>(hw ? hw : 1, n));
+  if (nt <= 1) {
+    for (int64_t i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int64_t t = 0; t < nt; ++t)
+    th.emplace_back([&, t] {
+      for (int64_t i = n * t / nt; i < n * (t + 1) / nt; ++i) f(i);
+    });
+  for (auto& x : th) x.join();
+}
+
+// Bytes of one piece record (see internal.h).
+int64_t record_bytes(int n, int w, int64_t nb, int kind, int felem, int64_t* voff) {
+  int64_t head = 2 * (int64_t)w + 2 * (int64_t)n + 2 * nb;
+  int64_t v = align_up(head, 16);
+  if (voff) *voff = v;
+  int64_t vals = (kind ? 9 * (int64_t)n : 0) + 9 * nb;
+  return align_up(v + vals * felem, 16);
+}
+
+// 3x3 inverse by Gauss-Jordan elimination with partial pivoting.
+bool inverse3(const double* M, double* X) {
+  double a[3][6];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 6; ++c) a[r][c] = c < 3 ? M[3 * r + c] : (c - 3 == r ? 1.0 : 0.0);
+  for (int c = 0; c < 3; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < 3; ++r)
+      if (std::fabs(a[r][c]) > std::fabs(a[piv][c])) piv = r;
+    double pv = a[piv][c];
+    if (!(std::fabs(pv) > 0.0) || !std::isfinite(pv)) return false;
+    if (piv != c)
+      for (int q = 0; q < 6; ++q) std::swap(a[c][q], a[piv][q]);
+    double inv = 1.0 / a[c][c];
+    for (int q = 0; q < 6; ++q) a[c][q] *= inv;
+    for (int r = 0; r < 3; ++r) {
+      if (r == c) continue;
+      double m = a[r][c];
+      if (m == 0.0) continue;
+      for (int q = 0; q < 6; ++q) a[r][q] -= m * a[c][q];
+    }
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      X[3 * r + c] = a[r][c + 3];
+      if (!std::isfinite(X[3 * r + c])) return false;
+    }
+  return true;
+}
+
+// C = A * B (3x3).
+inline void mul3(const double* A, const double* B, double* C) {
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k) s += A[3 * r + k] * B[3 * k + c];
+      C[3 * r + c] = s;
+    }
+}
+
+uint16_t to_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x7FFFFFu)) return (uint16_t)((u >> 16) | 0x40);
+  u += 0x7FFFu + ((u >> 16) & 1u);  // round to nearest even
+  return (uint16_t)(u >> 16);
+}
+
+void put_factor(uint8_t* dst, int felem, double v) {
+  if (felem == 8) {
+    std::memcpy(dst, &v, 8);
+  } else if (felem == 4) {
+    float f = (float)v;
+    std::memcpy(dst, &f, 4);
+  } else {
+    uint16_t h = to_bf16((float)v);
+    std::memcpy(dst, &h, 2);
+  }
+}
+
+}  // namespace
+
+int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, int max_smem,
+              Plan* P, std::string* why) {
+  if (!A || !g || !o || !P) return ILU0DD_ERR_INVALID;
+  if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0 || g->sx <= 0 || g->sy <= 0 || g->sz <= 0) {
+    *why = "grid and subdomain sides must be positive";
+    return ILU0DD_ERR_INVALID;
+  }
+  int64_t N64 = (int64_t)g->nx * g->ny * g->nz;
+  if (N64 != A->n_brows || N64 >= (1ll << 31)) {
+    *why = "n_brows must equal nx*ny*nz (< 2^31)";
+    return ILU0DD_ERR_INVALID;
+  }
+  if (!A->row_ptr || !A->col_idx || (A->nnzb > 0 && !A->val)) {
+    *why = "null matrix array";
+    return ILU0DD_ERR_INVALID;
+  }
+  const int32_t N = (int32_t)N64;
+  const int32_t* rp = A->row_ptr;
+  const int32_t* ci = A->col_idx;
+  if (rp[0] != 0 || rp[N] != A->nnzb) {
+    *why = "row_ptr[0] must be 0 and row_ptr[N] must equal nnzb";
+    return ILU0DD_ERR_INVALID;
+  }
+  for (int32_t i = 0; i < N; ++i) {
+    if (rp[i + 1] < rp[i]) { *why = "row_ptr not monotone"; return ILU0DD_ERR_INVALID; }
+    bool diag = false;
+    for (int64_t q = rp[i]; q < rp[i + 1]; ++q) {
+      if (ci[q] < 0 || ci[q] >= N) { *why = "column out of range"; return ILU0DD_ERR_INVALID; }
+      if (q > rp[i] && ci[q] <= ci[q - 1]) { *why = "columns not strictly ascending"; return ILU0DD_ERR_INVALID; }
+      diag |= ci[q] == i;
+    }
+    if (!diag) { *why = "missing diagonal block in row " + std::to_string(i); return ILU0DD_ERR_INVALID; }
+  }
+  Plan& p = *P;
+  p = Plan();
+  p.N = N;
+  p.nnzb = A->nnzb;
+  p.geom = *g;
+  p.opts = *o;
+
+  // ---- Algorithm 2: labels from geometric cuts (ceil-division at the edges)
+  const int bx = ceil_div(g->nx, g->sx), by = ceil_div(g->ny, g->sy), bz = ceil_div(g->nz, g->sz);
+  p.nsub = bx * by * bz;
+  p.part_id.resize(N);
+  for (int k = 0; k < g->nz; ++k)
+    for (int j = 0; j < g->ny; ++j)
+      for (int i = 0; i < g->nx; ++i)
+        p.part_id[(int64_t)i + (int64_t)g->nx * (j + (int64_t)g->ny * k)] =
+            i / g->sx + bx * (j / g->sy + by * (k / g->sz));
+
+  // ---- Section 3.1: stable grouping by label (perm[new] = old)
+  p.part_ptr.assign(p.nsub + 1, 0);
+  for (int32_t r = 0; r < N; ++r) p.part_ptr[p.part_id[r] + 1]++;
+  for (int s = 0; s < p.nsub; ++s) p.part_ptr[s + 1] += p.part_ptr[s];
+  {
+    std::vector<int32_t> next(p.part_ptr.begin(), p.part_ptr.end() - 1);
+    p.perm.resize(N);
+    p.iperm.resize(N);
+    for (int32_t r = 0; r < N; ++r) {
+      int32_t nr = next[p.part_id[r]]++;
+      p.perm[nr] = r;
+      p.iperm[r] = nr;
+    }
+  }
+
+  // ---- Algorithm 3 on BSR: reorder rows and columns, sort each row
+  p.ap_rp.resize(N + 1);
+  p.ap_rp[0] = 0;
+  for (int32_t i = 0; i < N; ++i) p.ap_rp[i + 1] = p.ap_rp[i] + (rp[p.perm[i] + 1] - rp[p.perm[i]]);
+  p.ap_col.resize(A->nnzb);
+  p.ap_src.resize(A->nnzb);
+  parallel_for(N, [&](int64_t i) {
+    int32_t old = p.perm[i];
+    int64_t base = p.ap_rp[i], len = rp[old + 1] - rp[old];
+    std::pair<int32_t, int64_t> tmp[64];
+    std::vector<std::pair<int32_t, int64_t>> big;
+    auto* e = tmp;
+    if (len > 64) { big.resize(len); e = big.data(); }
+    for (int64_t q = 0; q < len; ++q) e[q] = {p.iperm[ci[rp[old] + q]], rp[old] + q};
+    std::sort(e, e + len);
+    for (int64_t q = 0; q < len; ++q) {
+      p.ap_col[base + q] = e[q].first;
+      p.ap_src[base + q] = e[q].second;
+    }
+  });
+
+  // ---- Section 3.2: drop blocks whose row and column lie in different subdomains
+  std::vector<int32_t> label(N);
+  for (int32_t i = 0; i < N; ++i) label[i] = p.part_id[p.perm[i]];
+  p.dd_rp.assign(N + 1, 0);
+  for (int32_t i = 0; i < N; ++i) {
+    int32_t c = 0;
+    for (int64_t q = p.ap_rp[i]; q < p.ap_rp[i + 1]; ++q) c += label[p.ap_col[q]] == label[i];
+    p.dd_rp[i + 1] = p.dd_rp[i] + c;
+  }
+  int64_t kept = p.dd_rp[N];
+  p.dd_col.resize(kept);
+  p.dd_ap.resize(kept);
+  parallel_for(N, [&](int64_t i) {
+    int64_t d = p.dd_rp[i];
+    for (int64_t q = p.ap_rp[i]; q < p.ap_rp[i + 1]; ++q)
+      if (label[p.ap_col[q]] == label[i]) {
+        p.dd_col[d] = p.ap_col[q];
+        p.dd_ap[d++] = q;
+      }
+  });
+  for (int32_t i = 0; i < N; ++i)
+    for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1]; ++q) {
+      p.nL += p.dd_col[q] < i;
+      p.nU += p.dd_col[q] > i;
+    }
+
+  // ---- Algorithm 5 (level sets of each subdomain's L and U DAG)
+  p.lev_l.assign(N, 0);
+  p.lev_u.assign(N, 0);
+  std::vector<int32_t> nlev_l(p.nsub), nlev_u(p.nsub);
+  parallel_for(p.nsub, [&](int64_t s) {
+    int32_t r0 = p.part_ptr[s], r1 = p.part_ptr[s + 1], ml = 0, mu = 0;
+    for (int32_t i = r0; i < r1; ++i) {
+      int32_t l = 0;
+      for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1] && p.dd_col[q] < i; ++q)
+        l = std::max(l, p.lev_l[p.dd_col[q]] + 1);
+      p.lev_l[i] = l;
+      ml = std::max(ml, l + 1);
+    }
+    for (int32_t i = r1 - 1; i >= r0; --i) {
+      int32_t l = 0;
+      for (int64_t q = p.dd_rp[i + 1] - 1; q >= p.dd_rp[i] && p.dd_col[q] > i; --q)
+        l = std::max(l, p.lev_u[p.dd_col[q]] + 1);
+      p.lev_u[i] = l;
+      mu = std::max(mu, l + 1);
+    }
+    nlev_l[s] = r1 > r0 ? ml : 0;
+    nlev_u[s] = r1 > r0 ? mu : 0;
+  });
+
+  // ---- apply configuration
+  const int fp = o->factor_prec;
+  if (fp != ILU0DD_F64 && fp != ILU0DD_F32 && fp != ILU0DD_BF16) {
+    *why = "factor_prec must be ILU0DD_F64, ILU0DD_F32 or ILU0DD_BF16";
+    return ILU0DD_ERR_INVALID;
+  }
+  p.factor_elem = fp == ILU0DD_F64 ? 8 : fp == ILU0DD_F32 ? 4 : 2;
+  p.vec_elem = fp == ILU0DD_F64 ? 8 : 4;
+  for (int s = 0; s < p.nsub; ++s) p.rmax = std::max(p.rmax, p.part_ptr[s + 1] - p.part_ptr[s]);
+  if (p.rmax > 65535) {
+    *why = "a subdomain has more than 65535 rows";
+    return ILU0DD_ERR_SMEM;
+  }
+  // widest level decides the default block size
+  int widest = 1;
+  {
+    std::vector<int32_t> cnt;
+    for (int s = 0; s < p.nsub; ++s) {
+      int32_t r0 = p.part_ptr[s], r1 = p.part_ptr[s + 1];
+      int32_t nl = std::max(nlev_l[s], nlev_u[s]);
+      cnt.assign(2 * (size_t)nl, 0);
+      for (int32_t i = r0; i < r1; ++i) {
+        cnt[p.lev_l[i]]++;
+        cnt[nl + p.lev_u[i]]++;
+      }
+      for (int32_t c : cnt) widest = std::max(widest, c);
+      p.max_levels = std::max(p.max_levels, nlev_l[s] + nlev_u[s]);
+    }
+  }
+  p.threads = o->threads_per_cta > 0 ? o->threads_per_cta : std::min(kMaxApplyThreads, (int)align_up(widest, 32));
+  if (p.threads % 32 || p.threads > kMaxApplyThreads || p.threads < 32) {
+    *why = "threads_per_cta must be a multiple of 32 in [32, 512]";
+    return ILU0DD_ERR_INVALID;
+  }
+  p.ring_bytes = o->ring_bytes > 0 ? o->ring_bytes : 32768;
+  if (p.ring_bytes < 2048 || (p.ring_bytes & (p.ring_bytes - 1)) || p.ring_bytes > (1 << 20)) {
+    *why = "ring_bytes must be a power of two >= 2048";
+    return ILU0DD_ERR_INVALID;
+  }
+  p.nslot = 8;
+  p.chunk_bytes = p.ring_bytes / p.nslot;
+  const int64_t cap = (int64_t)(p.nslot - 1) * p.chunk_bytes;
+
+  // ---- pieces: per subdomain, L levels 1.. then U levels 0.., rows of a level
+  // sorted by block count (longest first), split by thread count and ring size
+  p.cta.resize(p.nsub);
+  std::vector<std::vector<std::vector<int32_t>>> sub_pieces(p.nsub);
+  std::vector<std::vector<int64_t>> sub_bytes(p.nsub);
+  std::vector<std::vector<PieceDesc>> sub_desc(p.nsub);
+  std::vector<int> sub_fail(p.nsub, 0);
+  parallel_for(p.nsub, [&](int64_t s) {
+    int32_t r0 = p.part_ptr[s], r1 = p.part_ptr[s + 1];
+    auto nblk = [&](int32_t i, int kind) {
+      int32_t c = 0;
+      for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1]; ++q)
+        c += kind ? (p.dd_col[q] > i) : (p.dd_col[q] < i);
+      return c;
+    };
+    uint32_t off = 0;
+    for (int kind = 0; kind < 2; ++kind) {
+      int32_t nl = kind ? nlev_u[s] : nlev_l[s];
+      std::vector<std::vector<int32_t>> by_level(nl);
+      for (int32_t i = r0; i < r1; ++i) {
+        int32_t l = kind ? p.lev_u[i] : p.lev_l[i];
+        if (kind == 0 && l == 0) continue;
+        by_level[l].push_back(i);
+      }
+      for (auto& rows : by_level) {
+        if (rows.empty()) continue;
+        std::vector<std::pair<int32_t, int32_t>> key;  // (-blocks, row)
+        for (int32_t i : rows) key.push_back({-nblk(i, kind), i});
+        std::sort(key.begin(), key.end());
+        size_t a = 0;
+        while (a < key.size()) {
+          // grow the piece while it fits the block and the ring
+          size_t b = a;
+          int64_t nb = 0;
+          while (b < key.size() && (int)(b - a) < p.threads) {
+            int w = -key[a].first;
+            int64_t bytes = record_bytes((int)(b - a + 1), w, nb - key[b].first, kind, p.factor_elem, nullptr);
+            if (bytes > cap && b > a) break;
+            nb += -key[b].first;
+            ++b;
+          }
+          int n = (int)(b - a), w = -key[a].first;
+          int64_t voff;
+          int64_t bytes = record_bytes(n, w, nb, kind, p.factor_elem, &voff);
+          if (bytes > cap || w > 255) sub_fail[s] = 1;
+          std::vector<int32_t> pr;
+          for (size_t t = a; t < b; ++t) pr.push_back(key[t].second - r0);
+          PieceDesc d;
+          d.off = off;
+          d.meta = (uint32_t)n | ((uint32_t)w << 16) | ((uint32_t)kind << 24);
+          d.nb = (uint32_t)nb;
+          d.voff = (uint32_t)voff;
+          sub_desc[s].push_back(d);
+          sub_pieces[s].push_back(std::move(pr));
+          sub_bytes[s].push_back(bytes);
+          off += (uint32_t)bytes;
+          a = b;
+        }
+      }
+    }
+  });
+  for (int s = 0; s < p.nsub; ++s)
+    if (sub_fail[s]) {
+      *why = "a single row's blocks exceed the apply staging ring; raise ring_bytes";
+      return ILU0DD_ERR_SMEM;
+    }
+  int64_t soff = 0;
+  for (int s = 0; s < p.nsub; ++s) {
+    CtaDesc& c = p.cta[s];
+    int64_t len = 0;
+    for (int64_t b : sub_bytes[s]) len += b;
+    if (len >= (1ll << 31)) {
+      *why = "subdomain stream exceeds 2 GiB";
+      return ILU0DD_ERR_INVALID;
+    }
+    c.stream_off = soff;
+    c.stream_len = (int32_t)len;
+    c.row0 = p.part_ptr[s];
+    c.nrows = p.part_ptr[s + 1] - p.part_ptr[s];
+    c.piece0 = (int32_t)p.pieces.size();
+    c.npieces = (int32_t)sub_desc[s].size();
+    c.pad = 0;
+    p.max_pieces = std::max(p.max_pieces, c.npieces);
+    for (auto& d : sub_desc[s]) p.pieces.push_back(d);
+    for (auto& r : sub_pieces[s]) p.piece_rows.push_back(std::move(r));
+    for (auto b : sub_bytes[s]) p.piece_record_bytes.push_back(b);
+    soff = align_up(soff + len, 128);
+  }
+  p.stream_bytes = soff;
+  p.n_pieces = (int64_t)p.pieces.size();
+  p.smem_bytes = (size_t)align_up(3ll * p.rmax * p.vec_elem, 128) + (size_t)p.ring_bytes;
+  if ((int64_t)p.smem_bytes > (int64_t)max_smem) {
+    *why = "subdomain vector (" + std::to_string(3ll * p.rmax * p.vec_elem) + " B) plus staging ring (" +
+           std::to_string(p.ring_bytes) + " B) exceeds the " + std::to_string(max_smem) +
+           " B of shared memory per block";
+    return ILU0DD_ERR_SMEM;
+  }
+
+  // ---- sliced ELL for the SpMV
+  p.nslices = (N + kSlice - 1) / kSlice;
+  p.slice_off.assign(p.nslices + 1, 0);
+  for (int64_t k = 0; k < p.nslices; ++k) {
+    int32_t w = 0;
+    for (int64_t r = k * kSlice; r < std::min<int64_t>(N, (k + 1) * kSlice); ++r)
+      w = std::max(w, p.ap_rp[r + 1] - p.ap_rp[r]);
+    p.slice_off[k + 1] = p.slice_off[k] + w;
+  }
+  p.sell_slots = p.slice_off[p.nslices];
+
+  // ---- dot tiles
+  p.ntiles = (N + kDotTile - 1) / kDotTile;
+  p.ntiles_pow2 = 1;
+  while (p.ntiles_pow2 < p.ntiles) p.ntiles_pow2 *= 2;
+
+  // ---- workspace layout
+  size_t cur = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = cur;
+    cur = (size_t)align_up((int64_t)(cur + bytes), 256);
+    return at;
+  };
+  Plan::Layout& L = p.lay;
+  L.stream = take((size_t)p.stream_bytes);
+  L.cta = take(sizeof(CtaDesc) * (size_t)p.nsub);
+  L.pieces = take(sizeof(PieceDesc) * (size_t)std::max<int64_t>(1, p.n_pieces));
+  L.sell_off = take(sizeof(int32_t) * (size_t)(p.nslices + 1));
+  L.sell_col = take(sizeof(int32_t) * (size_t)p.sell_slots * kSlice);
+  L.sell_val = take(sizeof(double) * 9 * (size_t)p.sell_slots * kSlice);
+  L.perm = take(sizeof(int32_t) * (size_t)N);
+  L.iperm = take(sizeof(int32_t) * (size_t)N);
+  for (int v = 0; v < kNumVec; ++v) L.vec[v] = take(sizeof(double) * 3 * (size_t)N);
+  L.partials = take(sizeof(double) * 5 * (size_t)p.ntiles_pow2);
+  L.counters = take(sizeof(uint32_t) * 16);
+  L.scal = take(sizeof(SolverScalars));
+  int32_t maxit = o->maxit > 0 ? o->maxit : 10000;
+  L.hist = take(sizeof(double) * (size_t)(maxit + 2));
+  L.err = take(sizeof(int32_t) * 4);
+  L.total = cur;
+
+  // ---- algorithmic bytes (values + int32 column indices + row pointers of L
+  // and U + FP64 r in and z out; SpMV: values + columns + row pointers + x, y)
+  p.apply_bytes = 9ll * p.factor_elem * (p.nL + p.nU + N) + 4 * (p.nL + p.nU) + 8ll * (N + 1) + 48ll * N;
+  p.spmv_bytes = 76ll * p.nnzb + 4ll * (N + 1) + 48ll * N;
+  return ILU0DD_OK;
+}
+
+int factor_ildu0(const Plan& p, const double* aval, std::vector<double>* Fp, std::vector<double>* invDp,
+                 int32_t* bad_row) {
+  std::vector<double>& F = *Fp;
+  std::vector<double>& invD = *invDp;
+  const int64_t kept = p.dd_rp[p.N];
+  F.assign(9 * (size_t)kept, 0.0);
+  invD.assign(9 * (size_t)p.N, 0.0);
+  std::vector<int32_t> fail(p.nsub, -1);
+  parallel_for(p.nsub, [&](int64_t s) {
+    const int32_t r0 = p.part_ptr[s], r1 = p.part_ptr[s + 1];
+    const int64_t q0 = p.dd_rp[r0], q1 = p.dd_rp[r1];
+    // W: working rows of the subdomain (Algorithm 7, U <- A)
+    std::vector<double> W(9 * (size_t)(q1 - q0));
+    for (int64_t q = q0; q < q1; ++q)
+      std::memcpy(&W[9 * (q - q0)], aval + 9 * p.ap_src[p.dd_ap[q]], 9 * sizeof(double));
+    std::vector<int64_t> pos(r1 - r0, -1);
+    std::vector<int64_t> diag(r1 - r0, -1);
+    double Lij[9], prod[9];
+    for (int32_t i = r0; i < r1; ++i) {
+      for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1]; ++q) {
+        pos[p.dd_col[q] - r0] = q - q0;
+        if (p.dd_col[q] == i) diag[i - r0] = q - q0;
+      }
+      if (diag[i - r0] < 0) { fail[s] = i; return; }
+      for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1] && p.dd_col[q] < i; ++q) {
+        int32_t j = p.dd_col[q];
+        // L_ij = W_ij U_jj^-1 (U_jj^-1 is invD of row j, already final)
+        mul3(&W[9 * (q - q0)], &invD[9 * (size_t)j], Lij);
+        std::memcpy(&W[9 * (q - q0)], Lij, sizeof Lij);
+        for (int64_t t = p.dd_rp[j + 1] - 1; t >= p.dd_rp[j] && p.dd_col[t] > j; --t) {
+          int64_t at = pos[p.dd_col[t] - r0];
+          if (at < 0) continue;
+          mul3(Lij, &W[9 * (t - q0)], prod);
+          for (int e = 0; e < 9; ++e) W[9 * at + e] -= prod[e];
+        }
+      }
+      if (!inverse3(&W[9 * diag[i - r0]], &invD[9 * (size_t)i])) { fail[s] = i; return; }
+      for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1]; ++q) pos[p.dd_col[q] - r0] = -1;
+    }
+    // ILDU0 (Algorithm 7, lower half, read as scaling the strictly-upper blocks):
+    // F <- L at lower positions, U~_ik = D_i^-1 U_ik at upper positions.
+    for (int32_t i = r0; i < r1; ++i)
+      for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1]; ++q) {
+        double* dst = &F[9 * (size_t)q];
+        if (p.dd_col[q] < i) {
+          std::memcpy(dst, &W[9 * (q - q0)], 9 * sizeof(double));
+        } else if (p.dd_col[q] > i) {
+          mul3(&invD[9 * (size_t)i], &W[9 * (q - q0)], dst);
+        }
+      }
+  });
+  for (int s = 0; s < p.nsub; ++s)
+    if (fail[s] >= 0) {
+      if (bad_row) *bad_row = fail[s];
+      return ILU0DD_ERR_ZERO_PIVOT;
+    }
+  return ILU0DD_OK;
+}
+
+void pack_stream(const Plan& p, const std::vector<double>& F, const std::vector<double>& invD,
+                 std::vector<uint8_t>* out) {
+  std::vector<uint8_t>& S = *out;
+  S.assign((size_t)p.stream_bytes, 0);
+  const int fe = p.factor_elem;
+  parallel_for(p.nsub, [&](int64_t s) {
+    const CtaDesc& c = p.cta[s];
+    for (int32_t k = 0; k < c.npieces; ++k) {
+      const PieceDesc& d = p.pieces[c.piece0 + k];
+      const std::vector<int32_t>& rows = p.piece_rows[c.piece0 + k];
+      const int n = (int)(d.meta & 0xFFFF), w = (int)((d.meta >> 16) & 0xFF), kind = (int)(d.meta >> 24);
+      uint8_t* rec = S.data() + c.stream_off + d.off;
+      // blocks of each row (ascending column), strictly lower (kind 0) or upper (kind 1)
+      std::vector<std::vector<int64_t>> blk(n);
+      for (int t = 0; t < n; ++t) {
+        int32_t i = c.row0 + rows[t];
+        for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1]; ++q)
+          if (kind ? p.dd_col[q] > i : p.dd_col[q] < i) blk[t].push_back(q);
+      }
+      std::vector<uint16_t> cnt(w, 0);
+      for (int slot = 0; slot < w; ++slot)
+        for (int t = 0; t < n; ++t) cnt[slot] += (int)blk[t].size() > slot;
+      uint16_t* h = reinterpret_cast<uint16_t*>(rec);
+      for (int slot = 0; slot < w; ++slot) h[slot] = cnt[slot];
+      for (int t = 0; t < n; ++t) h[w + t] = (uint16_t)rows[t];
+      int64_t cpos = w + n;
+      for (int slot = 0; slot < w; ++slot)
+        for (int t = 0; t < cnt[slot]; ++t) h[cpos++] = (uint16_t)(p.dd_col[blk[t][slot]] - c.row0);
+      uint8_t* v = rec + d.voff;
+      if (kind) {
+        for (int e = 0; e < 9; ++e)
+          for (int t = 0; t < n; ++t)
+            put_factor(v + ((int64_t)e * n + t) * fe, fe, invD[9 * (size_t)(c.row0 + rows[t]) + e]);
+        v += 9ll * n * fe;
+      }
+      for (int slot = 0; slot < w; ++slot) {
+        for (int e = 0; e < 9; ++e)
+          for (int t = 0; t < cnt[slot]; ++t)
+            put_factor(v + ((int64_t)e * cnt[slot] + t) * fe, fe, F[9 * (size_t)blk[t][slot] + e]);
+        v += 9ll * cnt[slot] * fe;
+      }
+    }
+  });
+}
+
+void pack_sell(const Plan& p, const double* aval, std::vector<int32_t>* cols, std::vector<double>* vals) {
+  cols->assign((size_t)p.sell_slots * kSlice, 0);
+  vals->assign((size_t)p.sell_slots * kSlice * 9, 0.0);
+  parallel_for(p.nslices, [&](int64_t k) {
+    int64_t so = p.slice_off[k];
+    int32_t w = p.slice_off[k + 1] - p.slice_off[k];
+    for (int lane = 0; lane < kSlice; ++lane) {
+      int64_t r = k * kSlice + lane;
+      for (int32_t s = 0; s < w; ++s) {
+        int64_t slot = so + s;
+        int32_t col = r < p.N ? (int32_t)r : 0;
+        double blk[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (r < p.N && s < p.ap_rp[r + 1] - p.ap_rp[r]) {
+          int64_t q = p.ap_rp[r] + s;
+          col = p.ap_col[q];
+          std::memcpy(blk, aval + 9 * p.ap_src[q], sizeof blk);
+        }
+        (*cols)[(size_t)slot * kSlice + lane] = col;
+        for (int e = 0; e < 9; ++e) (*vals)[((size_t)slot * 9 + e) * kSlice + lane] = blk[e];
+      }
+    }
+  });
+}
+
+}  // namespace ilu0dd

@@ -1,0 +1,85 @@
+"""CPU tests of the C ABI library: it builds, loads, exports every declared symbol,
+and its host-side structural logic (workspace query, argument checks) behaves.
+
+No kernel is launched here; the structural query runs the host part of the
+setup only (Algorithm 2, Algorithm 3, the drop of Section 3.2, level sets).
+"""
+import ctypes
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_2508_04917_gb300 as g
+import synth
+
+
+def test_library_exports_every_declared_symbol():
+    lib = g.load()
+    names = g.declared_functions()
+    assert {"ilu0_dd_setup", "ilu0_dd_apply", "bicgstab_solve", "ilu0_dd_workspace_size"} <= set(names)
+    for name in names:
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", g.library_path()], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert set(names) <= exported
+
+
+def test_strerror_and_defaults():
+    assert g.strerror(0) == "ok"
+    assert "shared memory" in g.strerror(3)
+    o = g.default_opts()
+    assert o.factor_prec == g.F64 and o.maxit == 10000 and o.rtol == 1e-8 and o.use_graphs == 1
+
+
+def _sys(grid=(8, 8, 8)):
+    return synth.system(*grid, 3)
+
+
+def test_workspace_size_scales_with_precision():
+    s = _sys((16, 16, 16))
+    sizes = {p: g.workspace_size(s.row_ptr, s.col, s.val, (16, 16, 16), (8, 8, 4), factor_prec=p)
+             for p in ("f64", "f32", "bf16")}
+    assert sizes["f64"] > sizes["f32"] > sizes["bf16"] > 0
+
+
+def test_rejects_bad_patterns():
+    s = _sys()
+    col = s.col.copy()
+    col[[1, 2]] = col[[2, 1]]  # unsorted row 0
+    with pytest.raises(g.Ilu0DDError) as e:
+        g.workspace_size(s.row_ptr, col, s.val, (8, 8, 8), (4, 4, 4))
+    assert e.value.code == 1
+    # drop the diagonal block of row 0 (keep the pattern consistent)
+    rp = s.row_ptr.copy()
+    q = [q for q in range(rp[0], rp[1]) if s.col[q] == 0][0]
+    keep = np.ones(len(s.col), bool)
+    keep[q] = False
+    rp[1:] -= 1
+    with pytest.raises(g.Ilu0DDError) as e:
+        g.workspace_size(rp, s.col[keep], s.val[keep], (8, 8, 8), (4, 4, 4))
+    assert e.value.code == 1
+    with pytest.raises(g.Ilu0DDError) as e:
+        g.workspace_size(s.row_ptr, s.col, s.val, (8, 8, 9), (4, 4, 4))  # N mismatch
+    assert e.value.code == 1
+    with pytest.raises(g.Ilu0DDError) as e:
+        g.workspace_size(s.row_ptr, s.col, s.val, (8, 8, 8), (4, 4, 4), factor_prec=7)
+    assert e.value.code == 1
+    with pytest.raises(g.Ilu0DDError) as e:
+        g.workspace_size(s.row_ptr, s.col, s.val, (8, 8, 8), (4, 4, 4), threads_per_cta=48)
+    assert e.value.code == 1
+
+
+def test_subdomain_shared_memory_limit():
+    """Section 4 sizes subdomains so their vector fits in shared memory: 8192 FP64 block
+    rows (192 KiB) plus the 32 KiB staging ring fit the 227 KiB of sm_103a; one more
+    z-layer does not."""
+    grid = (16, 16, 33)
+    rp, col = synth.pattern(*grid)
+    val = np.zeros((len(col), 3, 3))
+    assert g.workspace_size(rp, col, val, grid, (16, 16, 32)) > 0
+    with pytest.raises(g.Ilu0DDError) as e:
+        g.workspace_size(rp, col, val, grid, (16, 16, 33))
+    assert e.value.code == 3
+    # FP32 factors keep an FP32 vector: twice the rows fit
+    assert g.workspace_size(rp, col, val, grid, (16, 16, 33), factor_prec="f32") > 0

@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Bars: integer arrays (labels, permutation, levels, patterns) bit-exact;
+SpMV and dot products bit-exact (same per-row order, same fixed reduction
+order on both sides); FP64 apply and FP64 solve outputs within a normwise
+relative error of 1e-12 (max_i |g_i - o_i| / max_i |o_i|); BiCGSTAB iteration
+counts identical.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import paper_2508_04917_gb300 as g  # noqa: E402
+from paper_2508_04917_gb300 import binding as B  # noqa: E402
+
+FP64_TOL = 1e-12
+
+
+def nrel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    den = np.abs(b).max()
+    return float(np.abs(a - b).max() / (den if den > 0 else 1.0))
+
+
+def cu(x):
+    return torch.from_numpy(np.ascontiguousarray(x, np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def pvec(v, perm):
+    return np.ascontiguousarray(np.asarray(v).reshape(-1, 3)[perm].reshape(-1))
+
+
+_cache = {}
+
+
+def case(grid, sub, seed=1, model=synth.MODEL_LAPLACE, **opts):
+    key = (grid, sub, seed, model, tuple(sorted(opts.items())))
+    if key not in _cache:
+        s = synth.system(*grid, seed, model=model)
+        d = oracle.decompose(s.row_ptr, s.col, s.val, grid, sub)
+        ctx = g.Ilu0DD(s.row_ptr, s.col, s.val, grid, sub, keep_host=1, **opts)
+        _cache[key] = (s, d, ctx)
+    return _cache[key]
+
+
+GEOMS = [
+    ((16, 16, 16), (8, 8, 4), synth.MODEL_LAPLACE),     # the 16^3 correctness workload
+    ((16, 16, 16), (16, 16, 8), synth.MODEL_LAYERED),
+    ((33, 17, 9), (16, 16, 8), synth.MODEL_LAYERED),     # ragged: edge subdomains smaller
+    ((12, 12, 12), (4, 4, 4), synth.MODEL_LAPLACE),
+    ((4, 3, 2), (1, 1, 1), synth.MODEL_LAPLACE),         # one-cell subdomains (block Jacobi)
+    ((40, 1, 1), (40, 1, 1), synth.MODEL_LAPLACE),       # 1D chain, one subdomain (exact LU)
+    ((1, 1, 1), (1, 1, 1), synth.MODEL_LAPLACE),         # a single cell
+    ((6, 6, 6), (6, 6, 6), synth.MODEL_LAYERED),         # one subdomain = global ILU0
+]
+IDS = [f"{g_[0]}x{g_[1]}x{g_[2]}-sub{s_[0]}x{s_[1]}x{s_[2]}-m{m}" for g_, s_, m in GEOMS]
+
+
+@pytest.mark.parametrize("grid,sub,model", GEOMS, ids=IDS)
+def test_decomposition_and_levels_exact(grid, sub, model):
+    """Algorithm 2 labels, Algorithm 3 permutation, Section 3.2 pattern and the
+    level sets of every subdomain DAG: identical integers."""
+    s, d, ctx = case(grid, sub, model=model)
+    assert np.array_equal(ctx.export(B.X_PART_ID), d.part_id)
+    assert np.array_equal(ctx.export(B.X_PERM), d.perm)
+    assert np.array_equal(ctx.export(B.X_IPERM), d.iperm)
+    assert np.array_equal(ctx.export(B.X_PART_PTR), d.part_ptr)
+    assert np.array_equal(ctx.export(B.X_AP_ROW_PTR), d.Ap.row_ptr)
+    assert np.array_equal(ctx.export(B.X_AP_COL), d.Ap.col)
+    assert np.array_equal(ctx.export(B.X_DD_ROW_PTR), d.Add.row_ptr)
+    assert np.array_equal(ctx.export(B.X_DD_COL), d.Add.col)
+    assert np.array_equal(ctx.export(B.X_LEVEL_L), oracle.levels_lower(d.Add)[0])
+    assert np.array_equal(ctx.export(B.X_LEVEL_U), oracle.levels_upper(d.Add)[0])
+
+
+@pytest.mark.parametrize("grid,sub,model", GEOMS[:4], ids=IDS[:4])
+def test_ildu0_factors_match_oracle_ilu0(grid, sub, model):
+    """Algorithm 7: the library's L, D^-1 and U~ = D^-1 U against the oracle's ILU0
+    factors (L, U): L equal, D^-1 = U_ii^-1, U~_ik = U_ii^-1 U_ik."""
+    s, d, ctx = case(grid, sub, model=model)
+    kept = d.Add.nnzb
+    L = ctx.export(B.X_L).reshape(kept, 3, 3)
+    Ut = ctx.export(B.X_UT).reshape(kept, 3, 3)
+    invD = ctx.export(B.X_INVD).reshape(-1, 3, 3)
+    rp, col, lu = d.LU.row_ptr, d.LU.col, d.LU.val
+    rows = np.repeat(np.arange(s.n), np.diff(rp))
+    lower, upper, diag = col < rows, col > rows, col == rows
+    assert nrel(L[lower], lu[lower]) <= FP64_TOL
+    Uii = lu[diag]
+    assert nrel(invD, np.linalg.inv(Uii)) <= FP64_TOL
+    ref_ut = np.einsum("nab,nbc->nac", np.linalg.inv(Uii)[rows[upper]], lu[upper])
+    if upper.any():
+        assert nrel(Ut[upper], ref_ut) <= FP64_TOL
+    assert not L[~lower].any() and not Ut[~upper].any()
+
+
+@pytest.mark.parametrize("grid,sub,model", GEOMS, ids=IDS)
+def test_apply_fp64_matches_oracle(grid, sub, model):
+    """Fused L -> D^-1 -> U~ apply (Sections 4.3-4.4) against sequential ILU0
+    substitution: normwise relative error <= 1e-12; repeat calls are bitwise equal."""
+    s, d, ctx = case(grid, sub, model=model)
+    r = np.random.default_rng(5).uniform(-1, 1, 3 * s.n)
+    z = host(ctx.apply(cu(r)))
+    zo = oracle.apply(d.LU, r)
+    assert nrel(z, zo) <= FP64_TOL
+    assert np.array_equal(host(ctx.apply(cu(r))), z)
+
+
+@pytest.mark.parametrize("grid,sub,model", GEOMS, ids=IDS)
+def test_spmv_and_dot_bitwise(grid, sub, model):
+    """SpMV (full reordered matrix) and the fixed-order dot product are bit-identical
+    to the oracle's, which follow the same per-row and reduction order."""
+    s, d, ctx = case(grid, sub, model=model)
+    x = np.random.default_rng(6).uniform(-1, 1, 3 * s.n)
+    y = host(ctx.spmv(cu(x)))
+    assert np.array_equal(y, oracle.spmv(d.Ap, x))
+    w = np.random.default_rng(7).uniform(-1, 1, 3 * s.n)
+    assert host(ctx.dot(cu(x), cu(w)))[0] == oracle.dot(x, w)
+
+
+def test_dot_sizes_and_order():
+    """Dot products over many tile counts (1 .. > 256 tiles, ragged last tile) match the
+    oracle bit for bit, including the crafted order-sensitive case."""
+    for grid in [(1, 1, 1), (7, 1, 1), (16, 16, 1), (17, 16, 1), (64, 32, 16), (64, 64, 33)]:
+        s = synth.system(*grid, 2)
+        ctx = g.Ilu0DD(s.row_ptr, s.col, s.val, grid, grid if grid[0] * grid[1] * grid[2] <= 2048 else (16, 16, 8))
+        rng = np.random.default_rng(grid[0] * 1000 + grid[2])
+        x, w = rng.normal(size=3 * s.n), rng.normal(size=3 * s.n) * 1e3
+        assert host(ctx.dot(cu(x), cu(w)))[0] == oracle.dot(x, w)
+        ctx.close()
+    s = synth.system(32, 16, 1, 2)
+    ctx = g.Ilu0DD(s.row_ptr, s.col, s.val, (32, 16, 1), (16, 16, 1))
+    x = np.zeros(3 * 512)
+    x[0], x[3], x[3 * 129] = 2.0 ** 53, 1.0, 1.0
+    assert host(ctx.dot(cu(x), cu(np.ones_like(x))))[0] == 2.0 ** 53 + 2.0
+
+
+def test_permute_round_trip():
+    s, d, ctx = case((33, 17, 9), (16, 16, 8), model=synth.MODEL_LAYERED)
+    x = np.random.default_rng(8).uniform(-1, 1, 3 * s.n)
+    xp = host(ctx.permute(cu(x), 0))
+    assert np.array_equal(xp, pvec(x, d.perm))
+    assert np.array_equal(host(ctx.permute(cu(xp), 1)), x)
+
+
+@pytest.mark.parametrize("grid,sub,model", GEOMS, ids=IDS)
+def test_bicgstab_matches_oracle(grid, sub, model):
+    """Algorithm 1 on the device: same iteration count as the oracle, solution within
+    1e-12 (normwise) of the oracle's, true residual below 1e-8."""
+    s, d, ctx = case(grid, sub, model=model)
+    x, info = ctx.solve(cu(s.b))
+    x = host(x)
+    ref = oracle.bicgstab(d.Ap, d.LU, pvec(s.b, d.perm))
+    assert ref.status == 0 and info["status"] == 0
+    assert info["iterations"] == ref.iterations
+    assert info["restarts"] == ref.restarts
+    assert nrel(x, pvec(ref.x, d.iperm)) <= FP64_TOL
+    assert info["rel_res_true"] < 1e-8
+    hist = ctx.history(ref.iterations + 1)
+    assert np.allclose(hist, ref.history, rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("sub", [(4, 4, 4), (8, 8, 8), (16, 16, 8)])
+def test_bicgstab_64cubed_sweep(sub):
+    """64^3 laplace system (262,144 block rows) for the three subdomain sizes: the
+    oracle's iteration count, its solution within 1e-12, converged true residual."""
+    s, d, ctx = case((64, 64, 64), sub, seed=2)
+    x, info = ctx.solve(cu(s.b))
+    ref = oracle.bicgstab(d.Ap, d.LU, pvec(s.b, d.perm))
+    assert info["iterations"] == ref.iterations and info["status"] == 0
+    assert nrel(host(x), pvec(ref.x, d.iperm)) <= FP64_TOL
+
+
+def test_solve_repeatable_and_graph_free_path_agree():
+    """Two solves give identical bits; the CUDA-graph path equals plain launches."""
+    s, d, ctx = case((16, 16, 16), (8, 8, 4))
+    x1, i1 = ctx.solve(cu(s.b))
+    x2, i2 = ctx.solve(cu(s.b))
+    assert torch.equal(x1, x2) and i1["iterations"] == i2["iterations"]
+    ctx2 = g.Ilu0DD(s.row_ptr, s.col, s.val, (16, 16, 16), (8, 8, 4), use_graphs=0, check_every=3)
+    x3, i3 = ctx2.solve(cu(s.b))
+    assert torch.equal(x1, x3) and i3["iterations"] == i1["iterations"]
+    ctx2.close()
+
+
+def test_zero_and_nonfinite_rhs():
+    s, d, ctx = case((12, 12, 12), (4, 4, 4))
+    x, info = ctx.solve(cu(np.zeros(3 * s.n)))
+    assert info["status"] == 0 and info["iterations"] == 0 and not host(x).any()
+    b = s.b.copy()
+    b[5] = np.nan
+    _, info = ctx.solve(cu(b), check=False)
+    assert info["status"] == B.ERR_NONFINITE
+
+
+def test_maxit_reports_not_converged():
+    s = synth.system(16, 16, 16, 1, model=synth.MODEL_LAYERED)
+    ctx = g.Ilu0DD(s.row_ptr, s.col, s.val, (16, 16, 16), (4, 4, 4), maxit=3)
+    _, info = ctx.solve(cu(s.b), check=False)
+    assert info["status"] == B.ERR_NOT_CONVERGED and info["iterations"] == 3
+    ctx.close()
+
+
+def test_largest_subdomain_fits_shared_memory():
+    """8192-row subdomains (16x16x32 cells, 192 KiB FP64 vector) run and match."""
+    grid = sub = (16, 16, 32)
+    s, d, ctx = case(grid, sub, seed=4)
+    r = np.random.default_rng(9).uniform(-1, 1, 3 * s.n)
+    assert nrel(host(ctx.apply(cu(r))), oracle.apply(d.LU, r)) <= FP64_TOL
+    assert ctx.query("smem") <= 232448
+
+
+def test_zero_pivot_reported():
+    s = synth.system(4, 4, 4, 1)
+    val = s.val.copy()
+    q = [q for q in range(s.row_ptr[5], s.row_ptr[6]) if s.col[q] == 5][0]
+    val[q] = 0.0
+    with pytest.raises(g.Ilu0DDError) as e:
+        g.Ilu0DD(s.row_ptr, s.col, val, (4, 4, 4), (2, 2, 2))
+    assert e.value.code == B.ERR_ZERO_PIVOT
+
+
+@pytest.mark.parametrize("prec,tol", [("f32", 1e-5), ("bf16", 5e-2)])
+def test_reduced_precision_factors(prec, tol):
+    """FP32 / BF16-stored factors (FP32 arithmetic): apply error against the FP64
+    oracle within the storage precision times a modest growth factor, and BiCGSTAB
+    (FP64 vectors, dots and recurrences) still reaches 1e-8."""
+    s, d, ctx = case((64, 64, 64), (16, 16, 8), seed=4, factor_prec=prec)
+    r = np.random.default_rng(10).uniform(-1, 1, 3 * s.n)
+    err = nrel(host(ctx.apply(cu(r))), oracle.apply(d.LU, r))
+    assert err <= tol
+    x, info = ctx.solve(cu(s.b))
+    assert info["status"] == 0 and info["rel_res_true"] < 1e-8
+    assert nrel(host(x), s.xstar) < 1e-6
+
+
+def test_no_device_wait_expired():
+    s, d, ctx = case((16, 16, 16), (8, 8, 4))
+    ctx.apply(cu(np.ones(3 * s.n)))
+    assert ctx.device_error() == 0
