@@ -1,0 +1,412 @@
+#!/usr/bin/env python3
+"""Benchmark of the subdomain-ILU0 BiCGSTAB hot path on one GB300 (or N replicas).
+
+Workload (default): the 160^3-cell layered system (3 unknowns per cell, 3x3
+BSR, 28.5M blocks, log-normal coefficients constant through 8-cell z-layers)
+cut into 16x16x8-cell subdomains (2,000 subdomains of 2,048 block rows), FP64.
+
+A step is one BiCGSTAB iteration (Algorithm 1) through the library: two fused
+L -> D^-1 -> U~ applies (with the p and s updates fused into their loads), two
+SpMVs with their dot products, and the fused x/r update with its dot products.
+The timed region holds exactly --steps iterations after --warmup untimed ones;
+the factor stream (2.0 GB) and the matrix (2.1 GB) exceed the 129 MB L2, so no
+flush is needed between steps.
+
+value: L+U apply throughput, algorithmic bytes of the applies (factor values,
+int32 column indices and row pointers of L and U, FP64 r in and z out, plus
+the fused p/s vector traffic) over the applies' CUDA-event time inside the
+timed region. The JSON line also reports the whole-iteration throughput, the
+per-kernel breakdown, BiCGSTAB time to relative residual 1e-8 with FP64, FP32
+and BF16 factors, the CPU oracle's throughput and the clocks seen.
+
+--impl reference times the CPU oracle (plain FP64 C, one thread) on the same
+workload and metric: one step = one full L+U apply.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "L+U apply GB/s (% of HBM peak); BiCGSTAB s to rel-res 1e-8, FP64 vs mixed"
+WORKLOAD = "layered160_sub16x16x8"
+FALLBACK_HBM_GBS = 6800.0
+
+
+# --------------------------------------------------------------------------- helpers
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2508_04917_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the kernel
+    sources are unchanged since the capture; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel, {}).get(workload)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            t = [x.strip() for x in ln.split(",")]
+            if len(t) < 9:
+                continue
+            try:
+                sm.append(float(t[1]))
+                mx.append(float(t[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, t[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """MAX of a per-rank float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def workload_system(name: str):
+    import synth
+    w = synth.WORKLOADS[name]
+    s = synth.system(*w["grid"], w["seed"], model=w["model"])
+    return s, w
+
+
+def update_bytes(n: int) -> int:
+    # reads x, ph, sh, s, t, rh; writes x, r (3 doubles per block row each)
+    return 8 * 24 * n
+
+
+# --------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+
+    import paper_2508_04917_gb300 as pkg
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    s, w = workload_system(args.workload)
+    grid, sub = w["grid"], w["sub"]
+    n = s.n
+    b = torch.from_numpy(s.b).to(dev)
+
+    # ---- timed iterations (FP64; rtol 0 so no step can stop early)
+    t_setup = time.perf_counter()
+    ctx = pkg.Ilu0DD(s.row_ptr, s.col, s.val, grid, sub, rtol=1e-300, maxit=10 ** 6)
+    setup_s = time.perf_counter() - t_setup
+    apply_b = ctx.query("apply_bytes")
+    spmv_b = ctx.query("spmv_bytes")
+    bytes_k = [apply_b + 72 * n, spmv_b + 24 * n, apply_b + 48 * n, spmv_b + 24 * n, update_bytes(n)]
+    launches_per_step = ctx.query("iter_kernels")
+    ctx.start(b)
+    ctx.iterate(args.warmup)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record()
+        kms = ctx.iterate(args.steps, timed=True)
+        e1.record()
+        torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    total_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    st = ctx.state()
+    assert st["iterations"] == args.warmup + args.steps and st["status"] == 0, st
+    apply_ms = float(kms[:, 0].sum() + kms[:, 2].sum())
+    apply_bytes_total = args.steps * (bytes_k[0] + bytes_k[2])
+    apply_gbs_rank = apply_bytes_total / (apply_ms * 1e-3) / 1e9
+    apply_gbs = world * apply_bytes_total / (max_over_ranks(apply_ms, world, dev) * 1e-3) / 1e9
+    iter_bytes = sum(bytes_k)
+    iteration_gbs = world * args.steps * iter_bytes / (total_ms * 1e-3) / 1e9
+    per_kernel = {name: {"ms": float(np.mean(kms[:, k])),
+                         "gbs": bytes_k[k] / (float(np.mean(kms[:, k])) * 1e-3) / 1e9}
+                  for k, name in enumerate(["apply_p", "spmv_v", "apply_s", "spmv_t", "update"])}
+    shares = {k: v["ms"] * args.steps / float(kms.sum()) for k, v in per_kernel.items()}
+    peak, peak_kind = measured_peaks()
+
+    # ---- plain apply (the paper's single preconditioner invocation), outside the timed region
+    r = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, 3 * n)).to(dev)
+    z = torch.empty_like(r)
+    for _ in range(3):
+        ctx.apply(r, z)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record()
+    for _ in range(args.steps):
+        ctx.apply(r, z)
+    a1.record()
+    torch.cuda.synchronize()
+    plain_ms = a0.elapsed_time(a1) / args.steps
+    plain_gbs = apply_b / (plain_ms * 1e-3) / 1e9
+
+    # ---- end to end through the public API with pinned host buffers
+    r_h = torch.from_numpy(np.random.default_rng(2).uniform(-1, 1, 3 * n)).pin_memory()
+    z_h = torch.empty_like(r_h).pin_memory()
+    for _ in range(2):
+        r.copy_(r_h, non_blocking=True)
+        ctx.apply(r, z)
+        z_h.copy_(z, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x0.record()
+    for _ in range(args.steps):
+        r.copy_(r_h, non_blocking=True)
+        ctx.apply(r, z)
+        z_h.copy_(z, non_blocking=True)
+    x1.record()
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(x0.elapsed_time(x1) / args.steps, world, dev)
+    e2e = {"value": round(world * apply_b / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+           "h2d_bytes_per_step": 24 * n, "d2h_bytes_per_step": 24 * n,
+           "what": "ilu0_dd_apply with r copied from pinned host memory and z copied back, every step"}
+    ctx.close()
+    del ctx
+
+    # ---- BiCGSTAB time to relative residual 1e-8: FP64 vs FP32 / BF16 factors
+    solves = {}
+    if not args.no_solve:
+        for prec in args.precisions.split(","):
+            t0 = time.perf_counter()
+            c = pkg.Ilu0DD(s.row_ptr, s.col, s.val, grid, sub, factor_prec=prec)
+            su = time.perf_counter() - t0
+            c.solve(b)  # warm-up (graph capture)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x, info = c.solve(b)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            err = float((x.cpu().numpy() - s.xstar).__abs__().max() / np.abs(s.xstar).max())
+            solves[prec] = {"s": round(wall, 5), "iterations": info["iterations"], "restarts": info["restarts"],
+                            "rel_res_true": info["rel_res_true"], "setup_s": round(su, 3),
+                            "max_rel_err_vs_xstar": err, "status": info["status"]}
+            c.close()
+        if "f64" in solves:
+            for k in solves:
+                solves[k]["speedup_vs_f64"] = round(solves["f64"]["s"] / solves[k]["s"], 3)
+
+    # ---- CPU baseline: the oracle as it stands, rank 0 at N = 1 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = oracle_apply_baseline(s, grid, sub, apply_b, budget_s=args.cpu_seconds)
+
+    if rank != 0:
+        return
+    traffic = recorded_traffic("ildu0_apply", args.workload)
+    line = {
+        "metric": METRIC,
+        "value": round(apply_gbs, 2),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded layered 3x3-block 7-point stencil; no dataset)",
+        "config": {"workload": args.workload, "grid": list(grid), "subdomain": list(sub),
+                   "block_rows": n, "blocks": s.nnzb,
+                   "subdomains": int(np.prod([-(-g // sb) for g, sb in zip(grid, sub)])),
+                   "step": "one BiCGSTAB iteration: 2 fused applies + 2 SpMV/dot + fused update/dot",
+                   "l2": "inputs larger than L2 (2.0 GB factor stream, 2.1 GB matrix vs 129 MB L2); no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": round(apply_gbs_rank, 2), "peak": peak, "unit": "GB/s",
+                     "frac": round(apply_gbs_rank / peak, 4), "traffic": traffic,
+                     "kernel": "ildu0_apply_kernel<double, P|S>", "peak_source": f"{peak_kind} hbm_gbs",
+                     "algorithmic_bytes_per_launch": {"apply_p": bytes_k[0], "apply_s": bytes_k[2]}},
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "iteration_gbs": round(iteration_gbs, 2),
+        "per_kernel": {k: {"ms": round(v["ms"], 5), "gbs": round(v["gbs"], 1), "share": round(shares[k], 4)}
+                       for k, v in per_kernel.items()},
+        "plain_apply": {"ms": round(plain_ms, 5), "gbs": round(plain_gbs, 2), "bytes": apply_b,
+                        "frac_of_hbm": round(plain_gbs / peak, 4)},
+        "bicgstab": solves,
+        "setup_s": round(setup_s, 3),
+        "cpu_baseline": cpu,
+    }
+    line["clocks"] = clk.summary()
+    print(json.dumps(line))
+
+
+def oracle_apply_baseline(s, grid, sub, apply_bytes, budget_s=15.0):
+    """The CPU oracle's L+U apply on the same system, repeated for about budget_s."""
+    import oracle
+    d = oracle.decompose(s.row_ptr, s.col, s.val, grid, sub)
+    r = np.random.default_rng(3).uniform(-1, 1, 3 * s.n)
+    times = []
+    t_end = time.perf_counter() + budget_s
+    while not times or time.perf_counter() < t_end:
+        t0 = time.perf_counter()
+        oracle.apply(d.LU, r)
+        times.append(time.perf_counter() - t0)
+    t = float(np.median(times))
+    return {"value": round(apply_bytes / t / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(times)} full L+U applies of the {grid[0]}x{grid[1]}x{grid[2]} system "
+                      f"({len(times) * t:.1f} s), median {t * 1e3:.1f} ms"}
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle
+    s, w = workload_system(args.workload)
+    grid, sub = w["grid"], w["sub"]
+    d = oracle.decompose(s.row_ptr, s.col, s.val, grid, sub)
+    n = s.n
+    nl = int(np.sum(d.LU.col < np.repeat(np.arange(n), np.diff(d.LU.row_ptr))))
+    nu = d.LU.nnzb - nl - n
+    apply_bytes = 9 * 8 * (nl + nu + n) + 4 * (nl + nu) + 8 * (n + 1) + 48 * n
+    r = np.random.default_rng(3).uniform(-1, 1, 3 * n)
+    for _ in range(args.warmup):
+        oracle.apply(d.LU, r)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.apply(d.LU, r)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = round(apply_bytes / dt / 1e9, 4)
+    line = {
+        "impl": "reference",
+        "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded layered 3x3-block 7-point stencil; no dataset)",
+        "config": {"workload": args.workload, "grid": list(grid), "subdomain": list(sub), "block_rows": n,
+                   "step": "one full L+U apply by the CPU oracle (plain C, one thread)"},
+        "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full L+U applies of the {grid[0]}x{grid[1]}x{grid[2]} system"},
+        "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precisions", default="f64,f32,bf16")
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

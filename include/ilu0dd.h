@@ -171,6 +171,25 @@ int ilu0_dd_permute(const ilu0dd_ctx* ctx, const double* d_in, double* d_out, in
 int bicgstab_solve(ilu0dd_ctx* ctx, const double* d_b, double* d_x, ilu0dd_info* info,
                    void* stream);
 
+/*
+ * Stepwise form of bicgstab_solve, for timing and for callers that drive the
+ * iteration themselves. bicgstab_start permutes d_b (natural numbering,
+ * device) into the workspace and sets x = 0, r = r^ = p = b, rho = (b . b)
+ * on the device (asynchronous on `stream`). bicgstab_iterate then launches n
+ * iterations of Algorithm 1 on `stream` (5 kernels each: fused apply with
+ * the p update, SpMV with (r^ . v), fused apply with s = r - alpha v, SpMV
+ * with (t . s) and (t . t), update of x and r with ||r|| and (r^ . r)).
+ * Iterations after convergence or breakdown return at once. If
+ * host_kernel_ms is not NULL it receives 5*n per-kernel durations in
+ * milliseconds (CUDA events recorded on `stream` between the launches) and
+ * the call synchronizes `stream`; otherwise it is asynchronous.
+ * bicgstab_state synchronizes `stream` and reports the current iteration
+ * count, status and recurrence residual (restarts = 0, rel_res_true = 1).
+ */
+int bicgstab_start(ilu0dd_ctx* ctx, const double* d_b, void* stream);
+int bicgstab_iterate(ilu0dd_ctx* ctx, int32_t n, float* host_kernel_ms, void* stream);
+int bicgstab_state(ilu0dd_ctx* ctx, ilu0dd_info* info, void* stream);
+
 /* Residual history of the last solve: hist[j] = ||r_j||/||b||, j = 0..iterations
  * (host destination of n doubles; copies min(n, iterations+1) entries). */
 int ilu0_dd_history(const ilu0dd_ctx* ctx, double* host_dst, int32_t n);

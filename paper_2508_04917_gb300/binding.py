@@ -95,6 +95,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "ilu0_dd_dot": ([vp, vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_permute": ([vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
             "bicgstab_solve": ([vp, vp, vp, ctypes.POINTER(Info), vp], ctypes.c_int),
+            "bicgstab_start": ([vp, vp, vp], ctypes.c_int),
+            "bicgstab_iterate": ([vp, i32, vp, vp], ctypes.c_int),
+            "bicgstab_state": ([vp, ctypes.POINTER(Info), vp], ctypes.c_int),
             "ilu0_dd_history": ([vp, vp, i32], ctypes.c_int),
             "ilu0_dd_export": ([vp, ctypes.c_int, vp, sz], ctypes.c_int),
             "ilu0_dd_query": ([vp, ctypes.c_int, ctypes.POINTER(i64)], ctypes.c_int),
@@ -262,6 +265,23 @@ class Ilu0DD:
         d = info.as_dict()
         d["status"] = rc
         return x, d
+
+    def start(self, b, stream=None):
+        """bicgstab_start: load b (natural numbering) and set the initial state."""
+        self._check(self._lib.bicgstab_start(self._ctx, _dptr(b, self.size, "b"), _stream(stream)),
+                    "bicgstab_start")
+
+    def iterate(self, n, timed=False, stream=None):
+        """bicgstab_iterate: n iterations; with timed=True returns (n, 5) kernel milliseconds."""
+        ms = np.zeros(5 * n, np.float32) if timed else None
+        self._check(self._lib.bicgstab_iterate(self._ctx, int(n), None if ms is None else ms.ctypes.data,
+                                               _stream(stream)), "bicgstab_iterate")
+        return None if ms is None else ms.reshape(n, 5)
+
+    def state(self, stream=None):
+        info = Info()
+        self._check(self._lib.bicgstab_state(self._ctx, ctypes.byref(info), _stream(stream)), "bicgstab_state")
+        return info.as_dict()
 
     # -- inspection -------------------------------------------------------
     def history(self, n=None):

@@ -31,6 +31,7 @@ struct ilu0dd_ctx {
   int last_iterations = 0;
   cudaError_t last_cuda = cudaSuccess;
   std::string why;
+  std::vector<cudaEvent_t> events;  // bicgstab_iterate timing
   // host copies for ilu0_dd_export (opts.keep_host)
   std::vector<double> F, invD;
   bool have_factors = false;
@@ -398,6 +399,62 @@ int bicgstab_solve(ilu0dd_ctx* c, const double* d_b, double* d_x, ilu0dd_info* i
   return status;
 }
 
+int bicgstab_start(ilu0dd_ctx* c, const double* d_b, void* stream) {
+  if (!c || (c->plan.N > 0 && !d_b)) return ILU0DD_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CK(c, launch_permute(c->dev, d_b, c->dev.vec[kVecB], 0, s));
+  CK(c, launch_init(c->dev, c->rtol, c->maxit, s));
+  return ILU0DD_OK;
+}
+
+int bicgstab_iterate(ilu0dd_ctx* c, int32_t n, float* host_kernel_ms, void* stream) {
+  if (!c || n < 0) return ILU0DD_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const DevCtx& d = c->dev;
+  if (!host_kernel_ms) {
+    for (int32_t i = 0; i < n; ++i) CK(c, launch_iteration(d, s));
+    return ILU0DD_OK;
+  }
+  const size_t need = 5 * (size_t)n + 1;
+  while (c->events.size() < need) {
+    cudaEvent_t e;
+    CK(c, cudaEventCreate(&e));
+    c->events.push_back(e);
+  }
+  size_t k = 0;
+  CK(c, cudaEventRecord(c->events[k++], s));
+  for (int32_t i = 0; i < n; ++i) {
+    CK(c, launch_apply(d, kModeP, d.vec[kVecR], d.vec[kVecPh], s));
+    CK(c, cudaEventRecord(c->events[k++], s));
+    CK(c, launch_spmv(d, 1, d.vec[kVecPh], d.vec[kVecV], s));
+    CK(c, cudaEventRecord(c->events[k++], s));
+    CK(c, launch_apply(d, kModeS, d.vec[kVecR], d.vec[kVecSh], s));
+    CK(c, cudaEventRecord(c->events[k++], s));
+    CK(c, launch_spmv(d, 2, d.vec[kVecSh], d.vec[kVecT], s));
+    CK(c, cudaEventRecord(c->events[k++], s));
+    CK(c, launch_update(d, s));
+    CK(c, cudaEventRecord(c->events[k++], s));
+  }
+  CK(c, cudaStreamSynchronize(s));
+  for (size_t j = 0; j + 1 < k; ++j) CK(c, cudaEventElapsedTime(&host_kernel_ms[j], c->events[j], c->events[j + 1]));
+  return ILU0DD_OK;
+}
+
+int bicgstab_state(ilu0dd_ctx* c, ilu0dd_info* info, void* stream) {
+  if (!c || !info) return ILU0DD_ERR_INVALID;
+  SolverScalars h{};
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CK(c, cudaMemcpyAsync(&h, c->dev.scal, sizeof h, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  std::memset(info, 0, sizeof *info);
+  info->status = h.status;
+  info->iterations = h.iter;
+  info->rel_res_recurrence = h.rel;
+  info->rel_res_true = 1.0;
+  info->setup_s = c->setup_s;
+  return ILU0DD_OK;
+}
+
 int ilu0_dd_history(const ilu0dd_ctx* c, double* host_dst, int32_t n) {
   if (!c || !host_dst || n < 0) return ILU0DD_ERR_INVALID;
   int32_t m = std::min(n, c->last_iterations + 1);
@@ -482,6 +539,7 @@ int ilu0_dd_device_error(const ilu0dd_ctx* c, int32_t* code) {
 
 void ilu0_dd_destroy(ilu0dd_ctx* c) {
   if (!c) return;
+  for (cudaEvent_t e : c->events) cudaEventDestroy(e);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->own) cudaStreamDestroy(c->own);
   delete c;

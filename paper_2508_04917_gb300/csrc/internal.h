@@ -84,6 +84,8 @@ constexpr int kDotTile = 256;
 constexpr int kMaxSlots = 16;
 // Maximum apply threads per block.
 constexpr int kMaxApplyThreads = 512;
+// Static shared memory reserved by the apply kernel (mbarriers, flags).
+constexpr int kApplyStaticSmem = 256;
 
 enum ApplyMode : int {
   kModePlain = 0,   // smem <- r

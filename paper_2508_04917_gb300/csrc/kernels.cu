@@ -193,22 +193,26 @@ static cudaError_t configure_one(size_t smem) {
                               (int)smem);
 }
 
+// The attribute is a per-kernel permission shared by every context in the
+// process, so it is raised once to the device's opt-in maximum; each launch
+// still requests only its own context's shared memory.
 cudaError_t apply_configure(const DevCtx& d) {
-  cudaError_t e = cudaSuccess;
+  (void)d;
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  const size_t smem = (size_t)optin - kApplyStaticSmem;
   auto acc = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
-  if (d.factor_prec == ILU0DD_F64) {
-    acc(configure_one<double, kModePlain>(d.smem_bytes));
-    acc(configure_one<double, kModeP>(d.smem_bytes));
-    acc(configure_one<double, kModeS>(d.smem_bytes));
-  } else if (d.factor_prec == ILU0DD_F32) {
-    acc(configure_one<float, kModePlain>(d.smem_bytes));
-    acc(configure_one<float, kModeP>(d.smem_bytes));
-    acc(configure_one<float, kModeS>(d.smem_bytes));
-  } else {
-    acc(configure_one<bf16s, kModePlain>(d.smem_bytes));
-    acc(configure_one<bf16s, kModeP>(d.smem_bytes));
-    acc(configure_one<bf16s, kModeS>(d.smem_bytes));
-  }
+  acc(configure_one<double, kModePlain>(smem));
+  acc(configure_one<double, kModeP>(smem));
+  acc(configure_one<double, kModeS>(smem));
+  acc(configure_one<float, kModePlain>(smem));
+  acc(configure_one<float, kModeP>(smem));
+  acc(configure_one<float, kModeS>(smem));
+  acc(configure_one<bf16s, kModePlain>(smem));
+  acc(configure_one<bf16s, kModeP>(smem));
+  acc(configure_one<bf16s, kModeS>(smem));
   return e;
 }
 

@@ -140,6 +140,8 @@ WORKLOADS = {
     "laplace64_sub8": dict(grid=(64, 64, 64), sub=(8, 8, 8), model=MODEL_LAPLACE, seed=2),
     "laplace64_sub16x16x8": dict(grid=(64, 64, 64), sub=(16, 16, 8), model=MODEL_LAPLACE, seed=2),
     "layered160_sub16x16x8": dict(grid=(160, 160, 160), sub=(16, 16, 8), model=MODEL_LAYERED, seed=3),
+    # smaller case of the same shape (0.48 GB apply, above L2) for profiler captures
+    "layered96_sub16x16x8": dict(grid=(96, 96, 96), sub=(16, 16, 8), model=MODEL_LAYERED, seed=3),
     "laplace64_mixed_sub16x16x8": dict(grid=(64, 64, 64), sub=(16, 16, 8), model=MODEL_LAPLACE, seed=4),
 }
 
