@@ -76,8 +76,8 @@ typedef struct {
 
 typedef struct {
   int32_t factor_prec;      /* ILU0DD_F64 / ILU0DD_F32 / ILU0DD_BF16 */
-  int32_t threads_per_cta;  /* apply block size; 0 = smallest multiple of 32 >= widest level (<= 512) */
-  int32_t ring_bytes;       /* apply staging ring per block (power of two); 0 = automatic */
+  int32_t threads_per_cta;  /* apply block size; 0 = 32 per ten rows of the widest level (<= 384) */
+  int32_t prefetch_bytes;   /* apply: L2 prefetch distance per block, bytes (multiple of 16); 0 = 65536 */
   int32_t maxit;            /* BiCGSTAB iteration limit; 0 = 10000 */
   double rtol;              /* stop when ||r||_2/||b||_2 < rtol; 0 = 1e-8 */
   int32_t check_every;      /* iterations per CUDA-graph launch between convergence polls; 0 = 8 */

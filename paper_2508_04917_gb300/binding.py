@@ -48,7 +48,7 @@ class Geom(ctypes.Structure):
 
 class Opts(ctypes.Structure):
     _fields_ = [("factor_prec", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
-                ("ring_bytes", ctypes.c_int32), ("maxit", ctypes.c_int32), ("rtol", ctypes.c_double),
+                ("prefetch_bytes", ctypes.c_int32), ("maxit", ctypes.c_int32), ("rtol", ctypes.c_double),
                 ("check_every", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
                 ("keep_host", ctypes.c_int32), ("trace", ctypes.c_int32)]
 

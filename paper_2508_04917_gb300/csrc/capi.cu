@@ -83,7 +83,7 @@ int ilu0dd_default_opts(ilu0dd_opts* o) {
   std::memset(o, 0, sizeof *o);
   o->factor_prec = ILU0DD_F64;
   o->threads_per_cta = 0;
-  o->ring_bytes = 0;
+  o->prefetch_bytes = 0;
   o->maxit = 10000;
   o->rtol = 1e-8;
   o->check_every = 8;
@@ -201,10 +201,8 @@ int ilu0_dd_setup(const ilu0dd_bsr* A, const ilu0dd_geom* geom, const ilu0dd_opt
     d.pieces = reinterpret_cast<const PieceDesc*>(c->ws + L.pieces);
     d.nsub = p.nsub;
     d.threads = p.threads;
-    d.ring_bytes = p.ring_bytes;
-    d.chunk_bytes = p.chunk_bytes;
-    d.nslot = p.nslot;
-    d.vec_bytes = (int)(p.smem_bytes - (size_t)p.ring_bytes);
+    d.prefetch_bytes = p.prefetch_bytes;
+    d.vec_bytes = (int)p.smem_bytes;
     d.factor_prec = o.factor_prec;
     d.smem_bytes = p.smem_bytes;
     d.slice_off = reinterpret_cast<const int32_t*>(c->ws + L.sell_off);

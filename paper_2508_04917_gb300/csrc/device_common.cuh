@@ -73,11 +73,17 @@ template <>
 struct FactorLoad<double> {
   using compute = double;
   __device__ __forceinline__ static double get(const unsigned char* p) { return *reinterpret_cast<const double*>(p); }
+  __device__ __forceinline__ static double getg(const unsigned char* p) {
+    return __ldg(reinterpret_cast<const double*>(p));
+  }
 };
 template <>
 struct FactorLoad<float> {
   using compute = float;
   __device__ __forceinline__ static float get(const unsigned char* p) { return *reinterpret_cast<const float*>(p); }
+  __device__ __forceinline__ static float getg(const unsigned char* p) {
+    return __ldg(reinterpret_cast<const float*>(p));
+  }
 };
 struct bf16s {
   uint16_t v;
@@ -87,6 +93,9 @@ struct FactorLoad<bf16s> {
   using compute = float;
   __device__ __forceinline__ static float get(const unsigned char* p) {
     return bf16_to_f32(*reinterpret_cast<const uint16_t*>(p));
+  }
+  __device__ __forceinline__ static float getg(const unsigned char* p) {
+    return bf16_to_f32(__ldg(reinterpret_cast<const unsigned short*>(p)));
   }
 };
 

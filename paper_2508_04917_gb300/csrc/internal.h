@@ -14,7 +14,7 @@ namespace ilu0dd {
 // Fused-apply factor stream.
 //
 // Every subdomain owns one contiguous byte range ("its stream"), read in order
-// by its thread block through a ring of bulk copies. The stream is a sequence
+// by its thread block (with bulk L2 prefetches running ahead). The stream is a sequence
 // of piece records. A piece is a set of rows of one level of the subdomain's L
 // DAG (kind 0) or U DAG (kind 1); rows of one piece are independent, pieces
 // are separated by a block barrier. Rows with no strictly-lower block (L level
@@ -22,23 +22,32 @@ namespace ilu0dd {
 //
 // Inside a record the rows are sorted by block count, longest first, and the
 // blocks are stored slot-major ("jagged diagonal" order): slot s holds the
-// s-th block (ascending column) of the first cnt[s] rows. All arrays are
-// structure-of-arrays so consecutive threads read consecutive addresses.
+// s-th block (ascending column) of the first cnt[s] rows. Three threads work
+// on each row, one per output component a, so values are interleaved by
+// component: within slot s, entry B[a][c] of the block of row t sits at
+// (c * cnt[s] + t) * 3 + a, and consecutive threads read consecutive values.
 //
 //   u16 cnt[w]                 rows having more than s blocks, s = 0..w-1
 //   u16 rows[n]                local row index (0 .. nrows-1 of the subdomain)
 //   u16 cols[nb]               slot-major local column of each block
 //   pad to 16
-//   T   invD[9][n]             (kind 1 only) D^-1 = U_ii^-1, entry-major
-//   T   vals[...]              per slot s: 9 entry arrays of cnt[s] values
+//   T   invD[3 * n * 3]        (kind 1 only) D^-1 = U_ii^-1, entry [a][c] at (c * n + t) * 3 + a
+//   T   vals[...]              per slot s: 9 * cnt[s] values as above
 //   pad to 16
-// T is the factor storage type (double, float or bf16).
+// T is the factor storage type (double, float or bf16). Each warp of a block
+// covers ten rows of a piece with lanes 0..29 (lane = 3 * row + a; lanes 30
+// and 31 idle), so the three threads of a row share a warp and exchange values
+// with shuffles.
 // ---------------------------------------------------------------------------
-struct PieceDesc {          // 16 bytes, one per piece, device array
+constexpr int kRowsPerWarp = 10;
+constexpr int kDescSlots = 3;   // slot counts carried in the descriptor
+struct PieceDesc {          // 32 bytes, one per piece, device array
   uint32_t off;             // record start, bytes from the subdomain stream start
   uint32_t meta;            // n | (w << 16) | (kind << 24)
   uint32_t nb;              // blocks in the record
   uint32_t voff;            // first value array (invD or vals), bytes from record start
+  uint16_t cnt[4];          // cnt[s] for s < min(w, kDescSlots) (copy of the record's head), 0 beyond
+  uint32_t pad[2];
 };
 
 struct CtaDesc {            // 32 bytes, one per subdomain
@@ -80,12 +89,11 @@ enum CounterId : int { kCntInit = 0, kCntSpmvV, kCntSpmvT, kCntUpdate, kCntResid
 constexpr int kSlice = 32;
 // Block rows per tile of the fixed dot order.
 constexpr int kDotTile = 256;
-// Maximum apply ring slots.
-constexpr int kMaxSlots = 16;
-// Maximum apply threads per block.
-constexpr int kMaxApplyThreads = 512;
-// Static shared memory reserved by the apply kernel (mbarriers, flags).
-constexpr int kApplyStaticSmem = 256;
+// Maximum apply threads per block, and blocks per SM the register budget targets.
+constexpr int kMaxApplyThreads = 384;
+constexpr int kApplyMinBlocks = 3;
+// Static shared memory of the apply kernel (it uses dynamic shared memory only).
+constexpr int kApplyStaticSmem = 0;
 
 enum ApplyMode : int {
   kModePlain = 0,   // smem <- r
@@ -112,7 +120,7 @@ struct Plan {
   int32_t max_levels = 0;
   // apply packing
   int threads = 0;
-  int ring_bytes = 0, chunk_bytes = 0, nslot = 0;
+  int prefetch_bytes = 0;
   int vec_elem = 8, factor_elem = 8;
   int rmax = 0, max_pieces = 0;
   size_t smem_bytes = 0;

@@ -32,54 +32,53 @@ struct ApplyArgs {
   const double* v;
   const SolverScalars* scal;
   int32_t* err;
-  int ring_bytes, chunk_bytes, nslot, vec_bytes;
+  int prefetch_bytes, vec_bytes;
 };
 
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <typename TF>
-__device__ __forceinline__ typename FactorLoad<TF>::compute ring_factor(const unsigned char* ring, uint32_t mask,
-                                                                         uint32_t off) {
-  return FactorLoad<TF>::get(ring + (off & mask));
+__device__ __forceinline__ typename FactorLoad<TF>::compute gfactor(const unsigned char* p) {
+  return FactorLoad<TF>::getg(p);
 }
 
-__device__ __forceinline__ uint32_t ring_u16(const unsigned char* ring, uint32_t mask, uint32_t off) {
-  return *reinterpret_cast<const uint16_t*>(ring + (off & mask));
+__device__ __forceinline__ int gu16(const unsigned char* p) {
+  return (int)__ldg(reinterpret_cast<const unsigned short*>(p));
 }
 
+// One block per subdomain. The block reads its factor records straight from
+// global memory (coalesced: consecutive threads read consecutive values) while
+// thread 0 keeps bulk L2 prefetches (cp.async.bulk.prefetch.L2) a fixed
+// distance ahead in the subdomain's stream, so the per-level loads hit L2.
+// Shared memory holds only the subdomain vector. Three threads per row
+// (lane = 3 * (row in warp) + a, ten rows per warp); rows of one piece are
+// independent and pieces are separated by block barriers.
 template <typename TF, int MODE>
-__global__ void __launch_bounds__(kMaxApplyThreads) ildu0_apply_kernel(ApplyArgs a) {
+__global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks) ildu0_apply_kernel(ApplyArgs a) {
   using TV = typename FactorLoad<TF>::compute;
   constexpr uint32_t FE = sizeof(TF);
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ uint64_t bars[kMaxSlots];
-  __shared__ int abort_flag;
 
   if (MODE != kModePlain && a.scal->done) return;
   const CtaDesc cd = a.cta[blockIdx.x];
   const int tid = threadIdx.x;
   TV* y = reinterpret_cast<TV*>(smem);
-  unsigned char* ring = smem + a.vec_bytes;
-  const unsigned char* gsrc = a.stream + cd.stream_off;
-  const uint32_t CH = (uint32_t)a.chunk_bytes;
-  const uint32_t mask = (uint32_t)a.ring_bytes - 1u;
-  const int nslot = a.nslot;
-  const int nchunks = (int)((cd.stream_len + CH - 1) / CH);
-
-  auto issue = [&](int c) {
-    const int slot = c % nslot;
-    const uint32_t bytes = min(CH, (uint32_t)cd.stream_len - (uint32_t)c * CH);
-    mbar_arrive_expect_tx(&bars[slot], bytes);
-    bulk_g2s(ring + (uint32_t)slot * CH, gsrc + (size_t)c * CH, bytes, &bars[slot]);
+  const unsigned char* gs = a.stream + cd.stream_off;
+  const uint32_t len = (uint32_t)cd.stream_len;
+  const uint32_t dist = (uint32_t)a.prefetch_bytes;
+  constexpr uint32_t kPf = 16384;  // bytes per L2 prefetch instruction
+  uint32_t pf_end = 0;             // prefetched prefix of the stream (thread 0)
+  auto prefetch_upto = [&](uint32_t upto) {
+    upto = min(upto, len);
+    while (pf_end < upto) {
+      const uint32_t bytes = min(kPf, len - pf_end);
+      prefetch_l2(gs + pf_end, bytes);
+      pf_end += bytes;
+    }
   };
-
-  if (tid == 0) {
-    for (int i = 0; i < nslot; ++i) mbar_init(&bars[i], 1);
-    mbar_fence_init();
-    abort_flag = 0;
-  }
-  __syncthreads();
-  int issued = 0;  // tracked by thread 0
-  if (tid == 0)
-    for (; issued < nchunks && issued < nslot; ++issued) issue(issued);
+  if (tid == 0) prefetch_upto(dist);
 
   // subdomain vector -> shared memory (with the fused BiCGSTAB update)
   const int64_t base = 3ll * cd.row0;
@@ -102,87 +101,91 @@ __global__ void __launch_bounds__(kMaxApplyThreads) ildu0_apply_kernel(ApplyArgs
   }
   __syncthreads();
 
-  PieceDesc nxt = cd.npieces > 0 ? a.pieces[cd.piece0] : PieceDesc{0, 0, 0, 0};
+  const int warp = tid >> 5, lane = tid & 31;
+  const int comp = lane % 3;
+  const int trow = warp * kRowsPerWarp + lane / 3;
+  const bool lane_ok = lane < 3 * kRowsPerWarp;
+  const int base_lane = lane - comp;
+
+  PieceDesc nxt = cd.npieces > 0 ? a.pieces[cd.piece0] : PieceDesc{};
   for (int k = 0; k < cd.npieces; ++k) {
     const PieceDesc pd = nxt;
     if (k + 1 < cd.npieces) nxt = a.pieces[cd.piece0 + k + 1];
+    if (tid == 0) prefetch_upto(pd.off + dist);
     const int n = (int)(pd.meta & 0xFFFFu);
     const int w = (int)((pd.meta >> 16) & 0xFFu);
     const int kind = (int)(pd.meta >> 24);
-    const uint32_t beg = pd.off;
-    const uint32_t vend = pd.voff + ((kind ? 9u * (uint32_t)n : 0u) + 9u * pd.nb) * FE;
-    const uint32_t end = beg + ((vend + 15u) & ~15u);
-    const int c_first = (int)(beg / CH), c_last = (int)((end - 1) / CH);
-    if (tid == 0) {
-      const int lim = c_first + nslot;
-      for (; issued < nchunks && issued < lim; ++issued) issue(issued);
-    }
-    if (tid < n) {
-      bool ok = true;
-      for (int c = c_first; c <= c_last; ++c)
-        ok &= mbar_wait_bounded(&bars[c % nslot], (uint32_t)((c / nslot) & 1));
-      if (!ok) {
-        abort_flag = 1;
-        atomicOr(a.err, kDevErrWaitExpired);
-      } else {
-        const uint32_t rb = beg;  // record base in stream bytes
-        const int row = (int)ring_u16(ring, mask, rb + 2u * (uint32_t)(w + tid));
-        TV acc0 = y[3 * row], acc1 = y[3 * row + 1], acc2 = y[3 * row + 2];
-        uint32_t vb = rb + pd.voff;
-        if (kind) {
-          // D^-1 (Section 4.3): w_i = D_i^-1 y_i before the U~ updates
-          TV d[9];
+    if (warp * kRowsPerWarp < n) {  // warp-uniform: this warp has rows in the piece
+      const bool active = lane_ok && trow < n;
+      const unsigned char* rec = gs + pd.off;
+      const unsigned char* cb = rec + 2 * (w + n);
+      const unsigned char* vb = rec + pd.voff + (kind ? 9 * (size_t)n * FE : 0);
+      // Issue every load of this row's slots at once: slot s starts at block
+      // c0[s] = cnt[0] + .. + cnt[s-1] of the record (counts from the descriptor).
+      int col[kDescSlots];
+      TV bv[kDescSlots][3];
+      uint32_t c0 = 0;
+      int len = 0;
 #pragma unroll
-          for (int e = 0; e < 9; ++e) d[e] = ring_factor<TF>(ring, mask, vb + ((uint32_t)(e * n + tid)) * FE);
-          TV t0 = d[0] * acc0, t1 = d[3] * acc0, t2 = d[6] * acc0;
-          t0 = fma(d[1], acc1, t0);
-          t1 = fma(d[4], acc1, t1);
-          t2 = fma(d[7], acc1, t2);
-          t0 = fma(d[2], acc2, t0);
-          t1 = fma(d[5], acc2, t1);
-          t2 = fma(d[8], acc2, t2);
-          acc0 = t0;
-          acc1 = t1;
-          acc2 = t2;
-          vb += 9u * (uint32_t)n * FE;
-        }
-        const uint32_t cb = rb + 2u * (uint32_t)(w + n);
-        uint32_t c0 = 0;
-        for (int sl = 0; sl < w; ++sl) {
-          const uint32_t cs = ring_u16(ring, mask, rb + 2u * (uint32_t)sl);
-          if ((uint32_t)tid >= cs) break;
-          const int col = (int)ring_u16(ring, mask, cb + 2u * (c0 + (uint32_t)tid));
-          const uint32_t vo = vb + 9u * c0 * FE + (uint32_t)tid * FE;
-          TV b[9];
+      for (int sl = 0; sl < kDescSlots; ++sl) {
+        const uint32_t cs = pd.cnt[sl];  // 0 beyond w
+        const bool has = active && sl < w && (uint32_t)trow < cs;
+        len += has;
+        col[sl] = has ? gu16(cb + 2 * (c0 + (uint32_t)trow)) : 0;
+        const unsigned char* vo = vb + (9 * (size_t)c0 + (size_t)(3 * trow + comp)) * FE;
+        const size_t cstride = 3 * (size_t)cs * FE;
 #pragma unroll
-          for (int e = 0; e < 9; ++e) b[e] = ring_factor<TF>(ring, mask, vo + (uint32_t)e * cs * FE);
-          const TV x0 = y[3 * col], x1 = y[3 * col + 1], x2 = y[3 * col + 2];
-          acc0 = fma(-b[0], x0, acc0);
-          acc1 = fma(-b[3], x0, acc1);
-          acc2 = fma(-b[6], x0, acc2);
-          acc0 = fma(-b[1], x1, acc0);
-          acc1 = fma(-b[4], x1, acc1);
-          acc2 = fma(-b[7], x1, acc2);
-          acc0 = fma(-b[2], x2, acc0);
-          acc1 = fma(-b[5], x2, acc1);
-          acc2 = fma(-b[8], x2, acc2);
-          c0 += cs;
+        for (int c = 0; c < 3; ++c) bv[sl][c] = has ? gfactor<TF>(vo + c * cstride) : TV(0);
+        c0 += cs;
+      }
+      TV d[3] = {TV(0), TV(0), TV(0)};
+      if (kind && active) {
+        const unsigned char* io = rec + pd.voff + (size_t)(3 * trow + comp) * FE;
+        const size_t cstride = 3 * (size_t)n * FE;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d[c] = gfactor<TF>(io + c * cstride);
+      }
+      const int row = active ? gu16(rec + 2 * (w + trow)) : 0;
+      TV acc = active ? y[3 * row + comp] : TV(0);
+      if (kind) {
+        // D^-1 (Section 4.3): w_i = D_i^-1 y_i; the row's three components
+        // come from the neighbouring lanes
+        const TV y0 = __shfl_sync(0xffffffffu, acc, base_lane);
+        const TV y1 = __shfl_sync(0xffffffffu, acc, base_lane + 1);
+        const TV y2 = __shfl_sync(0xffffffffu, acc, base_lane + 2);
+        TV t = d[0] * y0;
+        t = fma(d[1], y1, t);
+        t = fma(d[2], y2, t);
+        if (active) acc = t;
+      }
+      if (active) {
+#pragma unroll
+        for (int sl = 0; sl < kDescSlots; ++sl) {
+          if (sl < len) {
+            const int cl = col[sl];
+            acc = fma(-bv[sl][0], y[3 * cl], acc);
+            acc = fma(-bv[sl][1], y[3 * cl + 1], acc);
+            acc = fma(-bv[sl][2], y[3 * cl + 2], acc);
+          }
         }
-        y[3 * row] = acc0;
-        y[3 * row + 1] = acc1;
-        y[3 * row + 2] = acc2;
+        // rows with more than kDescSlots blocks (general patterns): remaining slots
+        if (w > kDescSlots && len == kDescSlots) {
+          for (int sl = kDescSlots; sl < w; ++sl) {
+            const uint32_t cs = (uint32_t)gu16(rec + 2 * sl);
+            if ((uint32_t)trow >= cs) break;
+            const int cl = gu16(cb + 2 * (c0 + (uint32_t)trow));
+            const unsigned char* vo = vb + (9 * (size_t)c0 + (size_t)(3 * trow + comp)) * FE;
+            const size_t cstride = 3 * (size_t)cs * FE;
+            acc = fma(-gfactor<TF>(vo), y[3 * cl], acc);
+            acc = fma(-gfactor<TF>(vo + cstride), y[3 * cl + 1], acc);
+            acc = fma(-gfactor<TF>(vo + 2 * cstride), y[3 * cl + 2], acc);
+            c0 += cs;
+          }
+        }
+        y[3 * row + comp] = acc;
       }
     }
     __syncthreads();
-    if (abort_flag) break;
-  }
-  if (abort_flag) {
-    // drain copies still in flight (bounded) before the block exits
-    // (only the last nslot issued chunks can be pending; each is the latest use of its slot)
-    if (tid == 0)
-      for (int c = max(0, issued - nslot); c < issued; ++c)
-        mbar_wait_bounded(&bars[c % nslot], (uint32_t)((c / nslot) & 1));
-    return;
   }
   for (int e = tid; e < nv; e += blockDim.x) a.z[base + e] = (double)y[e];
 }
@@ -202,7 +205,7 @@ cudaError_t apply_configure(const DevCtx& d) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  const size_t smem = (size_t)optin - kApplyStaticSmem;
+  const size_t smem = (size_t)optin - kApplyStaticSmem;  // the kernel's static shared memory
   auto acc = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
   acc(configure_one<double, kModePlain>(smem));
   acc(configure_one<double, kModeP>(smem));
@@ -241,9 +244,7 @@ cudaError_t launch_apply(const DevCtx& d, int mode, const double* r, double* z, 
   a.v = d.vec[kVecV];
   a.scal = d.scal;
   a.err = d.err;
-  a.ring_bytes = d.ring_bytes;
-  a.chunk_bytes = d.chunk_bytes;
-  a.nslot = d.nslot;
+  a.prefetch_bytes = d.prefetch_bytes;
   a.vec_bytes = d.vec_bytes;
   if (d.factor_prec == ILU0DD_F64) return launch_apply_t<double>(d, mode, a, s);
   if (d.factor_prec == ILU0DD_F32) return launch_apply_t<float>(d, mode, a, s);

@@ -12,7 +12,7 @@ struct DevCtx {
   const unsigned char* stream;
   const CtaDesc* cta;
   const PieceDesc* pieces;
-  int nsub, threads, ring_bytes, chunk_bytes, nslot, vec_bytes, factor_prec;
+  int nsub, threads, prefetch_bytes, vec_bytes, factor_prec;
   size_t smem_bytes;
   // SpMV (sliced ELL of the reordered full matrix)
   const int32_t* slice_off;

@@ -276,22 +276,23 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
       p.max_levels = std::max(p.max_levels, nlev_l[s] + nlev_u[s]);
     }
   }
-  p.threads = o->threads_per_cta > 0 ? o->threads_per_cta : std::min(kMaxApplyThreads, (int)align_up(widest, 32));
+  // warps of ten rows each
+  p.threads = o->threads_per_cta > 0 ? o->threads_per_cta
+                                      : std::min(kMaxApplyThreads, 32 * ceil_div(widest, kRowsPerWarp));
   if (p.threads % 32 || p.threads > kMaxApplyThreads || p.threads < 32) {
-    *why = "threads_per_cta must be a multiple of 32 in [32, 512]";
+    *why = "threads_per_cta must be a multiple of 32 in [32, 384]";
     return ILU0DD_ERR_INVALID;
   }
-  p.ring_bytes = o->ring_bytes > 0 ? o->ring_bytes : 32768;
-  if (p.ring_bytes < 2048 || (p.ring_bytes & (p.ring_bytes - 1)) || p.ring_bytes > (1 << 20)) {
-    *why = "ring_bytes must be a power of two >= 2048";
+  p.prefetch_bytes = o->prefetch_bytes > 0 ? o->prefetch_bytes : 65536;
+  if (p.prefetch_bytes % 16 || p.prefetch_bytes > (1 << 24)) {
+    *why = "prefetch_bytes must be a multiple of 16 up to 16 MiB";
     return ILU0DD_ERR_INVALID;
   }
-  p.nslot = 8;
-  p.chunk_bytes = p.ring_bytes / p.nslot;
-  const int64_t cap = (int64_t)(p.nslot - 1) * p.chunk_bytes;
+  const int rows_cap = (p.threads / 32) * kRowsPerWarp;
+  const int64_t cap = 1ll << 30;  // record bytes (offsets are 32-bit)
 
   // ---- pieces: per subdomain, L levels 1.. then U levels 0.., rows of a level
-  // sorted by block count (longest first), split by thread count and ring size
+  // sorted by block count (longest first), split by the block's row capacity
   p.cta.resize(p.nsub);
   std::vector<std::vector<std::vector<int32_t>>> sub_pieces(p.nsub);
   std::vector<std::vector<int64_t>> sub_bytes(p.nsub);
@@ -321,10 +322,10 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
         std::sort(key.begin(), key.end());
         size_t a = 0;
         while (a < key.size()) {
-          // grow the piece while it fits the block and the ring
+          // grow the piece while it fits the block
           size_t b = a;
           int64_t nb = 0;
-          while (b < key.size() && (int)(b - a) < p.threads) {
+          while (b < key.size() && (int)(b - a) < rows_cap) {
             int w = -key[a].first;
             int64_t bytes = record_bytes((int)(b - a + 1), w, nb - key[b].first, kind, p.factor_elem, nullptr);
             if (bytes > cap && b > a) break;
@@ -337,11 +338,16 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
           if (bytes > cap || w > 255) sub_fail[s] = 1;
           std::vector<int32_t> pr;
           for (size_t t = a; t < b; ++t) pr.push_back(key[t].second - r0);
-          PieceDesc d;
+          PieceDesc d{};
           d.off = off;
           d.meta = (uint32_t)n | ((uint32_t)w << 16) | ((uint32_t)kind << 24);
           d.nb = (uint32_t)nb;
           d.voff = (uint32_t)voff;
+          for (int sl = 0; sl < std::min(w, kDescSlots); ++sl) {
+            int c = 0;
+            for (size_t t = a; t < b; ++t) c += -key[t].first > sl;
+            d.cnt[sl] = (uint16_t)c;
+          }
           sub_desc[s].push_back(d);
           sub_pieces[s].push_back(std::move(pr));
           sub_bytes[s].push_back(bytes);
@@ -353,7 +359,7 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   });
   for (int s = 0; s < p.nsub; ++s)
     if (sub_fail[s]) {
-      *why = "a single row's blocks exceed the apply staging ring; raise ring_bytes";
+      *why = "a piece record exceeds 1 GiB or has more than 255 blocks per row";
       return ILU0DD_ERR_SMEM;
     }
   int64_t soff = 0;
@@ -380,10 +386,10 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   }
   p.stream_bytes = soff;
   p.n_pieces = (int64_t)p.pieces.size();
-  p.smem_bytes = (size_t)align_up(3ll * p.rmax * p.vec_elem, 128) + (size_t)p.ring_bytes;
+  p.smem_bytes = (size_t)align_up(3ll * p.rmax * p.vec_elem, 128);
   if ((int64_t)p.smem_bytes > (int64_t)max_smem - kApplyStaticSmem) {
-    *why = "subdomain vector (" + std::to_string(3ll * p.rmax * p.vec_elem) + " B) plus staging ring (" +
-           std::to_string(p.ring_bytes) + " B) exceeds the " + std::to_string(max_smem) +
+    *why = "subdomain vector (" + std::to_string(3ll * p.rmax * p.vec_elem) + " B) exceeds the " +
+           std::to_string(max_smem) +
            " B of shared memory per block";
     return ILU0DD_ERR_SMEM;
   }
@@ -524,17 +530,22 @@ void pack_stream(const Plan& p, const std::vector<double>& F, const std::vector<
       for (int slot = 0; slot < w; ++slot)
         for (int t = 0; t < cnt[slot]; ++t) h[cpos++] = (uint16_t)(p.dd_col[blk[t][slot]] - c.row0);
       uint8_t* v = rec + d.voff;
+      // entry [a][c] of row t's block at (c * count + t) * 3 + a
       if (kind) {
-        for (int e = 0; e < 9; ++e)
+        for (int cc = 0; cc < 3; ++cc)
           for (int t = 0; t < n; ++t)
-            put_factor(v + ((int64_t)e * n + t) * fe, fe, invD[9 * (size_t)(c.row0 + rows[t]) + e]);
+            for (int a = 0; a < 3; ++a)
+              put_factor(v + (((int64_t)cc * n + t) * 3 + a) * fe, fe,
+                         invD[9 * (size_t)(c.row0 + rows[t]) + 3 * a + cc]);
         v += 9ll * n * fe;
       }
       for (int slot = 0; slot < w; ++slot) {
-        for (int e = 0; e < 9; ++e)
-          for (int t = 0; t < cnt[slot]; ++t)
-            put_factor(v + ((int64_t)e * cnt[slot] + t) * fe, fe, F[9 * (size_t)blk[t][slot] + e]);
-        v += 9ll * cnt[slot] * fe;
+        const int cs = cnt[slot];
+        for (int cc = 0; cc < 3; ++cc)
+          for (int t = 0; t < cs; ++t)
+            for (int a = 0; a < 3; ++a)
+              put_factor(v + (((int64_t)cc * cs + t) * 3 + a) * fe, fe, F[9 * (size_t)blk[t][slot] + 3 * a + cc]);
+        v += 9ll * cs * fe;
       }
     }
   });

@@ -71,15 +71,18 @@ def test_rejects_bad_patterns():
 
 
 def test_subdomain_shared_memory_limit():
-    """Section 4 sizes subdomains so their vector fits in shared memory: 8192 FP64 block
-    rows (192 KiB) plus the 32 KiB staging ring fit the 227 KiB of sm_103a; one more
-    z-layer does not."""
-    grid = (16, 16, 33)
+    """Section 4 sizes subdomains so their vector fits in shared memory. On sm_103a
+    (227 KiB per block) an FP64 subdomain of 9472 block rows (16x16x37 cells,
+    222 KiB) fits; one more z-layer does not. FP32-factor contexts keep an FP32
+    vector, so twice the rows fit."""
+    grid = (16, 16, 38)
     rp, col = synth.pattern(*grid)
     val = np.zeros((len(col), 3, 3))
-    assert g.workspace_size(rp, col, val, grid, (16, 16, 32)) > 0
+    assert g.workspace_size(rp, col, val, grid, (16, 16, 37)) > 0
     with pytest.raises(g.Ilu0DDError) as e:
-        g.workspace_size(rp, col, val, grid, (16, 16, 33))
+        g.workspace_size(rp, col, val, grid, (16, 16, 38))
     assert e.value.code == 3
-    # FP32 factors keep an FP32 vector: twice the rows fit
-    assert g.workspace_size(rp, col, val, grid, (16, 16, 33), factor_prec="f32") > 0
+    assert g.workspace_size(rp, col, val, grid, (16, 16, 38), factor_prec="f32") > 0
+    with pytest.raises(g.Ilu0DDError) as e:
+        g.workspace_size(rp, col, val, grid, (16, 16, 37), prefetch_bytes=100)
+    assert e.value.code == 1
