@@ -154,6 +154,26 @@ int ilu0_dd_spmv(const ilu0dd_ctx* ctx, const double* d_x, double* d_y, void* st
 int ilu0_dd_dot(const ilu0dd_ctx* ctx, const double* d_x, const double* d_y, double* d_result,
                 void* stream);
 
+/*
+ * Allocation-free variant of ilu0_dd_dot (the paper has no counterpart; it is
+ * a deployment convenience). *d_result = x . y over n_brows block rows
+ * (3*n_brows doubles, device pointers, same fixed summation order), without a
+ * context and without any allocation: the reduction scratch is a static
+ * device array of 16384 tile partials built into the library, present on
+ * every device that loads it until the process exits. It serves callers that
+ * cannot allocate device memory at the call site, e.g. code running under
+ * CUDA-graph capture or under a fixed device-memory budget. Limits and rules:
+ *  - n_brows <= 4,194,304 (16384 tiles of 256 block rows), else
+ *    ILU0DD_ERR_WORKSPACE;
+ *  - the first call on a device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture;
+ *  - all calls share the one array: calls that may overlap on the GPU (on
+ *    different streams, or from several threads) race and must be serialized
+ *    by the caller;
+ *  - asynchronous on `stream`; never calls cudaMalloc or cudaFree.
+ */
+int ilu0dd_dot_noalloc(const double* d_x, const double* d_y, int64_t n_brows, double* d_result, void* stream);
+
 /* Permute a device vector between numberings: dir 0 natural -> reordered,
  * dir 1 reordered -> natural (Algorithm 3's perm/iperm). Asynchronous. */
 int ilu0_dd_permute(const ilu0dd_ctx* ctx, const double* d_in, double* d_out, int dir, void* stream);

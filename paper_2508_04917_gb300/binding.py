@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "ilu0_dd_spmv": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_dot": ([vp, vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_permute": ([vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
+            "ilu0dd_dot_noalloc": ([vp, vp, i64, vp, vp], ctypes.c_int),
             "bicgstab_solve": ([vp, vp, vp, ctypes.POINTER(Info), vp], ctypes.c_int),
             "bicgstab_start": ([vp, vp, vp], ctypes.c_int),
             "bicgstab_iterate": ([vp, i32, vp, vp], ctypes.c_int),

@@ -656,6 +656,13 @@ cudaError_t launch_dot(const DevCtx& d, const double* x, const double* y, double
   return cudaGetLastError();
 }
 
+cudaError_t launch_dot_scratch(const double* x, const double* y, int32_t n_brows, double* partials, int64_t m,
+                               uint32_t* counter, double* out, cudaStream_t s) {
+  const int64_t ntiles = ((int64_t)n_brows + kDotTile - 1) / kDotTile;
+  dot_kernel<<<(unsigned)ntiles, kDotTile, 0, s>>>(x, y, n_brows, partials, m, counter, out);
+  return cudaGetLastError();
+}
+
 __global__ void permute_kernel(const double* in, double* out, const int32_t* map, int32_t N, int dir) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;

@@ -54,6 +54,12 @@ cudaError_t launch_residual(const DevCtx& d, int restart, cudaStream_t s);
 // *out = x . y in the fixed order.
 cudaError_t launch_dot(const DevCtx& d, const double* x, const double* y, double* out, cudaStream_t s);
 
+// Same dot product on caller-provided scratch: `partials` holds m doubles
+// (m = tiles padded to a power of two, entries past the tile count zero) and
+// `counter` one zeroed word; used by the allocation-free entry point.
+cudaError_t launch_dot_scratch(const double* x, const double* y, int32_t n_brows, double* partials, int64_t m,
+                               uint32_t* counter, double* out, cudaStream_t s);
+
 // dir 0: out = in[perm] (natural -> reordered); dir 1: inverse.
 cudaError_t launch_permute(const DevCtx& d, const double* in, double* out, int dir, cudaStream_t s);
 
