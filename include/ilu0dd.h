@@ -210,6 +210,36 @@ int bicgstab_start(ilu0dd_ctx* ctx, const double* d_b, void* stream);
 int bicgstab_iterate(ilu0dd_ctx* ctx, int32_t n, float* host_kernel_ms, void* stream);
 int bicgstab_state(ilu0dd_ctx* ctx, ilu0dd_info* info, void* stream);
 
+/*
+ * Batched BiCGSTAB over many independent systems (the batching pattern; the
+ * paper has no batched solver). Each system is an ilu0dd_ctx from
+ * ilu0_dd_setup (any grid and subdomain size, all with the same factor_prec,
+ * on the current device). ilu0dd_batch_create records them in a small device
+ * workspace (ilu0dd_batch_workspace_size bytes, 256-byte aligned, caller-owned)
+ * and keeps pointers to the contexts: they must outlive the batch, and a
+ * context must not be solved alone while a batched solve that uses it runs.
+ * opts supplies rtol, maxit (capped by each context's own maxit),
+ * check_every and use_graphs; the other fields are ignored.
+ *
+ * bicgstab_solve_batched runs Algorithm 1 on every system at once: each step
+ * of an iteration is ONE kernel launch over the work items of all systems
+ * ((system, subdomain) for the fused applies, (system, 256-row tile) for the
+ * SpMVs and vector steps, persistent grids), with per-system scalars on the
+ * device; systems that have converged are skipped by later launches; the
+ * iterations run as CUDA graphs of check_every iterations. d_b[i] and d_x[i]
+ * are device vectors of system i in its natural numbering (host arrays of
+ * nsys pointers); infos (optional, nsys entries) receives each system's
+ * result, as bicgstab_solve reports it. Returns ILU0DD_OK or the first
+ * failing system's status. Synchronizes `stream`.
+ */
+typedef struct ilu0dd_batch ilu0dd_batch;
+int ilu0dd_batch_workspace_size(ilu0dd_ctx* const* ctxs, int32_t nsys, size_t* bytes);
+int ilu0dd_batch_create(ilu0dd_ctx* const* ctxs, int32_t nsys, const ilu0dd_opts* opts, void* d_workspace,
+                        size_t ws_bytes, void* stream, ilu0dd_batch** out);
+int bicgstab_solve_batched(ilu0dd_batch* batch, const double* const* d_b, double* const* d_x, ilu0dd_info* infos,
+                           void* stream);
+void ilu0dd_batch_destroy(ilu0dd_batch* batch);
+
 /* Residual history of the last solve: hist[j] = ||r_j||/||b||, j = 0..iterations
  * (host destination of n doubles; copies min(n, iterations+1) entries). */
 int ilu0_dd_history(const ilu0dd_ctx* ctx, double* host_dst, int32_t n);

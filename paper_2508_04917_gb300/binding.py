@@ -95,6 +95,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "ilu0_dd_dot": ([vp, vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_permute": ([vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
             "ilu0dd_dot_noalloc": ([vp, vp, i64, vp, vp], ctypes.c_int),
+            "ilu0dd_batch_workspace_size": ([ctypes.POINTER(vp), i32, ctypes.POINTER(sz)], ctypes.c_int),
+            "ilu0dd_batch_create": ([ctypes.POINTER(vp), i32, ctypes.POINTER(Opts), vp, sz, vp, ctypes.POINTER(vp)],
+                                    ctypes.c_int),
+            "bicgstab_solve_batched": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(Info), vp],
+                                       ctypes.c_int),
+            "ilu0dd_batch_destroy": ([vp], None),
             "bicgstab_solve": ([vp, vp, vp, ctypes.POINTER(Info), vp], ctypes.c_int),
             "bicgstab_start": ([vp, vp, vp], ctypes.c_int),
             "bicgstab_iterate": ([vp, i32, vp, vp], ctypes.c_int),
@@ -313,3 +319,51 @@ class Ilu0DD:
         v = ctypes.c_int32(0)
         self._check(self._lib.ilu0_dd_device_error(self._ctx, ctypes.byref(v)), "ilu0_dd_device_error")
         return int(v.value)
+
+
+class Batch:
+    """Batched BiCGSTAB over several Ilu0DD contexts (one launch per step for all)."""
+
+    def __init__(self, ctxs, stream=None, **opts):
+        import torch
+        self._lib = load()
+        self.ctxs = list(ctxs)
+        arr = (ctypes.c_void_p * len(self.ctxs))(*[c._ctx for c in self.ctxs])
+        self._arr = arr
+        n = ctypes.c_size_t(0)
+        rc = self._lib.ilu0dd_batch_workspace_size(arr, len(self.ctxs), ctypes.byref(n))
+        if rc:
+            raise Ilu0DDError(rc, "ilu0dd_batch_workspace_size")
+        self.device = self.ctxs[0].device
+        self.workspace = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=self.device)
+        self.opts = default_opts(**opts)
+        b = ctypes.c_void_p()
+        rc = self._lib.ilu0dd_batch_create(arr, len(self.ctxs), ctypes.byref(self.opts),
+                                           ctypes.c_void_p(self.workspace.data_ptr()),
+                                           ctypes.c_size_t(self.workspace.numel()), _stream(stream), ctypes.byref(b))
+        if rc:
+            raise Ilu0DDError(rc, "ilu0dd_batch_create")
+        self._b = b
+
+    def solve(self, bs, xs=None, stream=None, check=True):
+        """bs: list of natural-order device vectors; returns (xs, [info dicts])."""
+        n = len(self.ctxs)
+        xs = [c._new() for c in self.ctxs] if xs is None else xs
+        pb = (ctypes.c_void_p * n)(*[_dptr(b, c.size, "b").value for b, c in zip(bs, self.ctxs)])
+        px = (ctypes.c_void_p * n)(*[_dptr(x, c.size, "x").value for x, c in zip(xs, self.ctxs)])
+        infos = (Info * n)()
+        rc = self._lib.bicgstab_solve_batched(self._b, pb, px, infos, _stream(stream))
+        if rc and check:
+            raise Ilu0DDError(rc, "bicgstab_solve_batched")
+        return xs, [i.as_dict() for i in infos]
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.ilu0dd_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libilu0dd.so")
-SOURCES = ["setup.cpp", "kernels.cu", "capi.cu", "noalloc.cu"]
+SOURCES = ["setup.cpp", "kernels.cu", "capi.cu", "batch.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_FLAGS = "-fPIC,-O2,-ffp-contract=off,-fno-fast-math,-Wall,-Wno-unused-function"
 

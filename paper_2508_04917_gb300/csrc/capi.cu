@@ -8,34 +8,10 @@
 #include <string>
 #include <vector>
 
-#include "internal.h"
-#include "kernels.h"
+#include "ctx.h"
 
 using namespace ilu0dd;
 
-struct ilu0dd_ctx {
-  Plan plan;
-  DevCtx dev{};
-  unsigned char* ws = nullptr;
-  size_t ws_bytes = 0;
-  int device = 0;
-  cudaStream_t own = nullptr;       // private stream of bicgstab_solve
-  cudaGraphExec_t graph = nullptr;  // opts.check_every iterations
-  int graph_iters = 0;
-  double rtol = 1e-8;
-  int32_t maxit = 10000;
-  int check_every = 8;
-  bool use_graphs = true;
-  bool trace = false;
-  double setup_s = 0.0;
-  int last_iterations = 0;
-  cudaError_t last_cuda = cudaSuccess;
-  std::string why;
-  std::vector<cudaEvent_t> events;  // bicgstab_iterate timing
-  // host copies for ilu0_dd_export (opts.keep_host)
-  std::vector<double> F, invD;
-  bool have_factors = false;
-};
 
 namespace {
 
@@ -196,30 +172,31 @@ int ilu0_dd_setup(const ilu0dd_bsr* A, const ilu0dd_geom* geom, const ilu0dd_opt
       return r;
     }
     DevCtx& d = c->dev;
-    d.stream = c->ws + L.stream;
-    d.cta = reinterpret_cast<const CtaDesc*>(c->ws + L.cta);
-    d.pieces = reinterpret_cast<const PieceDesc*>(c->ws + L.pieces);
-    d.nsub = p.nsub;
+    SysDesc& S = d.sd;
+    S.stream = c->ws + L.stream;
+    S.cta = reinterpret_cast<const CtaDesc*>(c->ws + L.cta);
+    S.pieces = reinterpret_cast<const PieceDesc*>(c->ws + L.pieces);
+    S.nsub = p.nsub;
+    S.prefetch_bytes = p.prefetch_bytes;
+    S.vec_bytes = (int)p.smem_bytes;
+    S.slice_off = reinterpret_cast<const int32_t*>(c->ws + L.sell_off);
+    S.sell_col = reinterpret_cast<const int32_t*>(c->ws + L.sell_col);
+    S.sell_val = reinterpret_cast<const double*>(c->ws + L.sell_val);
+    S.nslices = p.nslices;
+    S.perm = reinterpret_cast<const int32_t*>(c->ws + L.perm);
+    S.iperm = reinterpret_cast<const int32_t*>(c->ws + L.iperm);
+    S.N = p.N;
+    S.ntiles = p.ntiles;
+    S.ntiles_pow2 = p.ntiles_pow2;
+    for (int v = 0; v < kNumVec; ++v) S.vec[v] = reinterpret_cast<double*>(c->ws + L.vec[v]);
+    S.partials = reinterpret_cast<double*>(c->ws + L.partials);
+    S.counters = reinterpret_cast<uint32_t*>(c->ws + L.counters);
+    S.scal = reinterpret_cast<SolverScalars*>(c->ws + L.scal);
+    S.hist = reinterpret_cast<double*>(c->ws + L.hist);
+    S.err = reinterpret_cast<int32_t*>(c->ws + L.err);
     d.threads = p.threads;
-    d.prefetch_bytes = p.prefetch_bytes;
-    d.vec_bytes = (int)p.smem_bytes;
     d.factor_prec = o.factor_prec;
     d.smem_bytes = p.smem_bytes;
-    d.slice_off = reinterpret_cast<const int32_t*>(c->ws + L.sell_off);
-    d.sell_col = reinterpret_cast<const int32_t*>(c->ws + L.sell_col);
-    d.sell_val = reinterpret_cast<const double*>(c->ws + L.sell_val);
-    d.nslices = p.nslices;
-    d.perm = reinterpret_cast<const int32_t*>(c->ws + L.perm);
-    d.iperm = reinterpret_cast<const int32_t*>(c->ws + L.iperm);
-    d.N = p.N;
-    d.ntiles = p.ntiles;
-    d.ntiles_pow2 = p.ntiles_pow2;
-    for (int v = 0; v < kNumVec; ++v) d.vec[v] = reinterpret_cast<double*>(c->ws + L.vec[v]);
-    d.partials = reinterpret_cast<double*>(c->ws + L.partials);
-    d.counters = reinterpret_cast<uint32_t*>(c->ws + L.counters);
-    d.scal = reinterpret_cast<SolverScalars*>(c->ws + L.scal);
-    d.hist = reinterpret_cast<double*>(c->ws + L.hist);
-    d.err = reinterpret_cast<int32_t*>(c->ws + L.err);
     e = apply_configure(d);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -287,13 +264,13 @@ namespace {
 cudaError_t launch_iteration(const DevCtx& d, cudaStream_t s) {
   cudaError_t e;
   // p = r + beta (p - omega v); ph = M^-1 p
-  if ((e = launch_apply(d, kModeP, d.vec[kVecR], d.vec[kVecPh], s)) != cudaSuccess) return e;
+  if ((e = launch_apply(d, kModeP, d.sd.vec[kVecR], d.sd.vec[kVecPh], s)) != cudaSuccess) return e;
   // v = A ph; alpha = rho / (rh . v)
-  if ((e = launch_spmv(d, 1, d.vec[kVecPh], d.vec[kVecV], s)) != cudaSuccess) return e;
+  if ((e = launch_spmv(d, 1, d.sd.vec[kVecPh], d.sd.vec[kVecV], s)) != cudaSuccess) return e;
   // s = r - alpha v; sh = M^-1 s
-  if ((e = launch_apply(d, kModeS, d.vec[kVecR], d.vec[kVecSh], s)) != cudaSuccess) return e;
+  if ((e = launch_apply(d, kModeS, d.sd.vec[kVecR], d.sd.vec[kVecSh], s)) != cudaSuccess) return e;
   // t = A sh; omega = (t . s) / (t . t)
-  if ((e = launch_spmv(d, 2, d.vec[kVecSh], d.vec[kVecT], s)) != cudaSuccess) return e;
+  if ((e = launch_spmv(d, 2, d.sd.vec[kVecSh], d.sd.vec[kVecT], s)) != cudaSuccess) return e;
   // x += alpha ph + omega sh; r = s - omega t; convergence; beta
   return launch_update(d, s);
 }
@@ -323,7 +300,7 @@ cudaError_t run_chunk(ilu0dd_ctx* c) {
 }
 
 cudaError_t read_scalars(ilu0dd_ctx* c, SolverScalars* h) {
-  cudaError_t e = cudaMemcpyAsync(h, c->dev.scal, sizeof *h, cudaMemcpyDeviceToHost, c->own);
+  cudaError_t e = cudaMemcpyAsync(h, c->dev.sd.scal, sizeof *h, cudaMemcpyDeviceToHost, c->own);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->own);
   return e;
 }
@@ -347,7 +324,7 @@ int bicgstab_solve(ilu0dd_ctx* c, const double* d_b, double* d_x, ilu0dd_info* i
     }
     return ILU0DD_OK;
   }
-  CK(c, launch_permute(d, d_b, d.vec[kVecB], 0, c->own));
+  CK(c, launch_permute(d, d_b, d.sd.vec[kVecB], 0, c->own));
   CK(c, launch_init(d, c->rtol, c->maxit, c->own));
   CK(c, read_scalars(c, &h));
   if (h.status == ILU0DD_ERR_NONFINITE) status = ILU0DD_ERR_NONFINITE;
@@ -361,7 +338,7 @@ int bicgstab_solve(ilu0dd_ctx* c, const double* d_b, double* d_x, ilu0dd_info* i
       break;
     }
     // true residual r = b - A x
-    CK(c, launch_spmv(d, 0, d.vec[kVecX], d.vec[kVecT], c->own));
+    CK(c, launch_spmv(d, 0, d.sd.vec[kVecX], d.sd.vec[kVecT], c->own));
     CK(c, launch_residual(d, 0, c->own));
     CK(c, read_scalars(c, &h));
     if (h.rel_true < c->rtol) break;
@@ -376,8 +353,8 @@ int bicgstab_solve(ilu0dd_ctx* c, const double* d_b, double* d_x, ilu0dd_info* i
   }
   // a device wait that expired poisons the result
   int32_t derr = 0;
-  CK(c, cudaMemcpyAsync(&derr, d.err, sizeof derr, cudaMemcpyDeviceToHost, c->own));
-  CK(c, launch_permute(d, d.vec[kVecX], d_x, 1, c->own));
+  CK(c, cudaMemcpyAsync(&derr, d.sd.err, sizeof derr, cudaMemcpyDeviceToHost, c->own));
+  CK(c, launch_permute(d, d.sd.vec[kVecX], d_x, 1, c->own));
   CK(c, cudaStreamSynchronize(c->own));
   if (derr && status == ILU0DD_OK) status = ILU0DD_ERR_DEVICE_WAIT;
   c->last_iterations = h.iter;
@@ -400,7 +377,7 @@ int bicgstab_solve(ilu0dd_ctx* c, const double* d_b, double* d_x, ilu0dd_info* i
 int bicgstab_start(ilu0dd_ctx* c, const double* d_b, void* stream) {
   if (!c || (c->plan.N > 0 && !d_b)) return ILU0DD_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  CK(c, launch_permute(c->dev, d_b, c->dev.vec[kVecB], 0, s));
+  CK(c, launch_permute(c->dev, d_b, c->dev.sd.vec[kVecB], 0, s));
   CK(c, launch_init(c->dev, c->rtol, c->maxit, s));
   return ILU0DD_OK;
 }
@@ -422,13 +399,13 @@ int bicgstab_iterate(ilu0dd_ctx* c, int32_t n, float* host_kernel_ms, void* stre
   size_t k = 0;
   CK(c, cudaEventRecord(c->events[k++], s));
   for (int32_t i = 0; i < n; ++i) {
-    CK(c, launch_apply(d, kModeP, d.vec[kVecR], d.vec[kVecPh], s));
+    CK(c, launch_apply(d, kModeP, d.sd.vec[kVecR], d.sd.vec[kVecPh], s));
     CK(c, cudaEventRecord(c->events[k++], s));
-    CK(c, launch_spmv(d, 1, d.vec[kVecPh], d.vec[kVecV], s));
+    CK(c, launch_spmv(d, 1, d.sd.vec[kVecPh], d.sd.vec[kVecV], s));
     CK(c, cudaEventRecord(c->events[k++], s));
-    CK(c, launch_apply(d, kModeS, d.vec[kVecR], d.vec[kVecSh], s));
+    CK(c, launch_apply(d, kModeS, d.sd.vec[kVecR], d.sd.vec[kVecSh], s));
     CK(c, cudaEventRecord(c->events[k++], s));
-    CK(c, launch_spmv(d, 2, d.vec[kVecSh], d.vec[kVecT], s));
+    CK(c, launch_spmv(d, 2, d.sd.vec[kVecSh], d.sd.vec[kVecT], s));
     CK(c, cudaEventRecord(c->events[k++], s));
     CK(c, launch_update(d, s));
     CK(c, cudaEventRecord(c->events[k++], s));
@@ -442,7 +419,7 @@ int bicgstab_state(ilu0dd_ctx* c, ilu0dd_info* info, void* stream) {
   if (!c || !info) return ILU0DD_ERR_INVALID;
   SolverScalars h{};
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  CK(c, cudaMemcpyAsync(&h, c->dev.scal, sizeof h, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaMemcpyAsync(&h, c->dev.sd.scal, sizeof h, cudaMemcpyDeviceToHost, s));
   CK(c, cudaStreamSynchronize(s));
   std::memset(info, 0, sizeof *info);
   info->status = h.status;
@@ -457,7 +434,7 @@ int ilu0_dd_history(const ilu0dd_ctx* c, double* host_dst, int32_t n) {
   if (!c || !host_dst || n < 0) return ILU0DD_ERR_INVALID;
   int32_t m = std::min(n, c->last_iterations + 1);
   if (m <= 0) return ILU0DD_OK;
-  cudaError_t e = cudaMemcpy(host_dst, c->dev.hist, sizeof(double) * (size_t)m, cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpy(host_dst, c->dev.sd.hist, sizeof(double) * (size_t)m, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(const_cast<ilu0dd_ctx*>(c), e, "history copy");
   return ILU0DD_OK;
 }
@@ -529,8 +506,8 @@ int ilu0_dd_query(const ilu0dd_ctx* c, int what, int64_t* v) {
 int ilu0_dd_device_error(const ilu0dd_ctx* c, int32_t* code) {
   if (!c || !code) return ILU0DD_ERR_INVALID;
   cudaError_t e = cudaDeviceSynchronize();
-  if (e == cudaSuccess) e = cudaMemcpy(code, c->dev.err, sizeof *code, cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess) e = cudaMemset(c->dev.err, 0, sizeof *code);
+  if (e == cudaSuccess) e = cudaMemcpy(code, c->dev.sd.err, sizeof *code, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(c->dev.sd.err, 0, sizeof *code);
   if (e != cudaSuccess) return cuda_fail(const_cast<ilu0dd_ctx*>(c), e, "device error read");
   return ILU0DD_OK;
 }

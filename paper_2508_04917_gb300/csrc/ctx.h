@@ -1,0 +1,37 @@
+// Host-side context object behind the opaque ilu0dd_ctx of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.h"
+
+using namespace ilu0dd;
+
+struct ilu0dd_ctx {
+  Plan plan;
+  DevCtx dev{};
+  unsigned char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int device = 0;
+  cudaStream_t own = nullptr;       // private stream of bicgstab_solve
+  cudaGraphExec_t graph = nullptr;  // opts.check_every iterations
+  int graph_iters = 0;
+  double rtol = 1e-8;
+  int32_t maxit = 10000;
+  int check_every = 8;
+  bool use_graphs = true;
+  bool trace = false;
+  double setup_s = 0.0;
+  int last_iterations = 0;
+  cudaError_t last_cuda = cudaSuccess;
+  std::string why;
+  std::vector<cudaEvent_t> events;  // bicgstab_iterate timing
+  // host copies for ilu0_dd_export (opts.keep_host)
+  std::vector<double> F, invD;
+  bool have_factors = false;
+};
+

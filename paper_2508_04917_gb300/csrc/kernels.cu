@@ -1,15 +1,16 @@
 // sm_103a kernels of the hot path:
-//  - ildu0_apply: fused L -> D^-1 -> U~ sweep, one thread block per subdomain
-//    (Sections 4.2-4.4), subdomain vector in shared memory, factor records
-//    streamed through a ring of bulk copies (cp.async.bulk + mbarrier),
-//    vertex-centric rows (Section 4.2.3: one thread per block row, fixed
-//    per-row order, deterministic);
-//  - sell_spmv: y = A_p x on a sliced-ELL copy (coalesced, entry-major),
+//  - apply_block: fused L -> D^-1 -> U~ sweep of one subdomain (Sections
+//    4.2-4.4) by one thread block, subdomain vector in shared memory,
+//    vertex-centric rows (Section 4.2.3) with three threads per row;
+//  - spmv_block: y = A_p x on a sliced-ELL copy (coalesced, entry-major),
 //    with the dot products of Algorithm 1 fused into the epilogue;
 //  - update / init / residual / dot / permute: the BiCGSTAB vector steps.
+// Each step is a per-block device function; the single-system kernels call it
+// for their block, the batched kernels loop over a work list of
+// (system, block) items of many systems in one launch.
 // Dot products use one fixed order (per-row FMA, halving sums over 256-row
-// tiles and over tiles); the last block of each reduction kernel finishes the
-// sum and updates the device-resident scalars, so no scalar goes to the host
+// tiles and over tiles); the last block of each reduction finishes the sum and
+// updates the system's device-resident scalars, so no scalar goes to the host
 // inside an iteration.
 #include <cuda_runtime.h>
 
@@ -17,23 +18,6 @@
 #include "kernels.h"
 
 namespace ilu0dd {
-
-// ---------------------------------------------------------------------------
-// Fused ILDU0 apply
-// ---------------------------------------------------------------------------
-struct ApplyArgs {
-  const unsigned char* stream;
-  const CtaDesc* cta;
-  const PieceDesc* pieces;
-  const double* r;
-  double* z;
-  double* p;        // mode P: search direction, updated in place
-  double* s;        // mode S: s = r - alpha v (written)
-  const double* v;
-  const SolverScalars* scal;
-  int32_t* err;
-  int prefetch_bytes, vec_bytes;
-};
 
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
@@ -48,26 +32,39 @@ __device__ __forceinline__ int gu16(const unsigned char* p) {
   return (int)__ldg(reinterpret_cast<const unsigned short*>(p));
 }
 
+__device__ __forceinline__ double row_dot(const double* x, const double* y, int64_t i) {
+  return fma(x[3 * i + 2], y[3 * i + 2], fma(x[3 * i + 1], y[3 * i + 1], x[3 * i] * y[3 * i]));
+}
+
+__device__ __forceinline__ bool finite(double v) { return isfinite(v); }
+
+// ===========================================================================
+// Fused ILDU0 apply
+// ===========================================================================
+
 // One block per subdomain. The block reads its factor records straight from
-// global memory (coalesced: consecutive threads read consecutive values) while
-// thread 0 keeps bulk L2 prefetches (cp.async.bulk.prefetch.L2) a fixed
-// distance ahead in the subdomain's stream, so the per-level loads hit L2.
-// Shared memory holds only the subdomain vector. Three threads per row
-// (lane = 3 * (row in warp) + a, ten rows per warp); rows of one piece are
-// independent and pieces are separated by block barriers.
+// global memory (coalesced: consecutive threads read consecutive values; the
+// slot counts in the piece descriptor let every load of a level issue at
+// once) while thread 0 keeps bulk L2 prefetches (cp.async.bulk.prefetch.L2) a
+// fixed distance ahead in the subdomain's stream. Shared memory holds only the
+// subdomain vector. Three threads per row (lane = 3 * (row in warp) + a, ten
+// rows per warp); rows of one piece are independent and pieces are separated
+// by block barriers.
+// Modes: plain z = M^-1 r; P: p <- r + beta (p - omega v), z = M^-1 p;
+// S: s <- r - alpha v, z = M^-1 s. Modes P and S skip a finished solve.
 template <typename TF, int MODE>
-__global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks) ildu0_apply_kernel(ApplyArgs a) {
+__device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const double* r, double* z) {
   using TV = typename FactorLoad<TF>::compute;
   constexpr uint32_t FE = sizeof(TF);
   extern __shared__ __align__(128) unsigned char smem[];
 
-  if (MODE != kModePlain && a.scal->done) return;
-  const CtaDesc cd = a.cta[blockIdx.x];
+  if (MODE != kModePlain && S.scal->done) return;
+  const CtaDesc cd = S.cta[sub];
   const int tid = threadIdx.x;
   TV* y = reinterpret_cast<TV*>(smem);
-  const unsigned char* gs = a.stream + cd.stream_off;
+  const unsigned char* gs = S.stream + cd.stream_off;
   const uint32_t len = (uint32_t)cd.stream_len;
-  const uint32_t dist = (uint32_t)a.prefetch_bytes;
+  const uint32_t dist = (uint32_t)S.prefetch_bytes;
   constexpr uint32_t kPf = 16384;  // bytes per L2 prefetch instruction
   uint32_t pf_end = 0;             // prefetched prefix of the stream (thread 0)
   auto prefetch_upto = [&](uint32_t upto) {
@@ -84,18 +81,21 @@ __global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks) ildu0_apply
   const int64_t base = 3ll * cd.row0;
   const int nv = 3 * cd.nrows;
   double alpha = 0.0, beta = 0.0, omega = 0.0;
-  if (MODE == kModeP) { beta = a.scal->beta; omega = a.scal->omega; }
-  if (MODE == kModeS) alpha = a.scal->alpha;
+  if (MODE == kModeP) { beta = S.scal->beta; omega = S.scal->omega; }
+  if (MODE == kModeS) alpha = S.scal->alpha;
+  const double* vv = S.vec[kVecV];
+  double* pp = S.vec[kVecP];
+  double* ss = S.vec[kVecS];
   for (int e = tid; e < nv; e += blockDim.x) {
     double val;
     if (MODE == kModePlain) {
-      val = a.r[base + e];
+      val = r[base + e];
     } else if (MODE == kModeP) {
-      val = fma(beta, fma(-omega, a.v[base + e], a.p[base + e]), a.r[base + e]);
-      a.p[base + e] = val;
+      val = fma(beta, fma(-omega, vv[base + e], pp[base + e]), r[base + e]);
+      pp[base + e] = val;
     } else {
-      val = fma(-alpha, a.v[base + e], a.r[base + e]);
-      a.s[base + e] = val;
+      val = fma(-alpha, vv[base + e], r[base + e]);
+      ss[base + e] = val;
     }
     y[e] = (TV)val;
   }
@@ -107,10 +107,10 @@ __global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks) ildu0_apply
   const bool lane_ok = lane < 3 * kRowsPerWarp;
   const int base_lane = lane - comp;
 
-  PieceDesc nxt = cd.npieces > 0 ? a.pieces[cd.piece0] : PieceDesc{};
+  PieceDesc nxt = cd.npieces > 0 ? S.pieces[cd.piece0] : PieceDesc{};
   for (int k = 0; k < cd.npieces; ++k) {
     const PieceDesc pd = nxt;
-    if (k + 1 < cd.npieces) nxt = a.pieces[cd.piece0 + k + 1];
+    if (k + 1 < cd.npieces) nxt = S.pieces[cd.piece0 + k + 1];
     if (tid == 0) prefetch_upto(pd.off + dist);
     const int n = (int)(pd.meta & 0xFFFFu);
     const int w = (int)((pd.meta >> 16) & 0xFFu);
@@ -125,12 +125,12 @@ __global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks) ildu0_apply
       int col[kDescSlots];
       TV bv[kDescSlots][3];
       uint32_t c0 = 0;
-      int len = 0;
+      int nsl = 0;
 #pragma unroll
       for (int sl = 0; sl < kDescSlots; ++sl) {
         const uint32_t cs = pd.cnt[sl];  // 0 beyond w
         const bool has = active && sl < w && (uint32_t)trow < cs;
-        len += has;
+        nsl += has;
         col[sl] = has ? gu16(cb + 2 * (c0 + (uint32_t)trow)) : 0;
         const unsigned char* vo = vb + (9 * (size_t)c0 + (size_t)(3 * trow + comp)) * FE;
         const size_t cstride = 3 * (size_t)cs * FE;
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks) ildu0_apply
       if (active) {
 #pragma unroll
         for (int sl = 0; sl < kDescSlots; ++sl) {
-          if (sl < len) {
+          if (sl < nsl) {
             const int cl = col[sl];
             acc = fma(-bv[sl][0], y[3 * cl], acc);
             acc = fma(-bv[sl][1], y[3 * cl + 1], acc);
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks) ildu0_apply
           }
         }
         // rows with more than kDescSlots blocks (general patterns): remaining slots
-        if (w > kDescSlots && len == kDescSlots) {
+        if (w > kDescSlots && nsl == kDescSlots) {
           for (int sl = kDescSlots; sl < w; ++sl) {
             const uint32_t cs = (uint32_t)gu16(rec + 2 * sl);
             if ((uint32_t)trow >= cs) break;
@@ -187,13 +187,34 @@ __global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks) ildu0_apply
     }
     __syncthreads();
   }
-  for (int e = tid; e < nv; e += blockDim.x) a.z[base + e] = (double)y[e];
+  for (int e = tid; e < nv; e += blockDim.x) z[base + e] = (double)y[e];
+}
+
+template <typename TF, int MODE>
+__global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
+    ildu0_apply_kernel(SysDesc S, const double* r, double* z) {
+  apply_block<TF, MODE>(S, blockIdx.x, r, z);
+}
+
+// Batched apply (modes P and S): persistent blocks walk (system, subdomain) items.
+template <typename TF, int MODE>
+__global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
+    ildu0_apply_batched(const SysDesc* __restrict__ sys, const BatchItem* __restrict__ items, int64_t nitems) {
+  for (int64_t i = blockIdx.x; i < nitems; i += gridDim.x) {
+    const BatchItem it = items[i];
+    const SysDesc& S = sys[it.sys];
+    apply_block<TF, MODE>(S, it.local, S.vec[kVecR], S.vec[MODE == kModeP ? kVecPh : kVecSh]);
+    __syncthreads();  // the next item reuses shared memory
+  }
 }
 
 template <typename TF, int MODE>
 static cudaError_t configure_one(size_t smem) {
-  return cudaFuncSetAttribute(ildu0_apply_kernel<TF, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(ildu0_apply_kernel<TF, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e == cudaSuccess && MODE != kModePlain)
+    e = cudaFuncSetAttribute(ildu0_apply_batched<TF, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e;
 }
 
 // The attribute is a per-kernel permission shared by every context in the
@@ -205,7 +226,7 @@ cudaError_t apply_configure(const DevCtx& d) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  const size_t smem = (size_t)optin - kApplyStaticSmem;  // the kernel's static shared memory
+  const size_t smem = (size_t)optin - kApplyStaticSmem;  // minus the kernel's static shared memory
   auto acc = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
   acc(configure_one<double, kModePlain>(smem));
   acc(configure_one<double, kModeP>(smem));
@@ -220,53 +241,76 @@ cudaError_t apply_configure(const DevCtx& d) {
 }
 
 template <typename TF>
-static cudaError_t launch_apply_t(const DevCtx& d, int mode, const ApplyArgs& a, cudaStream_t s) {
-  dim3 grid(d.nsub), block(d.threads);
+static cudaError_t launch_apply_t(const DevCtx& d, int mode, const double* r, double* z, cudaStream_t s) {
+  dim3 grid(d.sd.nsub), block(d.threads);
   if (mode == kModePlain)
-    ildu0_apply_kernel<TF, kModePlain><<<grid, block, d.smem_bytes, s>>>(a);
+    ildu0_apply_kernel<TF, kModePlain><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z);
   else if (mode == kModeP)
-    ildu0_apply_kernel<TF, kModeP><<<grid, block, d.smem_bytes, s>>>(a);
+    ildu0_apply_kernel<TF, kModeP><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z);
   else
-    ildu0_apply_kernel<TF, kModeS><<<grid, block, d.smem_bytes, s>>>(a);
+    ildu0_apply_kernel<TF, kModeS><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z);
   return cudaGetLastError();
 }
 
 cudaError_t launch_apply(const DevCtx& d, int mode, const double* r, double* z, cudaStream_t s) {
-  if (d.nsub == 0) return cudaSuccess;
-  ApplyArgs a;
-  a.stream = d.stream;
-  a.cta = d.cta;
-  a.pieces = d.pieces;
-  a.r = r;
-  a.z = z;
-  a.p = d.vec[kVecP];
-  a.s = d.vec[kVecS];
-  a.v = d.vec[kVecV];
-  a.scal = d.scal;
-  a.err = d.err;
-  a.prefetch_bytes = d.prefetch_bytes;
-  a.vec_bytes = d.vec_bytes;
-  if (d.factor_prec == ILU0DD_F64) return launch_apply_t<double>(d, mode, a, s);
-  if (d.factor_prec == ILU0DD_F32) return launch_apply_t<float>(d, mode, a, s);
-  return launch_apply_t<bf16s>(d, mode, a, s);
+  if (d.sd.nsub == 0) return cudaSuccess;
+  if (d.factor_prec == ILU0DD_F64) return launch_apply_t<double>(d, mode, r, z, s);
+  if (d.factor_prec == ILU0DD_F32) return launch_apply_t<float>(d, mode, r, z, s);
+  return launch_apply_t<bf16s>(d, mode, r, z, s);
 }
 
-// ---------------------------------------------------------------------------
+template <typename TF>
+static cudaError_t launch_apply_batched_t(const SysDesc* sys, const BatchItem* items, int64_t nitems, int mode,
+                                          int threads, size_t smem, int grid, cudaStream_t s) {
+  if (mode == kModeP)
+    ildu0_apply_batched<TF, kModeP><<<grid, threads, smem, s>>>(sys, items, nitems);
+  else
+    ildu0_apply_batched<TF, kModeS><<<grid, threads, smem, s>>>(sys, items, nitems);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int mode,
+                                 int factor_prec, int threads, size_t smem, int grid, cudaStream_t s) {
+  if (nitems == 0) return cudaSuccess;
+  if (factor_prec == ILU0DD_F64)
+    return launch_apply_batched_t<double>(sys, items, nitems, mode, threads, smem, grid, s);
+  if (factor_prec == ILU0DD_F32)
+    return launch_apply_batched_t<float>(sys, items, nitems, mode, threads, smem, grid, s);
+  return launch_apply_batched_t<bf16s>(sys, items, nitems, mode, threads, smem, grid, s);
+}
+
+int apply_blocks_per_sm(int factor_prec, int threads, size_t smem) {
+  int n = 0;
+  cudaError_t e;
+  if (factor_prec == ILU0DD_F64)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ildu0_apply_batched<double, kModeP>, threads, smem);
+  else if (factor_prec == ILU0DD_F32)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ildu0_apply_batched<float, kModeP>, threads, smem);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ildu0_apply_batched<bf16s, kModeP>, threads, smem);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n > 0 ? n : 1;
+}
+
+// ===========================================================================
 // Reductions: last-block completion
-// ---------------------------------------------------------------------------
+// ===========================================================================
 
 // Write this tile's partials; returns true in every thread of the block that
-// arrived last (it then owns the final reduction).
+// completed the `count`-th tile of the reduction (it owns the final sum).
 template <int NV>
 __device__ __forceinline__ bool publish_partials(const double (&q)[NV], double* partials, int64_t stride,
-                                                 uint32_t* counter) {
+                                                 int64_t tile, int64_t count, uint32_t* counter) {
   __shared__ unsigned int s_last;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) partials[v * stride + blockIdx.x] = q[v];
+    for (int v = 0; v < NV; ++v) partials[v * stride + tile] = q[v];
     __threadfence();
     const unsigned int prev = atomicAdd(counter, 1u);
-    s_last = prev == gridDim.x - 1;
+    s_last = prev == (unsigned int)(count - 1);
   }
   __syncthreads();
   const bool last = s_last != 0;
@@ -283,48 +327,27 @@ __device__ __forceinline__ void finish_sum(double* partials, int64_t stride, int
   final_halving_sum<NV>(part, m, out, buf);
 }
 
-__device__ __forceinline__ double row_dot(const double* x, const double* y, int64_t i) {
-  return fma(x[3 * i + 2], y[3 * i + 2], fma(x[3 * i + 1], y[3 * i + 1], x[3 * i] * y[3 * i]));
-}
-
-__device__ __forceinline__ bool finite(double v) { return isfinite(v); }
-
-// ---------------------------------------------------------------------------
+// ===========================================================================
 // SpMV (sliced ELL), kinds: 0 plain, 1 (rh . v) -> alpha, 2 (t . s), (t . t) -> omega
-// ---------------------------------------------------------------------------
-struct SpmvArgs {
-  const int32_t* slice_off;
-  const int32_t* cols;
-  const double* vals;
-  int64_t nslices;
-  int32_t N;
-  const double* x;
-  double* y;
-  const double* w;       // kind 1: rh, kind 2: s
-  double* partials;
-  int64_t stride, m;
-  uint32_t* counter;
-  SolverScalars* scal;
-};
-
+// ===========================================================================
 template <int KIND>
-__global__ void __launch_bounds__(kDotTile) sell_spmv_kernel(SpmvArgs a) {
-  if (KIND != 0 && a.scal->done) return;
+__device__ __forceinline__ void spmv_block(const SysDesc& S, int64_t tile, const double* x, double* y) {
+  if (KIND != 0 && S.scal->done) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t slice = (int64_t)blockIdx.x * (kDotTile / kSlice) + warp;
+  const int64_t slice = tile * (kDotTile / kSlice) + warp;
   const int64_t row = slice * kSlice + lane;
   double y0 = 0.0, y1 = 0.0, y2 = 0.0;
-  if (slice < a.nslices) {
-    const int64_t so = a.slice_off[slice];
-    const int w = a.slice_off[slice + 1] - (int32_t)so;
-    const int32_t* cp = a.cols + so * kSlice + lane;
-    const double* vp = a.vals + so * 9 * kSlice + lane;
+  if (slice < S.nslices) {
+    const int64_t so = S.slice_off[slice];
+    const int w = S.slice_off[slice + 1] - (int32_t)so;
+    const int32_t* cp = S.sell_col + so * kSlice + lane;
+    const double* vp = S.sell_val + so * 9 * kSlice + lane;
     for (int sl = 0; sl < w; ++sl) {
       const int c = __ldg(cp + sl * kSlice);
       double b[9];
 #pragma unroll
       for (int e = 0; e < 9; ++e) b[e] = __ldg(vp + (sl * 9 + e) * kSlice);
-      const double x0 = a.x[3ll * c], x1 = a.x[3ll * c + 1], x2 = a.x[3ll * c + 2];
+      const double x0 = x[3ll * c], x1 = x[3ll * c + 1], x2 = x[3ll * c + 2];
       y0 = fma(b[0], x0, y0);
       y1 = fma(b[3], x0, y1);
       y2 = fma(b[6], x0, y2);
@@ -335,108 +358,120 @@ __global__ void __launch_bounds__(kDotTile) sell_spmv_kernel(SpmvArgs a) {
       y1 = fma(b[5], x2, y1);
       y2 = fma(b[8], x2, y2);
     }
-    if (row < a.N) {
-      a.y[3 * row] = y0;
-      a.y[3 * row + 1] = y1;
-      a.y[3 * row + 2] = y2;
+    if (row < S.N) {
+      y[3 * row] = y0;
+      y[3 * row + 1] = y1;
+      y[3 * row + 2] = y2;
     }
   }
   if (KIND == 0) return;
   __shared__ double buf[2][kDotTile];
-  const bool in = row < a.N;
+  const bool in = row < S.N;
+  const int64_t m = S.ntiles_pow2;
   if (KIND == 1) {
-    double q[1] = {in ? fma(a.w[3 * row + 2], y2, fma(a.w[3 * row + 1], y1, a.w[3 * row] * y0)) : 0.0};
+    const double* w = S.vec[kVecRh];
+    double q[1] = {in ? fma(w[3 * row + 2], y2, fma(w[3 * row + 1], y1, w[3 * row] * y0)) : 0.0};
     tile_halving_sum<1>(q, buf);
-    if (!publish_partials<1>(q, a.partials, a.stride, a.counter)) return;
+    uint32_t* counter = S.counters + kCntSpmvV;
+    if (!publish_partials<1>(q, S.partials, m, tile, S.ntiles, counter)) return;
     double out[1];
-    finish_sum<1>(a.partials, a.stride, a.m, out, buf);
+    finish_sum<1>(S.partials, m, m, out, buf);
     if (threadIdx.x == 0) {
-      SolverScalars* S = a.scal;
+      SolverScalars* sc = S.scal;
       const double rv = out[0];
-      S->rv = rv;
+      sc->rv = rv;
       if (rv == 0.0 || !finite(rv)) {
-        S->status = ILU0DD_ERR_BREAKDOWN;
-        S->done = 1;
+        sc->status = ILU0DD_ERR_BREAKDOWN;
+        sc->done = 1;
       } else {
-        S->alpha = S->rho / rv;
+        sc->alpha = sc->rho / rv;
       }
-      *a.counter = 0;
+      *counter = 0;
     }
   } else {
     // (t . s) and (t . t), t = y
-    double q[2] = {in ? fma(y2, a.w[3 * row + 2], fma(y1, a.w[3 * row + 1], y0 * a.w[3 * row])) : 0.0,
+    const double* w = S.vec[kVecS];
+    double q[2] = {in ? fma(y2, w[3 * row + 2], fma(y1, w[3 * row + 1], y0 * w[3 * row])) : 0.0,
                    in ? fma(y2, y2, fma(y1, y1, y0 * y0)) : 0.0};
     tile_halving_sum<2>(q, buf);
-    if (!publish_partials<2>(q, a.partials, a.stride, a.counter)) return;
+    uint32_t* counter = S.counters + kCntSpmvT;
+    if (!publish_partials<2>(q, S.partials, m, tile, S.ntiles, counter)) return;
     double out[2];
-    finish_sum<2>(a.partials, a.stride, a.m, out, buf);
+    finish_sum<2>(S.partials, m, m, out, buf);
     if (threadIdx.x == 0) {
-      SolverScalars* S = a.scal;
-      S->ts = out[0];
-      S->tt = out[1];
-      S->omega = out[1] == 0.0 ? 0.0 : out[0] / out[1];
-      *a.counter = 0;
+      SolverScalars* sc = S.scal;
+      sc->ts = out[0];
+      sc->tt = out[1];
+      sc->omega = out[1] == 0.0 ? 0.0 : out[0] / out[1];
+      *counter = 0;
     }
   }
 }
 
+template <int KIND>
+__global__ void __launch_bounds__(kDotTile) sell_spmv_kernel(SysDesc S, const double* x, double* y) {
+  spmv_block<KIND>(S, blockIdx.x, x, y);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kDotTile)
+    sell_spmv_batched(const SysDesc* __restrict__ sys, const BatchItem* __restrict__ items, int64_t nitems) {
+  for (int64_t i = blockIdx.x; i < nitems; i += gridDim.x) {
+    const BatchItem it = items[i];
+    const SysDesc& S = sys[it.sys];
+    if (KIND == 0)
+      spmv_block<0>(S, it.local, S.vec[kVecX], S.vec[kVecT]);
+    else if (KIND == 1)
+      spmv_block<1>(S, it.local, S.vec[kVecPh], S.vec[kVecV]);
+    else
+      spmv_block<2>(S, it.local, S.vec[kVecSh], S.vec[kVecT]);
+    __syncthreads();
+  }
+}
+
 cudaError_t launch_spmv(const DevCtx& d, int kind, const double* x, double* y, cudaStream_t s) {
-  if (d.N == 0) return cudaSuccess;
-  SpmvArgs a;
-  a.slice_off = d.slice_off;
-  a.cols = d.sell_col;
-  a.vals = d.sell_val;
-  a.nslices = d.nslices;
-  a.N = d.N;
-  a.x = x;
-  a.y = y;
-  a.w = kind == 1 ? d.vec[kVecRh] : d.vec[kVecS];
-  a.partials = d.partials;
-  a.stride = d.ntiles_pow2;
-  a.m = d.ntiles_pow2;
-  a.counter = d.counters + (kind == 1 ? kCntSpmvV : kCntSpmvT);
-  a.scal = d.scal;
-  dim3 grid((unsigned)d.ntiles), block(kDotTile);
+  if (d.sd.N == 0) return cudaSuccess;
+  dim3 grid((unsigned)d.sd.ntiles), block(kDotTile);
   if (kind == 0)
-    sell_spmv_kernel<0><<<grid, block, 0, s>>>(a);
+    sell_spmv_kernel<0><<<grid, block, 0, s>>>(d.sd, x, y);
   else if (kind == 1)
-    sell_spmv_kernel<1><<<grid, block, 0, s>>>(a);
+    sell_spmv_kernel<1><<<grid, block, 0, s>>>(d.sd, x, y);
   else
-    sell_spmv_kernel<2><<<grid, block, 0, s>>>(a);
+    sell_spmv_kernel<2><<<grid, block, 0, s>>>(d.sd, x, y);
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
+cudaError_t launch_spmv_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int kind, int grid,
+                                cudaStream_t s) {
+  if (nitems == 0) return cudaSuccess;
+  if (kind == 0)
+    sell_spmv_batched<0><<<grid, kDotTile, 0, s>>>(sys, items, nitems);
+  else if (kind == 1)
+    sell_spmv_batched<1><<<grid, kDotTile, 0, s>>>(sys, items, nitems);
+  else
+    sell_spmv_batched<2><<<grid, kDotTile, 0, s>>>(sys, items, nitems);
+  return cudaGetLastError();
+}
+
+// ===========================================================================
 // Vector steps
-// ---------------------------------------------------------------------------
-struct VecArgs {
-  double* v[kNumVec];
-  int32_t N;
-  double* partials;
-  int64_t stride, m;
-  uint32_t* counters;
-  SolverScalars* scal;
-  double* hist;
-  double rtol;
-  int32_t maxit;
-  int restart;
-};
+// ===========================================================================
 
 // x += alpha ph + omega sh; r = s - omega t; then ||r||/||b|| and rho.
-__global__ void __launch_bounds__(kDotTile) update_kernel(VecArgs a) {
-  SolverScalars* S = a.scal;
-  if (S->done) return;
-  const int64_t i = (int64_t)blockIdx.x * kDotTile + threadIdx.x;
-  const double alpha = S->alpha, omega = S->omega;
+__device__ __forceinline__ void update_block(const SysDesc& S, int64_t tile) {
+  SolverScalars* sc = S.scal;
+  if (sc->done) return;
+  const int64_t i = tile * kDotTile + threadIdx.x;
+  const double alpha = sc->alpha, omega = sc->omega;
   double q[2] = {0.0, 0.0};
-  if (i < a.N) {
-    double* x = a.v[kVecX];
-    double* r = a.v[kVecR];
-    const double* ph = a.v[kVecPh];
-    const double* sh = a.v[kVecSh];
-    const double* sv = a.v[kVecS];
-    const double* t = a.v[kVecT];
-    const double* rh = a.v[kVecRh];
+  if (i < S.N) {
+    double* x = S.vec[kVecX];
+    double* r = S.vec[kVecR];
+    const double* ph = S.vec[kVecPh];
+    const double* sh = S.vec[kVecSh];
+    const double* sv = S.vec[kVecS];
+    const double* t = S.vec[kVecT];
+    const double* rh = S.vec[kVecRh];
     double rr[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -450,197 +485,235 @@ __global__ void __launch_bounds__(kDotTile) update_kernel(VecArgs a) {
   }
   __shared__ double buf[2][kDotTile];
   tile_halving_sum<2>(q, buf);
-  uint32_t* counter = a.counters + kCntUpdate;
-  if (!publish_partials<2>(q, a.partials, a.stride, counter)) return;
+  uint32_t* counter = S.counters + kCntUpdate;
+  if (!publish_partials<2>(q, S.partials, S.ntiles_pow2, tile, S.ntiles, counter)) return;
   double out[2];
-  finish_sum<2>(a.partials, a.stride, a.m, out, buf);
+  finish_sum<2>(S.partials, S.ntiles_pow2, S.ntiles_pow2, out, buf);
   if (threadIdx.x == 0) {
     const double rr = out[0], rho_new = out[1];
-    const double rel = sqrt(rr) / sqrt(S->bb);
-    S->rr = rr;
-    S->rhr = rho_new;
-    S->rel = rel;
-    S->iter += 1;
-    if (S->iter <= S->maxit) a.hist[S->iter] = rel;
+    const double rel = sqrt(rr) / sqrt(sc->bb);
+    sc->rr = rr;
+    sc->rhr = rho_new;
+    sc->rel = rel;
+    sc->iter += 1;
+    if (sc->iter <= sc->maxit) S.hist[sc->iter] = rel;
     if (!finite(rel)) {
-      S->status = ILU0DD_ERR_BREAKDOWN;
-      S->done = 1;
-    } else if (rel < S->rtol) {
-      S->converged = 1;
-      S->done = 1;
-    } else if (S->iter >= S->maxit) {
-      S->status = ILU0DD_ERR_NOT_CONVERGED;
-      S->done = 1;
+      sc->status = ILU0DD_ERR_BREAKDOWN;
+      sc->done = 1;
+    } else if (rel < sc->rtol) {
+      sc->converged = 1;
+      sc->done = 1;
+    } else if (sc->iter >= sc->maxit) {
+      sc->status = ILU0DD_ERR_NOT_CONVERGED;
+      sc->done = 1;
     } else if (rho_new == 0.0 || omega == 0.0 || !finite(rho_new)) {
-      S->status = ILU0DD_ERR_BREAKDOWN;
-      S->done = 1;
+      sc->status = ILU0DD_ERR_BREAKDOWN;
+      sc->done = 1;
     } else {
-      S->beta = (alpha / omega) * (rho_new / S->rho);
-      S->rho = rho_new;
+      sc->beta = (alpha / omega) * (rho_new / sc->rho);
+      sc->rho = rho_new;
     }
     *counter = 0;
   }
 }
 
-cudaError_t launch_update(const DevCtx& d, cudaStream_t s) {
-  if (d.N == 0) return cudaSuccess;
-  VecArgs a{};
-  for (int v = 0; v < kNumVec; ++v) a.v[v] = d.vec[v];
-  a.N = d.N;
-  a.partials = d.partials;
-  a.stride = d.ntiles_pow2;
-  a.m = d.ntiles_pow2;
-  a.counters = d.counters;
-  a.scal = d.scal;
-  a.hist = d.hist;
-  update_kernel<<<(unsigned)d.ntiles, kDotTile, 0, s>>>(a);
-  return cudaGetLastError();
-}
-
 // x = 0, r = rh = p = b, v = 0; bb = rho = (b . b).
-__global__ void __launch_bounds__(kDotTile) init_kernel(VecArgs a) {
-  const int64_t i = (int64_t)blockIdx.x * kDotTile + threadIdx.x;
+__device__ __forceinline__ void init_block(const SysDesc& S, int64_t tile, double rtol, int32_t maxit) {
+  const int64_t i = tile * kDotTile + threadIdx.x;
   double q[1] = {0.0};
-  if (i < a.N) {
-    const double* b = a.v[kVecB];
+  if (i < S.N) {
+    const double* b = S.vec[kVecB];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const int64_t e = 3 * i + c;
       const double be = b[e];
-      a.v[kVecX][e] = 0.0;
-      a.v[kVecR][e] = be;
-      a.v[kVecRh][e] = be;
-      a.v[kVecP][e] = be;
-      a.v[kVecV][e] = 0.0;
+      S.vec[kVecX][e] = 0.0;
+      S.vec[kVecR][e] = be;
+      S.vec[kVecRh][e] = be;
+      S.vec[kVecP][e] = be;
+      S.vec[kVecV][e] = 0.0;
     }
     q[0] = row_dot(b, b, i);
   }
   __shared__ double buf[1][kDotTile];
   tile_halving_sum<1>(q, buf);
-  uint32_t* counter = a.counters + kCntInit;
-  if (!publish_partials<1>(q, a.partials, a.stride, counter)) return;
+  uint32_t* counter = S.counters + kCntInit;
+  if (!publish_partials<1>(q, S.partials, S.ntiles_pow2, tile, S.ntiles, counter)) return;
   double out[1];
-  finish_sum<1>(a.partials, a.stride, a.m, out, buf);
+  finish_sum<1>(S.partials, S.ntiles_pow2, S.ntiles_pow2, out, buf);
   if (threadIdx.x == 0) {
-    SolverScalars* S = a.scal;
+    SolverScalars* sc = S.scal;
     const double bb = out[0];
-    S->bb = bb;
-    S->rho = bb;
-    S->alpha = S->beta = S->omega = 0.0;
-    S->rv = S->ts = S->tt = S->rr = S->rhr = 0.0;
-    S->rel = 1.0;
-    S->rel_true = 1.0;
-    S->rtol = a.rtol;
-    S->maxit = a.maxit;
-    S->iter = 0;
-    S->converged = 0;
-    S->status = ILU0DD_OK;
-    S->done = 0;
-    a.hist[0] = 1.0;
+    sc->bb = bb;
+    sc->rho = bb;
+    sc->alpha = sc->beta = sc->omega = 0.0;
+    sc->rv = sc->ts = sc->tt = sc->rr = sc->rhr = 0.0;
+    sc->rel = 1.0;
+    sc->rel_true = 1.0;
+    sc->rtol = rtol;
+    sc->maxit = maxit;
+    sc->iter = 0;
+    sc->converged = 0;
+    sc->status = ILU0DD_OK;
+    sc->done = 0;
+    S.hist[0] = 1.0;
     if (!finite(bb)) {
-      S->status = ILU0DD_ERR_NONFINITE;
-      S->done = 1;
+      sc->status = ILU0DD_ERR_NONFINITE;
+      sc->done = 1;
     } else if (bb == 0.0) {
-      S->converged = 1;
-      S->rel = 0.0;
-      S->rel_true = 0.0;
-      S->done = 1;
-    } else if (a.maxit <= 0) {
-      S->status = ILU0DD_ERR_NOT_CONVERGED;
-      S->done = 1;
+      sc->converged = 1;
+      sc->rel = 0.0;
+      sc->rel_true = 0.0;
+      sc->done = 1;
+    } else if (maxit <= 0) {
+      sc->status = ILU0DD_ERR_NOT_CONVERGED;
+      sc->done = 1;
     }
     *counter = 0;
   }
 }
 
-cudaError_t launch_init(const DevCtx& d, double rtol, int32_t maxit, cudaStream_t s) {
-  if (d.N == 0) return cudaSuccess;
-  VecArgs a{};
-  for (int v = 0; v < kNumVec; ++v) a.v[v] = d.vec[v];
-  a.N = d.N;
-  a.partials = d.partials;
-  a.stride = d.ntiles_pow2;
-  a.m = d.ntiles_pow2;
-  a.counters = d.counters;
-  a.scal = d.scal;
-  a.hist = d.hist;
-  a.rtol = rtol;
-  a.maxit = maxit;
-  init_kernel<<<(unsigned)d.ntiles, kDotTile, 0, s>>>(a);
-  return cudaGetLastError();
-}
-
-// restart 0: r = b - t (t = A x), rel_true = ||r||/||b||.
-// restart 1: continue from r: rh = p = r, v = 0, rho = (r . r), done = 0.
-__global__ void __launch_bounds__(kDotTile) residual_kernel(VecArgs a) {
-  const int64_t i = (int64_t)blockIdx.x * kDotTile + threadIdx.x;
-  SolverScalars* S = a.scal;
-  if (a.restart) {
-    if (i < a.N) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const int64_t e = 3 * i + c;
-        const double re = a.v[kVecR][e];
-        a.v[kVecRh][e] = re;
-        a.v[kVecP][e] = re;
-        a.v[kVecV][e] = 0.0;
-      }
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      S->rho = S->rr;
-      S->alpha = S->beta = S->omega = 0.0;
-      S->converged = 0;
-      S->done = 0;
-    }
-    return;
-  }
+// r = b - t (t = A x computed before), rel_true = ||r||/||b||.
+__device__ __forceinline__ void residual_block(const SysDesc& S, int64_t tile) {
+  const int64_t i = tile * kDotTile + threadIdx.x;
   double q[1] = {0.0};
-  if (i < a.N) {
+  if (i < S.N) {
     double rr[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const int64_t e = 3 * i + c;
-      rr[c] = a.v[kVecB][e] - a.v[kVecT][e];
-      a.v[kVecR][e] = rr[c];
+      rr[c] = S.vec[kVecB][e] - S.vec[kVecT][e];
+      S.vec[kVecR][e] = rr[c];
     }
     q[0] = fma(rr[2], rr[2], fma(rr[1], rr[1], rr[0] * rr[0]));
   }
   __shared__ double buf[1][kDotTile];
   tile_halving_sum<1>(q, buf);
-  uint32_t* counter = a.counters + kCntResid;
-  if (!publish_partials<1>(q, a.partials, a.stride, counter)) return;
+  uint32_t* counter = S.counters + kCntResid;
+  if (!publish_partials<1>(q, S.partials, S.ntiles_pow2, tile, S.ntiles, counter)) return;
   double out[1];
-  finish_sum<1>(a.partials, a.stride, a.m, out, buf);
+  finish_sum<1>(S.partials, S.ntiles_pow2, S.ntiles_pow2, out, buf);
   if (threadIdx.x == 0) {
-    S->rr = out[0];
-    S->rel_true = sqrt(out[0]) / sqrt(S->bb);
+    const double bb = S.scal->bb;
+    S.scal->rr = out[0];
+    // b = 0: x = 0 is exact (rel_true 0); otherwise ||r|| / ||b||
+    S.scal->rel_true = bb > 0.0 ? sqrt(out[0]) / sqrt(bb) : (out[0] == 0.0 ? 0.0 : HUGE_VAL);
     *counter = 0;
   }
 }
 
-cudaError_t launch_residual(const DevCtx& d, int restart, cudaStream_t s) {
-  if (d.N == 0) return cudaSuccess;
-  VecArgs a{};
-  for (int v = 0; v < kNumVec; ++v) a.v[v] = d.vec[v];
-  a.N = d.N;
-  a.partials = d.partials;
-  a.stride = d.ntiles_pow2;
-  a.m = d.ntiles_pow2;
-  a.counters = d.counters;
-  a.scal = d.scal;
-  a.restart = restart;
-  residual_kernel<<<(unsigned)d.ntiles, kDotTile, 0, s>>>(a);
+// Continue from r: rh = p = r, v = 0, rho = (r . r) of the true residual, done = 0.
+__device__ __forceinline__ void restart_block(const SysDesc& S, int64_t tile) {
+  const int64_t i = tile * kDotTile + threadIdx.x;
+  if (i < S.N) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int64_t e = 3 * i + c;
+      const double re = S.vec[kVecR][e];
+      S.vec[kVecRh][e] = re;
+      S.vec[kVecP][e] = re;
+      S.vec[kVecV][e] = 0.0;
+    }
+  }
+  if (tile == 0 && threadIdx.x == 0) {
+    SolverScalars* sc = S.scal;
+    sc->rho = sc->rr;
+    sc->alpha = sc->beta = sc->omega = 0.0;
+    sc->converged = 0;
+    sc->done = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kDotTile) update_kernel(SysDesc S) { update_block(S, blockIdx.x); }
+
+__global__ void __launch_bounds__(kDotTile) init_kernel(SysDesc S, double rtol, int32_t maxit) {
+  init_block(S, blockIdx.x, rtol, maxit);
+}
+
+__global__ void __launch_bounds__(kDotTile) residual_kernel(SysDesc S, int restart) {
+  if (restart)
+    restart_block(S, blockIdx.x);
+  else
+    residual_block(S, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kDotTile)
+    update_batched(const SysDesc* __restrict__ sys, const BatchItem* __restrict__ items, int64_t nitems) {
+  for (int64_t i = blockIdx.x; i < nitems; i += gridDim.x) {
+    const BatchItem it = items[i];
+    update_block(sys[it.sys], it.local);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kDotTile)
+    vec_batched(const SysDesc* __restrict__ sys, const BatchItem* __restrict__ items, int64_t nitems, int mode,
+                double rtol, int32_t maxit, const int32_t* __restrict__ flags) {
+  for (int64_t i = blockIdx.x; i < nitems; i += gridDim.x) {
+    const BatchItem it = items[i];
+    if (flags && !flags[it.sys]) continue;  // uniform per item
+    const SysDesc& S = sys[it.sys];
+    if (mode == 0)
+      init_block(S, it.local, rtol, maxit);
+    else if (mode == 1)
+      residual_block(S, it.local);
+    else
+      restart_block(S, it.local);
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_update(const DevCtx& d, cudaStream_t s) {
+  if (d.sd.N == 0) return cudaSuccess;
+  update_kernel<<<(unsigned)d.sd.ntiles, kDotTile, 0, s>>>(d.sd);
   return cudaGetLastError();
 }
 
-// Standalone dot product in the fixed order.
+cudaError_t launch_init(const DevCtx& d, double rtol, int32_t maxit, cudaStream_t s) {
+  if (d.sd.N == 0) return cudaSuccess;
+  init_kernel<<<(unsigned)d.sd.ntiles, kDotTile, 0, s>>>(d.sd, rtol, maxit);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const DevCtx& d, int restart, cudaStream_t s) {
+  if (d.sd.N == 0) return cudaSuccess;
+  residual_kernel<<<(unsigned)d.sd.ntiles, kDotTile, 0, s>>>(d.sd, restart);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int grid,
+                                  cudaStream_t s) {
+  if (nitems == 0) return cudaSuccess;
+  update_batched<<<grid, kDotTile, 0, s>>>(sys, items, nitems);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vec_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int mode, double rtol,
+                               int32_t maxit, const int32_t* flags, int grid, cudaStream_t s) {
+  if (nitems == 0) return cudaSuccess;
+  vec_batched<<<grid, kDotTile, 0, s>>>(sys, items, nitems, mode, rtol, maxit, flags);
+  return cudaGetLastError();
+}
+
+int tile_blocks_per_sm() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sell_spmv_batched<2>, kDotTile, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n > 0 ? n : 1;
+}
+
+// ===========================================================================
+// Standalone dot product, permutation, status
+// ===========================================================================
 __global__ void __launch_bounds__(kDotTile) dot_kernel(const double* x, const double* y, int32_t N, double* partials,
                                                        int64_t m, uint32_t* counter, double* out_p) {
   const int64_t i = (int64_t)blockIdx.x * kDotTile + threadIdx.x;
   double q[1] = {i < N ? row_dot(x, y, i) : 0.0};
   __shared__ double buf[1][kDotTile];
   tile_halving_sum<1>(q, buf);
-  if (!publish_partials<1>(q, partials, m, counter)) return;
+  if (!publish_partials<1>(q, partials, m, blockIdx.x, gridDim.x, counter)) return;
   double out[1];
   finish_sum<1>(partials, m, m, out, buf);
   if (threadIdx.x == 0) {
@@ -650,9 +723,9 @@ __global__ void __launch_bounds__(kDotTile) dot_kernel(const double* x, const do
 }
 
 cudaError_t launch_dot(const DevCtx& d, const double* x, const double* y, double* out, cudaStream_t s) {
-  if (d.N == 0) return cudaMemsetAsync(out, 0, sizeof(double), s);
-  dot_kernel<<<(unsigned)d.ntiles, kDotTile, 0, s>>>(x, y, d.N, d.partials, d.ntiles_pow2,
-                                                      d.counters + kCntDot, out);
+  if (d.sd.N == 0) return cudaMemsetAsync(out, 0, sizeof(double), s);
+  dot_kernel<<<(unsigned)d.sd.ntiles, kDotTile, 0, s>>>(x, y, d.sd.N, d.sd.partials, d.sd.ntiles_pow2,
+                                                         d.sd.counters + kCntDot, out);
   return cudaGetLastError();
 }
 
@@ -663,26 +736,58 @@ cudaError_t launch_dot_scratch(const double* x, const double* y, int32_t n_brows
   return cudaGetLastError();
 }
 
-__global__ void permute_kernel(const double* in, double* out, const int32_t* map, int32_t N, int dir) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+// out[i] = in[map[i]] (3 doubles per row): map = perm gathers natural -> reordered,
+// map = iperm gathers reordered -> natural.
+__device__ __forceinline__ void gather_rows(const double* in, double* out, const int32_t* map, int64_t i) {
   const int64_t j = map[i];
-  if (dir == 0) {
-    // out[i] = in[perm[i]]
 #pragma unroll
-    for (int c = 0; c < 3; ++c) out[3 * i + c] = in[3 * j + c];
-  } else {
-    // out[old] = in[iperm[old]]
-#pragma unroll
-    for (int c = 0; c < 3; ++c) out[3 * i + c] = in[3 * j + c];
-  }
+  for (int c = 0; c < 3; ++c) out[3 * i + c] = in[3 * j + c];
+}
+
+__global__ void permute_kernel(const double* in, double* out, const int32_t* map, int32_t N) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) gather_rows(in, out, map, i);
 }
 
 cudaError_t launch_permute(const DevCtx& d, const double* in, double* out, int dir, cudaStream_t s) {
-  if (d.N == 0) return cudaSuccess;
+  if (d.sd.N == 0) return cudaSuccess;
   const int threads = 256;
-  const unsigned blocks = (unsigned)((d.N + threads - 1) / threads);
-  permute_kernel<<<blocks, threads, 0, s>>>(in, out, dir == 0 ? d.perm : d.iperm, d.N, dir);
+  const unsigned blocks = (unsigned)((d.sd.N + threads - 1) / threads);
+  permute_kernel<<<blocks, threads, 0, s>>>(in, out, dir == 0 ? d.sd.perm : d.sd.iperm, d.sd.N);
+  return cudaGetLastError();
+}
+
+// Tile items of 256 rows; dir 0: vec B <- ptrs[sys] permuted; dir 1: ptrs[sys] <- vec X natural.
+__global__ void __launch_bounds__(kDotTile)
+    permute_batched(const SysDesc* __restrict__ sys, const BatchItem* __restrict__ items, int64_t nitems,
+                    const double* const* __restrict__ ptrs, int dir) {
+  for (int64_t k = blockIdx.x; k < nitems; k += gridDim.x) {
+    const BatchItem it = items[k];
+    const SysDesc& S = sys[it.sys];
+    const int64_t i = (int64_t)it.local * kDotTile + threadIdx.x;
+    if (i >= S.N) continue;
+    if (dir == 0)
+      gather_rows(ptrs[it.sys], S.vec[kVecB], S.perm, i);
+    else
+      gather_rows(S.vec[kVecX], const_cast<double*>(ptrs[it.sys]), S.iperm, i);
+  }
+}
+
+cudaError_t launch_permute_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems,
+                                   const double* const* ptrs, int dir, int grid, cudaStream_t s) {
+  if (nitems == 0) return cudaSuccess;
+  permute_batched<<<grid, kDotTile, 0, s>>>(sys, items, nitems, ptrs, dir);
+  return cudaGetLastError();
+}
+
+__global__ void gather_status(const SysDesc* __restrict__ sys, int32_t nsys, SolverScalars* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nsys) out[i] = *sys[i].scal;
+}
+
+cudaError_t launch_gather_status(const SysDesc* sys, int32_t nsys, SolverScalars* out, cudaStream_t s) {
+  if (nsys == 0) return cudaSuccess;
+  gather_status<<<(nsys + 127) / 128, 128, 0, s>>>(sys, nsys, out);
   return cudaGetLastError();
 }
 

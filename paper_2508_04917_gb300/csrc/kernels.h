@@ -7,13 +7,14 @@
 
 namespace ilu0dd {
 
-struct DevCtx {
+// Everything a kernel needs about one system (copied by value into kernel
+// parameters for single-system launches, and into a device array for batched
+// launches).
+struct SysDesc {
   // preconditioner (fused apply)
   const unsigned char* stream;
   const CtaDesc* cta;
   const PieceDesc* pieces;
-  int nsub, threads, prefetch_bytes, vec_bytes, factor_prec;
-  size_t smem_bytes;
   // SpMV (sliced ELL of the reordered full matrix)
   const int32_t* slice_off;
   const int32_t* sell_col;
@@ -23,17 +24,30 @@ struct DevCtx {
   const int32_t* perm;
   const int32_t* iperm;
   // solver state
-  int32_t N;
-  int64_t ntiles, ntiles_pow2;
   double* vec[kNumVec];
   double* partials;     // 5 arrays of ntiles_pow2
   uint32_t* counters;
   SolverScalars* scal;
   double* hist;
   int32_t* err;
+  int64_t ntiles, ntiles_pow2;
+  int32_t N, nsub;
+  int32_t vec_bytes, prefetch_bytes;
 };
 
-// Opt the apply kernels into the context's dynamic shared memory.
+// Host view of one context: the system and its launch configuration.
+struct DevCtx {
+  SysDesc sd;
+  int threads, factor_prec;
+  size_t smem_bytes;
+};
+
+// Work item of a batched launch: system index and block index inside it.
+struct BatchItem {
+  int32_t sys, local;
+};
+
+// Opt the apply kernels into the device's shared memory.
 cudaError_t apply_configure(const DevCtx& d);
 
 // z = M^-1 r (mode plain), or the fused BiCGSTAB variants (modes P and S).
@@ -62,5 +76,29 @@ cudaError_t launch_dot_scratch(const double* x, const double* y, int32_t n_brows
 
 // dir 0: out = in[perm] (natural -> reordered); dir 1: inverse.
 cudaError_t launch_permute(const DevCtx& d, const double* in, double* out, int dir, cudaStream_t s);
+
+// ---- batched launches: one launch covers the work items of many systems.
+// `sys` is a device array of SysDesc; items list (system, subdomain) for the
+// apply and (system, dot tile) for the others. Systems whose solve is done are
+// skipped. `grid` blocks loop over the items (persistent launch).
+cudaError_t launch_apply_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int mode,
+                                 int factor_prec, int threads, size_t smem, int grid, cudaStream_t s);
+cudaError_t launch_spmv_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int kind, int grid,
+                                cudaStream_t s);
+cudaError_t launch_update_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int grid,
+                                  cudaStream_t s);
+// mode 0: init from b (vec B), 1: r = b - t with rel_true, 2: restart from r
+// (systems flagged in `flags`).
+cudaError_t launch_vec_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int mode, double rtol,
+                               int32_t maxit, const int32_t* flags, int grid, cudaStream_t s);
+// dir 0: vec B of system i <- in[i] permuted; dir 1: out[i] <- vec X of system i.
+cudaError_t launch_permute_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems,
+                                   const double* const* ptrs, int dir, int grid, cudaStream_t s);
+// out[i] = the solver scalars of system i (one small launch).
+cudaError_t launch_gather_status(const SysDesc* sys, int32_t nsys, SolverScalars* out, cudaStream_t s);
+
+// Blocks per SM of the batched kernels (for persistent grids).
+int apply_blocks_per_sm(int factor_prec, int threads, size_t smem);
+int tile_blocks_per_sm();
 
 }  // namespace ilu0dd
