@@ -178,7 +178,7 @@ int ilu0_dd_setup(const ilu0dd_bsr* A, const ilu0dd_geom* geom, const ilu0dd_opt
     S.pieces = reinterpret_cast<const PieceDesc*>(c->ws + L.pieces);
     S.nsub = p.nsub;
     S.prefetch_bytes = p.prefetch_bytes;
-    S.vec_bytes = (int)p.smem_bytes;
+    S.vec_bytes = (int)(p.smem_bytes - sizeof(PieceDesc) * kDescCache);
     S.slice_off = reinterpret_cast<const int32_t*>(c->ws + L.sell_off);
     S.sell_col = reinterpret_cast<const int32_t*>(c->ws + L.sell_col);
     S.sell_val = reinterpret_cast<const double*>(c->ws + L.sell_val);

@@ -41,6 +41,7 @@ namespace ilu0dd {
 // ---------------------------------------------------------------------------
 constexpr int kRowsPerWarp = 10;
 constexpr int kDescSlots = 3;   // slot counts carried in the descriptor
+constexpr int kDescCache = 128; // piece descriptors staged in shared memory at a time
 struct PieceDesc {          // 32 bytes, one per piece, device array
   uint32_t off;             // record start, bytes from the subdomain stream start
   uint32_t meta;            // n | (w << 16) | (kind << 24)

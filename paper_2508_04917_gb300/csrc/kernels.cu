@@ -75,7 +75,10 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
       pf_end += bytes;
     }
   };
-  if (tid == 0) prefetch_upto(dist);
+  // L2 prefetches come from lane 0 of the last warp, which has rows only in the
+  // widest levels, so the issue cost stays off the other warps' paths
+  const bool pf_thread = tid == (int)blockDim.x - 32;
+  if (pf_thread) prefetch_upto(dist);
 
   // subdomain vector -> shared memory (with the fused BiCGSTAB update)
   const int64_t base = 3ll * cd.row0;
@@ -107,11 +110,19 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
   const bool lane_ok = lane < 3 * kRowsPerWarp;
   const int base_lane = lane - comp;
 
-  PieceDesc nxt = cd.npieces > 0 ? S.pieces[cd.piece0] : PieceDesc{};
+  // piece descriptors are staged in shared memory, kDescCache at a time
+  PieceDesc* dsm = reinterpret_cast<PieceDesc*>(smem + S.vec_bytes);
   for (int k = 0; k < cd.npieces; ++k) {
-    const PieceDesc pd = nxt;
-    if (k + 1 < cd.npieces) nxt = S.pieces[cd.piece0 + k + 1];
-    if (tid == 0) prefetch_upto(pd.off + dist);
+    if (k % kDescCache == 0) {
+      if (k > 0) __syncthreads();
+      const int cnt = min(kDescCache, cd.npieces - k);
+      const uint4* src = reinterpret_cast<const uint4*>(S.pieces + cd.piece0 + k);
+      uint4* dst = reinterpret_cast<uint4*>(dsm);
+      for (int q = tid; q < 2 * cnt; q += blockDim.x) dst[q] = __ldg(src + q);
+      __syncthreads();
+    }
+    const PieceDesc pd = dsm[k % kDescCache];
+    if (pf_thread) prefetch_upto(pd.off + dist);
     const int n = (int)(pd.meta & 0xFFFFu);
     const int w = (int)((pd.meta >> 16) & 0xFFu);
     const int kind = (int)(pd.meta >> 24);

@@ -386,7 +386,7 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   }
   p.stream_bytes = soff;
   p.n_pieces = (int64_t)p.pieces.size();
-  p.smem_bytes = (size_t)align_up(3ll * p.rmax * p.vec_elem, 128);
+  p.smem_bytes = (size_t)align_up(3ll * p.rmax * p.vec_elem, 128) + sizeof(PieceDesc) * kDescCache;
   if ((int64_t)p.smem_bytes > (int64_t)max_smem - kApplyStaticSmem) {
     *why = "subdomain vector (" + std::to_string(3ll * p.rmax * p.vec_elem) + " B) exceeds the " +
            std::to_string(max_smem) +
