@@ -201,8 +201,21 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
   for (int e = tid; e < nv; e += blockDim.x) z[base + e] = (double)y[e];
 }
 
+// Resident blocks per SM the single-system apply's register budget targets:
+// FP32/BF16 blocks are latency-bound, so four per SM; FP64 keeps three (its
+// working set would spill at four, and the FP64 pipe is already the busiest
+// unit). The batched apply keeps three (its work loop holds more state).
+template <typename TF>
+struct ApplyMinBlocks {
+  static constexpr int value = 4;
+};
+template <>
+struct ApplyMinBlocks<double> {
+  static constexpr int value = kApplyMinBlocks;
+};
+
 template <typename TF, int MODE>
-__global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
+__global__ void __launch_bounds__(kMaxApplyThreads, ApplyMinBlocks<TF>::value)
     ildu0_apply_kernel(SysDesc S, const double* r, double* z) {
   apply_block<TF, MODE>(S, blockIdx.x, r, z);
 }
