@@ -17,7 +17,10 @@ int32 column indices and row pointers of L and U, FP64 r in and z out, plus
 the fused p/s vector traffic) over the applies' CUDA-event time inside the
 timed region. The JSON line also reports the whole-iteration throughput, the
 per-kernel breakdown, BiCGSTAB time to relative residual 1e-8 with FP64, FP32
-and BF16 factors, the CPU oracle's throughput and the clocks seen.
+and BF16 factors, the FP64-pipe roof of the apply, the 64^3 subdomain-size and
+factor-precision sweeps, the cuSPARSE global-ILU0 context on the same system,
+the batched solve of 64 ragged systems, the CPU oracle's throughput and the
+clocks seen.
 
 --impl reference times the CPU oracle (plain FP64 C, one thread) on the same
 workload and metric: one step = one full L+U apply.
@@ -241,6 +244,18 @@ def run_ours(args):
     torch.cuda.synchronize()
     plain_ms = a0.elapsed_time(a1) / args.steps
     plain_gbs = apply_b / (plain_ms * 1e-3) / 1e9
+    # FP64 pipe roof of the same apply: 9 FMAs per stored 3x3 block (L, U~ and D^-1)
+    fp64_flops = 18 * (ctx.query("nl") + ctx.query("nu") + n)
+    fp64_roof = None
+    if not args.no_context:
+        import context
+        fp64_peak = context.fp64_fma_gflops() / 1e3
+        fp64_roof = {"bound": "alu", "pipe": "fp64", "achieved": round(fp64_flops / plain_ms / 1e9, 4),
+                     "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                     "frac": round(fp64_flops / plain_ms / 1e9 / fp64_peak, 4), "flops_per_apply": fp64_flops,
+                     "floor_ms": round(fp64_flops / fp64_peak / 1e9, 4),
+                     "hbm_floor_ms": round(apply_b / peak / 1e6, 4),
+                     "peak_source": "measured on this GPU: FP64 FMA chains (libilu0dd_context ctx_fp64_fma_rate)"}
 
     # ---- end to end through the public API with pinned host buffers
     r_h = torch.from_numpy(np.random.default_rng(2).uniform(-1, 1, 3 * n)).pin_memory()
@@ -265,6 +280,12 @@ def run_ours(args):
            "what": "ilu0_dd_apply with r copied from pinned host memory and z copied back, every step"}
     ctx.close()
     del ctx
+
+    # ---- context: the cuSPARSE global ILU0 on the same system; the 64^3 sweeps
+    vendor = sweep = None
+    if not args.no_context and rank == 0:
+        vendor = run_vendor(s, w, dev, plain_ms)
+        sweep = run_sweep(dev)
 
     # ---- BiCGSTAB time to relative residual 1e-8: FP64 vs FP32 / BF16 factors
     solves = {}
@@ -331,7 +352,10 @@ def run_ours(args):
                        for k, v in per_kernel.items()},
         "plain_apply": {"ms": round(plain_ms, 5), "gbs": round(plain_gbs, 2), "bytes": apply_b,
                         "frac_of_hbm": round(plain_gbs / peak, 4)},
+        "fp64_pipe_roofline": fp64_roof,
         "bicgstab": solves,
+        "sweep_64cubed": sweep,
+        "vendor_context": vendor,
         "batched": batched,
         "setup_s": round(setup_s, 3),
         "cpu_baseline": cpu,
@@ -393,6 +417,143 @@ def run_batched(args, dev):
     for c in ctxs:
         c.close()
     return out
+
+
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def time_apply_warm(ctx, r, z, reps):
+    """Mean apply time (ms) over `reps` back-to-back applies (L2-warm when the
+    factors fit in L2)."""
+    import torch
+    for _ in range(3):
+        ctx.apply(r, z)
+    e0, e1 = _events()
+    e0.record()
+    for _ in range(reps):
+        ctx.apply(r, z)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def time_apply_cold(ctx, r, z, reps, flush):
+    """Median apply time (ms), L2 flushed (a write of `flush`, 4x L2) before each."""
+    import torch
+    times = []
+    e0, e1 = _events()
+    for _ in range(reps):
+        flush.zero_()
+        e0.record()
+        ctx.apply(r, z)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return float(np.median(times))
+
+
+def timed_solve(ctx, b):
+    """BiCGSTAB wall time after one warm-up solve (graph capture), and its info."""
+    import torch
+    ctx.solve(b)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, info = ctx.solve(b)
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, x, info
+
+
+def run_sweep(dev, reps=50):
+    """64^3 laplace system (seed 2): subdomain boxes 4^3, 8^3 and 16x16x8, FP64:
+    apply GB/s L2-warm and L2-cold (the 0.12-0.14 GB footprint is L2-sized),
+    BiCGSTAB iterations and time to 1e-8. Then factor precision on the 64^3
+    seed-4 system with 16x16x8 boxes: FP64 / FP32 / BF16 factors, each apply's
+    relative error against the FP64 apply (which the parity tests hold to the
+    oracle within 1e-12), iterations and time to 1e-8."""
+    import torch
+
+    import paper_2508_04917_gb300 as pkg
+    flush = torch.empty(4 * 129 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    out = {"subdomain_sweep": [], "precision": []}
+    for wl in ("laplace64_sub4", "laplace64_sub8", "laplace64_sub16x16x8"):
+        s, w = workload_system(wl)
+        ctx = pkg.Ilu0DD(s.row_ptr, s.col, s.val, w["grid"], w["sub"])
+        r = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, 3 * s.n)).to(dev)
+        z = torch.empty_like(r)
+        ab = ctx.query("apply_bytes")
+        warm = time_apply_warm(ctx, r, z, reps)
+        cold = time_apply_cold(ctx, r, z, reps, flush)
+        sec, _, info = timed_solve(ctx, torch.from_numpy(s.b).to(dev))
+        out["subdomain_sweep"].append({
+            "workload": wl, "subdomain": list(w["sub"]), "subdomains": ctx.query("nsub"),
+            "dropped_blocks_pct": round(100.0 * (1 - ctx.query("kept") / ctx.query("nnzb")), 2),
+            "apply_bytes": ab, "apply_ms_l2_warm": round(warm, 5), "apply_gbs_l2_warm": round(ab / warm / 1e6, 1),
+            "apply_ms_l2_cold": round(cold, 5), "apply_gbs_l2_cold": round(ab / cold / 1e6, 1),
+            "iterations": info["iterations"], "solve_s": round(sec, 5), "status": info["status"]})
+        ctx.close()
+    s, w = workload_system("laplace64_mixed_sub16x16x8")
+    b = torch.from_numpy(s.b).to(dev)
+    r = torch.from_numpy(np.random.default_rng(10).uniform(-1, 1, 3 * s.n)).to(dev)
+    z64 = None
+    for prec in ("f64", "f32", "bf16"):
+        ctx = pkg.Ilu0DD(s.row_ptr, s.col, s.val, w["grid"], w["sub"], factor_prec=prec)
+        z = ctx.apply(r)
+        if z64 is None:
+            z64 = z.clone()
+        err = float((z - z64).abs().max() / z64.abs().max())
+        cold = time_apply_cold(ctx, r, z, reps, flush)
+        sec, x, info = timed_solve(ctx, b)
+        xs = torch.from_numpy(s.xstar).to(dev)
+        out["precision"].append({
+            "factor_prec": prec, "apply_bytes": ctx.query("apply_bytes"), "apply_ms_l2_cold": round(cold, 5),
+            "apply_rel_err_vs_f64_apply": err, "iterations": info["iterations"], "solve_s": round(sec, 5),
+            "rel_res_true": info["rel_res_true"], "status": info["status"],
+            "max_rel_err_vs_xstar": float((x - xs).abs().max() / xs.abs().max())})
+        ctx.close()
+    out["workloads"] = {"sweep": "64^3 laplace, seed 2", "precision": "64^3 laplace, seed 4, 16x16x8 boxes"}
+    return out
+
+
+def run_vendor(s, w, dev, ours_apply_ms, reps=20):
+    """cuSPARSE global block ILU0 on the same system (natural order, nothing
+    dropped): setup (analysis + bsrilu02), the apply (bsrsv2 lower then upper)
+    and bsrmv, against the library's subdomain apply of the same system."""
+    import torch
+
+    import context
+    t0 = time.perf_counter()
+    v = context.VendorIlu0(s.row_ptr, s.col, s.val)
+    wall = time.perf_counter() - t0
+    n, nnzb = s.n, s.nnzb
+    apply_bytes = 72 * nnzb + 4 * (nnzb - n) + 8 * (n + 1) + 48 * n
+    r = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, 3 * n)).to(dev)
+    z = torch.empty_like(r)
+    for _ in range(3):
+        v.apply(r, z)
+    e0, e1 = _events()
+    e0.record()
+    for _ in range(reps):
+        v.apply(r, z)
+    e1.record()
+    torch.cuda.synchronize()
+    ams = e0.elapsed_time(e1) / reps
+    for _ in range(3):
+        v.spmv(r, z)
+    e0.record()
+    for _ in range(reps):
+        v.spmv(r, z)
+    e1.record()
+    torch.cuda.synchronize()
+    sms = e0.elapsed_time(e1) / reps
+    v.close()
+    return {"workload": f"{w['grid'][0]}^3 natural order, global ILU0 (no decomposition)",
+            "library": "cuSPARSE bsrilu02 + bsrsv2 (level policy) + bsrmv, FP64",
+            "setup_ms_device": round(v.setup_ms, 2), "setup_s_wall": round(wall, 3),
+            "apply_ms": round(ams, 4), "apply_bytes": apply_bytes, "apply_gbs": round(apply_bytes / ams / 1e6, 1),
+            "spmv_ms": round(sms, 4), "ours_apply_ms": round(ours_apply_ms, 5),
+            "apply_speedup_ours_vs_vendor": round(ams / ours_apply_ms, 2)}
 
 
 def oracle_apply_baseline(s, grid, sub, apply_bytes, budget_s=15.0):
@@ -461,6 +622,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-systems", type=int, default=64)
+    ap.add_argument("--no-context", action="store_true", help="skip the cuSPARSE context and the 64^3 sweeps")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -86,3 +86,15 @@ def test_subdomain_shared_memory_limit():
     with pytest.raises(g.Ilu0DDError) as e:
         g.workspace_size(rp, col, val, grid, (16, 16, 37), prefetch_bytes=100)
     assert e.value.code == 1
+
+
+def test_context_library_builds_and_exports():
+    """The measurement library beside the path (vendor global ILU0, FP64 FMA rate)."""
+    import context
+
+    context.build()
+    lib = context.load()
+    for name in ("ctx_vendor_ilu0_create", "ctx_vendor_ilu0_apply", "ctx_vendor_spmv", "ctx_vendor_ilu0_factors",
+                 "ctx_vendor_ilu0_destroy", "ctx_fp64_fma_rate"):
+        assert hasattr(lib, name), name
+    assert lib.ctx_vendor_ilu0_apply(None, None, None, None) == 4
