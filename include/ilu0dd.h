@@ -52,6 +52,12 @@ extern "C" {
 #define ILU0DD_F64 0   /* factors and apply arithmetic in FP64 */
 #define ILU0DD_F32 1   /* factors stored in FP32, apply in FP32 */
 #define ILU0DD_BF16 2  /* factors stored in BF16, apply in FP32 */
+#define ILU0DD_DF64 3  /* factors stored as float pairs hi + lo (8 bytes, about 48
+                          significant bits), apply in double-float arithmetic on
+                          the FP32 pipe; every factor magnitude must lie in
+                          [2^-70, 2^100] (else ILU0DD_ERR_INVALID). Not in the
+                          paper: FP64-accurate to about 1e-14 relative per
+                          operation where this GPU's FP64 pipe is the bound. */
 
 /* ---- inputs ----------------------------------------------------------- */
 
@@ -75,7 +81,7 @@ typedef struct {
 } ilu0dd_geom;
 
 typedef struct {
-  int32_t factor_prec;      /* ILU0DD_F64 / ILU0DD_F32 / ILU0DD_BF16 */
+  int32_t factor_prec;      /* ILU0DD_F64 / ILU0DD_F32 / ILU0DD_BF16 / ILU0DD_DF64 */
   int32_t threads_per_cta;  /* apply block size; 0 = 32 per ten rows of the widest level (<= 384) */
   int32_t prefetch_bytes;   /* apply: L2 prefetch distance per block, bytes (multiple of 16); 0 = 65536 */
   int32_t maxit;            /* BiCGSTAB iteration limit; 0 = 10000 */

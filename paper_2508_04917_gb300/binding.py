@@ -20,8 +20,8 @@ _HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 OK = 0
 ERR_INVALID, ERR_ZERO_PIVOT, ERR_SMEM, ERR_CUDA = 1, 2, 3, 4
 ERR_BREAKDOWN, ERR_NOT_CONVERGED, ERR_NONFINITE, ERR_WORKSPACE, ERR_DEVICE_WAIT = 5, 6, 7, 8, 9
-F64, F32, BF16 = 0, 1, 2
-PRECISIONS = {"f64": F64, "f32": F32, "bf16": BF16}
+F64, F32, BF16, DF64 = 0, 1, 2, 3
+PRECISIONS = {"f64": F64, "f32": F32, "bf16": BF16, "df64": DF64}
 
 X_PART_ID, X_PERM, X_IPERM, X_PART_PTR, X_LEVEL_L, X_LEVEL_U = 0, 1, 2, 3, 4, 5
 X_DD_ROW_PTR, X_DD_COL, X_L, X_UT, X_INVD, X_AP_ROW_PTR, X_AP_COL = 6, 7, 8, 9, 10, 11, 12

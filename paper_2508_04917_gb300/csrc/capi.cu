@@ -129,6 +129,12 @@ int ilu0_dd_setup(const ilu0dd_bsr* A, const ilu0dd_geom* geom, const ilu0dd_opt
     delete c;
     return rc;
   }
+  if (p.factor_prec == ILU0DD_DF64 && !df64_range_ok(F, invD)) {
+    c->why = "a factor magnitude lies outside [2^-70, 2^100], the double-float range";
+    if (c->trace) std::fprintf(stderr, "[ilu0dd] setup: %s\n", c->why.c_str());
+    delete c;
+    return ILU0DD_ERR_INVALID;
+  }
   const double t2 = wall_seconds();
   std::vector<uint8_t> sbytes;
   pack_stream(p, F, invD, &sbytes);

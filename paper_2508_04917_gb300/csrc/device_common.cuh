@@ -99,6 +99,99 @@ struct FactorLoad<bf16s> {
   }
 };
 
+// ---- double-float arithmetic (the DF64 factor mode) -----------------------
+// A value is the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2,
+// about 48 significant bits, computed on the FP32 pipe (this GPU's FP64 pipe
+// runs at 1/55 of its FP32 rate). Built from error-free transformations: the
+// exact error of a float product, fma(a, b, -a*b); Knuth's two-sum, exact for
+// any a, b; Dekker's fast two-sum, exact when |a| >= |b|. Every step uses the
+// explicitly rounded intrinsics, so no contraction can break them.
+struct df64s {  // storage of one factor entry: hi then lo (8 bytes)
+  float hi, lo;
+};
+struct df64 {
+  float hi, lo;
+  __device__ __forceinline__ df64() {}
+  __device__ __forceinline__ df64(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ explicit df64(int z) : hi((float)z), lo(0.f) {}
+};
+
+// Nearest float pair of a double: hi = fl(v), lo = fl(v - hi) (v - hi is exact).
+__device__ __forceinline__ df64 df_from_double(double v) {
+  const float h = __double2float_rn(v);
+  return df64(h, __double2float_rn(v - (double)h));
+}
+__device__ __forceinline__ double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+
+// a * b (the lo * lo term, below 2^-48 relative, is dropped)
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float h = __fadd_rn(p, e);
+  return df64(h, __fsub_rn(e, __fsub_rn(h, p)));
+}
+
+// a * b + c: the product's head and tail as above, two-sum of the head with
+// c.hi, then the tails, then a fast two-sum to renormalise.
+__device__ __forceinline__ df64 df_fma(df64 a, df64 b, df64 c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float s = __fadd_rn(p, c.hi);
+  const float v = __fsub_rn(s, p);
+  float t = __fadd_rn(__fsub_rn(p, __fsub_rn(s, v)), __fsub_rn(c.hi, v));
+  t = __fadd_rn(t, __fadd_rn(e, c.lo));
+  const float h = __fadd_rn(s, t);
+  return df64(h, __fsub_rn(t, __fsub_rn(h, s)));
+}
+
+// Generic helpers of the apply over its compute types (float, double, df64).
+template <typename T>
+__device__ __forceinline__ T mac(T a, T b, T c) {  // a * b + c
+  return fma(a, b, c);
+}
+template <>
+__device__ __forceinline__ df64 mac<df64>(df64 a, df64 b, df64 c) {
+  return df_fma(a, b, c);
+}
+template <typename T>
+__device__ __forceinline__ T shfl(T v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+template <>
+__device__ __forceinline__ df64 shfl<df64>(df64 v, int src) {
+  return df64(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
+}
+template <typename T>
+__device__ __forceinline__ T to_compute(double v) {
+  return (T)v;
+}
+template <>
+__device__ __forceinline__ df64 to_compute<df64>(double v) {
+  return df_from_double(v);
+}
+__device__ __forceinline__ double to_double(float v) { return (double)v; }
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(df64 v) { return df_to_double(v); }
+
+template <>
+struct FactorLoad<df64s> {
+  using compute = df64;
+  __device__ __forceinline__ static df64 get(const unsigned char* p) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    return df64(v.x, v.y);
+  }
+  __device__ __forceinline__ static df64 getg(const unsigned char* p) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return df64(v.x, v.y);
+  }
+};
+
 // Fixed-order block reduction of kDotTile values, one per thread of a
 // kDotTile-thread block: halving sums s[i] += s[i + h], h = 128 .. 1. `buf`
 // holds kDotTile doubles of shared memory. Result valid in thread 0.

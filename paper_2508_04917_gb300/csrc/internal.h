@@ -123,6 +123,7 @@ struct Plan {
   int threads = 0;
   int prefetch_bytes = 0;
   int vec_elem = 8, factor_elem = 8;
+  int factor_prec = ILU0DD_F64;
   int rmax = 0, max_pieces = 0;
   size_t smem_bytes = 0;
   int64_t n_pieces = 0;
@@ -156,6 +157,10 @@ int factor_ildu0(const Plan& plan, const double* aval, std::vector<double>* F,
                  std::vector<double>* invD, int32_t* bad_row);
 
 // Pack the factor stream (bytes) in the plan's precision.
+// DF64 mode: every nonzero factor magnitude within [2^-70, 2^100], so both
+// floats of a pair stay normal after the split.
+bool df64_range_ok(const std::vector<double>& F, const std::vector<double>& invD);
+
 void pack_stream(const Plan& plan, const std::vector<double>& F, const std::vector<double>& invD,
                  std::vector<uint8_t>* stream);
 

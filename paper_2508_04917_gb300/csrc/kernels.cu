@@ -14,6 +14,8 @@
 // inside an iteration.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "device_common.cuh"
 #include "kernels.h"
 
@@ -45,11 +47,14 @@ __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 // One block per subdomain. The block reads its factor records straight from
 // global memory (coalesced: consecutive threads read consecutive values; the
 // slot counts in the piece descriptor let every load of a level issue at
-// once) while thread 0 keeps bulk L2 prefetches (cp.async.bulk.prefetch.L2) a
-// fixed distance ahead in the subdomain's stream. Shared memory holds only the
-// subdomain vector. Three threads per row (lane = 3 * (row in warp) + a, ten
-// rows per warp); rows of one piece are independent and pieces are separated
-// by block barriers.
+// once) while one thread keeps bulk L2 prefetches (cp.async.bulk.prefetch.L2)
+// a fixed distance ahead in the subdomain's stream. Shared memory holds the
+// subdomain vector and the block's piece descriptors. Three threads per row
+// (lane = 3 * (row in warp) + a, ten rows per warp); rows of one piece are
+// independent and pieces are separated by block barriers.
+// In the DF64 mode the vector is held as float pairs, scaled by a power of two
+// per block (exact, and the apply is linear and local to the block) so that
+// the FP32 exponent range never limits it.
 // Modes: plain z = M^-1 r; P: p <- r + beta (p - omega v), z = M^-1 p;
 // S: s <- r - alpha v, z = M^-1 s. Modes P and S skip a finished solve.
 template <typename TF, int MODE>
@@ -89,6 +94,8 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
   const double* vv = S.vec[kVecV];
   double* pp = S.vec[kVecP];
   double* ss = S.vec[kVecS];
+  constexpr bool kDF = std::is_same<TV, df64>::value;
+  double amax = 0.0;  // DF64: largest |value| this thread loads
   for (int e = tid; e < nv; e += blockDim.x) {
     double val;
     if (MODE == kModePlain) {
@@ -100,7 +107,27 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
       val = fma(-alpha, vv[base + e], r[base + e]);
       ss[base + e] = val;
     }
-    y[e] = (TV)val;
+    if constexpr (kDF) {
+      reinterpret_cast<double*>(y)[e] = val;  // same 8 bytes; converted below
+      amax = fmax(amax, fabs(val));
+    } else {
+      y[e] = to_compute<TV>(val);
+    }
+  }
+  double unscale = 1.0;
+  if constexpr (kDF) {
+    // block maximum -> scale 2^-k with max |value| * 2^-k in [0.5, 1)
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    double* red = reinterpret_cast<double*>(smem + S.vec_bytes);  // descriptor area, not yet in use
+    if ((tid & 31) == 0) red[tid >> 5] = amax;
+    __syncthreads();
+    amax = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) amax = fmax(amax, red[w]);
+    int k = 0;
+    if (amax > 0.0 && isfinite(amax)) frexp(amax, &k);
+    const double scale = ldexp(1.0, -k);
+    unscale = ldexp(1.0, k);
+    for (int e = tid; e < nv; e += blockDim.x) y[e] = df_from_double(reinterpret_cast<double*>(y)[e] * scale);
   }
   __syncthreads();
 
@@ -161,12 +188,12 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
       if (kind) {
         // D^-1 (Section 4.3): w_i = D_i^-1 y_i; the row's three components
         // come from the neighbouring lanes
-        const TV y0 = __shfl_sync(0xffffffffu, acc, base_lane);
-        const TV y1 = __shfl_sync(0xffffffffu, acc, base_lane + 1);
-        const TV y2 = __shfl_sync(0xffffffffu, acc, base_lane + 2);
+        const TV y0 = shfl(acc, base_lane);
+        const TV y1 = shfl(acc, base_lane + 1);
+        const TV y2 = shfl(acc, base_lane + 2);
         TV t = d[0] * y0;
-        t = fma(d[1], y1, t);
-        t = fma(d[2], y2, t);
+        t = mac(d[1], y1, t);
+        t = mac(d[2], y2, t);
         if (active) acc = t;
       }
       if (active) {
@@ -174,9 +201,9 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
         for (int sl = 0; sl < kDescSlots; ++sl) {
           if (sl < nsl) {
             const int cl = col[sl];
-            acc = fma(-bv[sl][0], y[3 * cl], acc);
-            acc = fma(-bv[sl][1], y[3 * cl + 1], acc);
-            acc = fma(-bv[sl][2], y[3 * cl + 2], acc);
+            acc = mac(-bv[sl][0], y[3 * cl], acc);
+            acc = mac(-bv[sl][1], y[3 * cl + 1], acc);
+            acc = mac(-bv[sl][2], y[3 * cl + 2], acc);
           }
         }
         // rows with more than kDescSlots blocks (general patterns): remaining slots
@@ -187,9 +214,9 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
             const int cl = gu16(cb + 2 * (c0 + (uint32_t)trow));
             const unsigned char* vo = vb + (9 * (size_t)c0 + (size_t)(3 * trow + comp)) * FE;
             const size_t cstride = 3 * (size_t)cs * FE;
-            acc = fma(-gfactor<TF>(vo), y[3 * cl], acc);
-            acc = fma(-gfactor<TF>(vo + cstride), y[3 * cl + 1], acc);
-            acc = fma(-gfactor<TF>(vo + 2 * cstride), y[3 * cl + 2], acc);
+            acc = mac(-gfactor<TF>(vo), y[3 * cl], acc);
+            acc = mac(-gfactor<TF>(vo + cstride), y[3 * cl + 1], acc);
+            acc = mac(-gfactor<TF>(vo + 2 * cstride), y[3 * cl + 2], acc);
             c0 += cs;
           }
         }
@@ -198,19 +225,23 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
     }
     __syncthreads();
   }
-  for (int e = tid; e < nv; e += blockDim.x) z[base + e] = (double)y[e];
+  for (int e = tid; e < nv; e += blockDim.x) z[base + e] = kDF ? to_double(y[e]) * unscale : to_double(y[e]);
 }
 
 // Resident blocks per SM the single-system apply's register budget targets:
-// FP32/BF16 blocks are latency-bound, so four per SM; FP64 keeps three (its
-// working set would spill at four, and the FP64 pipe is already the busiest
-// unit). The batched apply keeps three (its work loop holds more state).
+// FP32/BF16 blocks are latency-bound, so four per SM; FP64 and DF64 keep
+// three (their working sets would spill at four). The batched apply keeps
+// three (its work loop holds more state).
 template <typename TF>
 struct ApplyMinBlocks {
   static constexpr int value = 4;
 };
 template <>
 struct ApplyMinBlocks<double> {
+  static constexpr int value = kApplyMinBlocks;
+};
+template <>
+struct ApplyMinBlocks<df64s> {  // pairs need FP64-sized registers
   static constexpr int value = kApplyMinBlocks;
 };
 
@@ -261,6 +292,9 @@ cudaError_t apply_configure(const DevCtx& d) {
   acc(configure_one<bf16s, kModePlain>(smem));
   acc(configure_one<bf16s, kModeP>(smem));
   acc(configure_one<bf16s, kModeS>(smem));
+  acc(configure_one<df64s, kModePlain>(smem));
+  acc(configure_one<df64s, kModeP>(smem));
+  acc(configure_one<df64s, kModeS>(smem));
   return e;
 }
 
@@ -280,6 +314,7 @@ cudaError_t launch_apply(const DevCtx& d, int mode, const double* r, double* z, 
   if (d.sd.nsub == 0) return cudaSuccess;
   if (d.factor_prec == ILU0DD_F64) return launch_apply_t<double>(d, mode, r, z, s);
   if (d.factor_prec == ILU0DD_F32) return launch_apply_t<float>(d, mode, r, z, s);
+  if (d.factor_prec == ILU0DD_DF64) return launch_apply_t<df64s>(d, mode, r, z, s);
   return launch_apply_t<bf16s>(d, mode, r, z, s);
 }
 
@@ -300,6 +335,8 @@ cudaError_t launch_apply_batched(const SysDesc* sys, const BatchItem* items, int
     return launch_apply_batched_t<double>(sys, items, nitems, mode, threads, smem, grid, s);
   if (factor_prec == ILU0DD_F32)
     return launch_apply_batched_t<float>(sys, items, nitems, mode, threads, smem, grid, s);
+  if (factor_prec == ILU0DD_DF64)
+    return launch_apply_batched_t<df64s>(sys, items, nitems, mode, threads, smem, grid, s);
   return launch_apply_batched_t<bf16s>(sys, items, nitems, mode, threads, smem, grid, s);
 }
 
@@ -310,6 +347,8 @@ int apply_blocks_per_sm(int factor_prec, int threads, size_t smem) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ildu0_apply_batched<double, kModeP>, threads, smem);
   else if (factor_prec == ILU0DD_F32)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ildu0_apply_batched<float, kModeP>, threads, smem);
+  else if (factor_prec == ILU0DD_DF64)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ildu0_apply_batched<df64s, kModeP>, threads, smem);
   else
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ildu0_apply_batched<bf16s, kModeP>, threads, smem);
   if (e != cudaSuccess) {

@@ -97,12 +97,18 @@ uint16_t to_bf16(float f) {
   return (uint16_t)(u >> 16);
 }
 
-void put_factor(uint8_t* dst, int felem, double v) {
-  if (felem == 8) {
+void put_factor(uint8_t* dst, int prec, double v) {
+  if (prec == ILU0DD_F64) {
     std::memcpy(dst, &v, 8);
-  } else if (felem == 4) {
+  } else if (prec == ILU0DD_F32) {
     float f = (float)v;
     std::memcpy(dst, &f, 4);
+  } else if (prec == ILU0DD_DF64) {
+    // hi = fl32(v), lo = fl32(v - hi); v - hi is exact in FP64
+    float hl[2];
+    hl[0] = (float)v;
+    hl[1] = (float)(v - (double)hl[0]);
+    std::memcpy(dst, hl, 8);
   } else {
     uint16_t h = to_bf16((float)v);
     std::memcpy(dst, &h, 2);
@@ -249,12 +255,13 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
 
   // ---- apply configuration
   const int fp = o->factor_prec;
-  if (fp != ILU0DD_F64 && fp != ILU0DD_F32 && fp != ILU0DD_BF16) {
-    *why = "factor_prec must be ILU0DD_F64, ILU0DD_F32 or ILU0DD_BF16";
+  if (fp != ILU0DD_F64 && fp != ILU0DD_F32 && fp != ILU0DD_BF16 && fp != ILU0DD_DF64) {
+    *why = "factor_prec must be ILU0DD_F64, ILU0DD_F32, ILU0DD_BF16 or ILU0DD_DF64";
     return ILU0DD_ERR_INVALID;
   }
-  p.factor_elem = fp == ILU0DD_F64 ? 8 : fp == ILU0DD_F32 ? 4 : 2;
-  p.vec_elem = fp == ILU0DD_F64 ? 8 : 4;
+  p.factor_prec = fp;
+  p.factor_elem = (fp == ILU0DD_F64 || fp == ILU0DD_DF64) ? 8 : fp == ILU0DD_F32 ? 4 : 2;
+  p.vec_elem = (fp == ILU0DD_F64 || fp == ILU0DD_DF64) ? 8 : 4;
   for (int s = 0; s < p.nsub; ++s) p.rmax = std::max(p.rmax, p.part_ptr[s + 1] - p.part_ptr[s]);
   if (p.rmax > 65535) {
     *why = "a subdomain has more than 65535 rows";
@@ -501,11 +508,23 @@ int factor_ildu0(const Plan& p, const double* aval, std::vector<double>* Fp, std
   return ILU0DD_OK;
 }
 
+bool df64_range_ok(const std::vector<double>& F, const std::vector<double>& invD) {
+  const double lo = std::ldexp(1.0, -70), hi = std::ldexp(1.0, 100);
+  auto ok = [&](const std::vector<double>& v) {
+    for (double x : v) {
+      const double a = std::fabs(x);
+      if (a != 0.0 && !(a >= lo && a <= hi)) return false;
+    }
+    return true;
+  };
+  return ok(F) && ok(invD);
+}
+
 void pack_stream(const Plan& p, const std::vector<double>& F, const std::vector<double>& invD,
                  std::vector<uint8_t>* out) {
   std::vector<uint8_t>& S = *out;
   S.assign((size_t)p.stream_bytes, 0);
-  const int fe = p.factor_elem;
+  const int fe = p.factor_elem, fp = p.factor_prec;
   parallel_for(p.nsub, [&](int64_t s) {
     const CtaDesc& c = p.cta[s];
     for (int32_t k = 0; k < c.npieces; ++k) {
@@ -535,7 +554,7 @@ void pack_stream(const Plan& p, const std::vector<double>& F, const std::vector<
         for (int cc = 0; cc < 3; ++cc)
           for (int t = 0; t < n; ++t)
             for (int a = 0; a < 3; ++a)
-              put_factor(v + (((int64_t)cc * n + t) * 3 + a) * fe, fe,
+              put_factor(v + (((int64_t)cc * n + t) * 3 + a) * fe, fp,
                          invD[9 * (size_t)(c.row0 + rows[t]) + 3 * a + cc]);
         v += 9ll * n * fe;
       }
@@ -544,7 +563,7 @@ void pack_stream(const Plan& p, const std::vector<double>& F, const std::vector<
         for (int cc = 0; cc < 3; ++cc)
           for (int t = 0; t < cs; ++t)
             for (int a = 0; a < 3; ++a)
-              put_factor(v + (((int64_t)cc * cs + t) * 3 + a) * fe, fe, F[9 * (size_t)blk[t][slot] + 3 * a + cc]);
+              put_factor(v + (((int64_t)cc * cs + t) * 3 + a) * fe, fp, F[9 * (size_t)blk[t][slot] + 3 * a + cc]);
         v += 9ll * cs * fe;
       }
     }

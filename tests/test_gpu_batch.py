@@ -34,7 +34,7 @@ SPECS = [
 ]
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "df64"])
 def test_batched_equals_per_system_solves(prec):
     systems = _systems(SPECS)
     ctxs = [g.Ilu0DD(s.row_ptr, s.col, s.val, grid, sub, factor_prec=prec) for grid, sub, s in systems]
