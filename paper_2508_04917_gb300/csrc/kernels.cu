@@ -136,6 +136,8 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
   const int trow = warp * kRowsPerWarp + lane / 3;
   const bool lane_ok = lane < 3 * kRowsPerWarp;
   const int base_lane = lane - comp;
+  const uint32_t lane_voff = (uint32_t)(3 * trow + comp) * FE;  // this thread's value offset in a slot
+  const uint32_t trow2 = 2u * (uint32_t)trow;
 
   // piece descriptors are staged in shared memory, kDescCache at a time
   PieceDesc* dsm = reinterpret_cast<PieceDesc*>(smem + S.vec_bytes);
@@ -156,10 +158,10 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
     if (warp * kRowsPerWarp < n) {  // warp-uniform: this warp has rows in the piece
       const bool active = lane_ok && trow < n;
       const unsigned char* rec = gs + pd.off;
-      const unsigned char* cb = rec + 2 * (w + n);
-      const unsigned char* vb = rec + pd.voff + (kind ? 9 * (size_t)n * FE : 0);
-      // Issue every load of this row's slots at once: slot s starts at block
-      // c0[s] = cnt[0] + .. + cnt[s-1] of the record (counts from the descriptor).
+      // 32-bit byte offsets from the block's (uniform) stream base: the
+      // warp-uniform part per slot plus this thread's fixed part
+      const uint32_t vbase = pd.off + pd.voff + (kind ? 9u * (uint32_t)n * FE : 0u);
+      const uint32_t cbase = pd.off + 2u * (uint32_t)(w + n);
       int col[kDescSlots];
       TV bv[kDescSlots][3];
       uint32_t c0 = 0;
@@ -169,21 +171,21 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
         const uint32_t cs = pd.cnt[sl];  // 0 beyond w
         const bool has = active && sl < w && (uint32_t)trow < cs;
         nsl += has;
-        col[sl] = has ? gu16(cb + 2 * (c0 + (uint32_t)trow)) : 0;
-        const unsigned char* vo = vb + (9 * (size_t)c0 + (size_t)(3 * trow + comp)) * FE;
-        const size_t cstride = 3 * (size_t)cs * FE;
+        col[sl] = has ? gu16(gs + (cbase + 2u * c0 + trow2)) : 0;
+        const uint32_t vo = vbase + 9u * FE * c0 + lane_voff;
+        const uint32_t cstride = 3u * FE * cs;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) bv[sl][c] = has ? gfactor<TF>(vo + c * cstride) : TV(0);
+        for (int c = 0; c < 3; ++c) bv[sl][c] = has ? gfactor<TF>(gs + (vo + (uint32_t)c * cstride)) : TV(0);
         c0 += cs;
       }
       TV d[3] = {TV(0), TV(0), TV(0)};
       if (kind && active) {
-        const unsigned char* io = rec + pd.voff + (size_t)(3 * trow + comp) * FE;
-        const size_t cstride = 3 * (size_t)n * FE;
+        const uint32_t io = pd.off + pd.voff + lane_voff;
+        const uint32_t cstride = 3u * FE * (uint32_t)n;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) d[c] = gfactor<TF>(io + c * cstride);
+        for (int c = 0; c < 3; ++c) d[c] = gfactor<TF>(gs + (io + (uint32_t)c * cstride));
       }
-      const int row = active ? gu16(rec + 2 * (w + trow)) : 0;
+      const int row = active ? gu16(gs + (pd.off + 2u * (uint32_t)w + trow2)) : 0;
       TV acc = active ? y[3 * row + comp] : TV(0);
       if (kind) {
         // D^-1 (Section 4.3): w_i = D_i^-1 y_i; the row's three components
@@ -211,12 +213,12 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
           for (int sl = kDescSlots; sl < w; ++sl) {
             const uint32_t cs = (uint32_t)gu16(rec + 2 * sl);
             if ((uint32_t)trow >= cs) break;
-            const int cl = gu16(cb + 2 * (c0 + (uint32_t)trow));
-            const unsigned char* vo = vb + (9 * (size_t)c0 + (size_t)(3 * trow + comp)) * FE;
-            const size_t cstride = 3 * (size_t)cs * FE;
-            acc = mac(-gfactor<TF>(vo), y[3 * cl], acc);
-            acc = mac(-gfactor<TF>(vo + cstride), y[3 * cl + 1], acc);
-            acc = mac(-gfactor<TF>(vo + 2 * cstride), y[3 * cl + 2], acc);
+            const int cl = gu16(gs + (cbase + 2u * c0 + trow2));
+            const uint32_t vo = vbase + 9u * FE * c0 + lane_voff;
+            const uint32_t cstride = 3u * FE * cs;
+            acc = mac(-gfactor<TF>(gs + vo), y[3 * cl], acc);
+            acc = mac(-gfactor<TF>(gs + (vo + cstride)), y[3 * cl + 1], acc);
+            acc = mac(-gfactor<TF>(gs + (vo + 2u * cstride)), y[3 * cl + 2], acc);
             c0 += cs;
           }
         }
