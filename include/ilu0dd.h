@@ -135,6 +135,39 @@ int ilu0_dd_workspace_size(const ilu0dd_bsr* A, const ilu0dd_geom* geom, const i
 int ilu0_dd_setup(const ilu0dd_bsr* A, const ilu0dd_geom* geom, const ilu0dd_opts* opts,
                   void* d_workspace, size_t ws_bytes, void* stream, ilu0dd_ctx** out);
 
+/* ---- two-phase setup: plan once on the host, factor on the device ------- */
+
+typedef struct ilu0dd_plan ilu0dd_plan;
+
+/*
+ * The structural half of ilu0_dd_setup on the host (Algorithm 2, Algorithm 3,
+ * the drop of Section 3.2, Algorithm 5 level sets, the packing layout), run
+ * once. Reports the device workspace bytes (*workspace_bytes, as
+ * ilu0_dd_workspace_size) and the device scratch bytes (*scratch_bytes) that
+ * ilu0_dd_setup_planned needs to factor and pack on the device; either
+ * pointer may be NULL. Only A's pattern is read. On success *out owns host
+ * memory released by ilu0dd_plan_destroy. Errors as ilu0_dd_workspace_size.
+ */
+int ilu0dd_plan_create(const ilu0dd_bsr* A, const ilu0dd_geom* geom, const ilu0dd_opts* opts,
+                       ilu0dd_plan** out, size_t* workspace_bytes, size_t* scratch_bytes);
+
+/*
+ * The numeric half: as ilu0_dd_setup, for a matrix with the pattern given to
+ * ilu0dd_plan_create (n_brows and nnzb are checked, the pattern is not).
+ * With d_scratch (device, >= *scratch_bytes of the plan, 256-byte aligned)
+ * the block ILU0 (Algorithm 7; one thread block per subdomain, one thread per
+ * row of an L level) and the packing of the factor stream and of the SpMV
+ * matrix run on the device, bit-identical to the host path; with d_scratch ==
+ * NULL they run on the host. The scratch is free for other use on return.
+ * The plan is consumed (it may be used once) and must still be destroyed.
+ * Errors: INVALID (plan already used, size mismatch, DF64 range),
+ * ZERO_PIVOT, WORKSPACE (workspace or scratch too small or misaligned), CUDA.
+ */
+int ilu0_dd_setup_planned(ilu0dd_plan* plan, const ilu0dd_bsr* A, void* d_workspace, size_t ws_bytes,
+                          void* d_scratch, size_t scratch_bytes, void* stream, ilu0dd_ctx** out);
+
+int ilu0dd_plan_destroy(ilu0dd_plan* plan);
+
 /*
  * z = M^-1 r = U~^-1 D^-1 L^-1 r (Sections 4.3-4.4), one fused kernel launch.
  * d_r, d_z: device, 3*N doubles each, in the reordered (subdomain-
@@ -264,6 +297,9 @@ int ilu0_dd_history(const ilu0dd_ctx* ctx, double* host_dst, int32_t n);
 #define ILU0DD_X_INVD 10     /* double[N*9]: D^-1 = U_ii^-1 per row */
 #define ILU0DD_X_AP_ROW_PTR 11 /* int32[N+1] reordered full matrix */
 #define ILU0DD_X_AP_COL 12   /* int32[nnzb] */
+#define ILU0DD_X_STREAM 13   /* uint8[Q_STREAM_BYTES]: the packed factor stream (device copy) */
+#define ILU0DD_X_SELL_COL 14 /* int32[sell slots * 32]: sliced-ELL columns of the SpMV matrix (device copy) */
+#define ILU0DD_X_SELL_VAL 15 /* double[sell slots * 32 * 9]: sliced-ELL values (device copy) */
 
 /* Copy one array to host memory (`bytes` must equal its size). Arrays
  * 4..10 need opts.keep_host = 1 at setup. */
@@ -286,6 +322,7 @@ int ilu0_dd_export(const ilu0dd_ctx* ctx, int what, void* host_dst, size_t bytes
 #define ILU0DD_Q_WORKSPACE 14     /* workspace bytes in use */
 #define ILU0DD_Q_APPLY_KERNELS 15 /* kernel launches per apply (always 1) */
 #define ILU0DD_Q_ITER_KERNELS 16  /* kernel launches per BiCGSTAB iteration */
+#define ILU0DD_Q_SELL_SLOTS 17    /* slots of the sliced-ELL SpMV matrix (32 entries each) */
 
 int ilu0_dd_query(const ilu0dd_ctx* ctx, int what, int64_t* value);
 

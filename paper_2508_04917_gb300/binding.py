@@ -25,10 +25,11 @@ PRECISIONS = {"f64": F64, "f32": F32, "bf16": BF16, "df64": DF64}
 
 X_PART_ID, X_PERM, X_IPERM, X_PART_PTR, X_LEVEL_L, X_LEVEL_U = 0, 1, 2, 3, 4, 5
 X_DD_ROW_PTR, X_DD_COL, X_L, X_UT, X_INVD, X_AP_ROW_PTR, X_AP_COL = 6, 7, 8, 9, 10, 11, 12
+X_STREAM, X_SELL_COL, X_SELL_VAL = 13, 14, 15
 
 Q = dict(n=0, nnzb=1, kept=2, nsub=3, nl=4, nu=5, apply_bytes=6, spmv_bytes=7, stream_bytes=8,
          threads=9, smem=10, pieces=11, cuda_error=12, max_levels=13, workspace=14,
-         apply_kernels=15, iter_kernels=16)
+         apply_kernels=15, iter_kernels=16, sell_slots=17)
 
 
 class Ilu0DDError(RuntimeError):
@@ -90,6 +91,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                         ctypes.POINTER(sz)], ctypes.c_int),
             "ilu0_dd_setup": ([ctypes.POINTER(Bsr), ctypes.POINTER(Geom), ctypes.POINTER(Opts), vp, sz, vp,
                                ctypes.POINTER(vp)], ctypes.c_int),
+            "ilu0dd_plan_create": ([ctypes.POINTER(Bsr), ctypes.POINTER(Geom), ctypes.POINTER(Opts),
+                                    ctypes.POINTER(vp), ctypes.POINTER(sz), ctypes.POINTER(sz)], ctypes.c_int),
+            "ilu0_dd_setup_planned": ([vp, ctypes.POINTER(Bsr), vp, sz, vp, sz, vp, ctypes.POINTER(vp)],
+                                      ctypes.c_int),
+            "ilu0dd_plan_destroy": ([vp], ctypes.c_int),
             "ilu0_dd_apply": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_spmv": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_dot": ([vp, vp, vp, vp, vp], ctypes.c_int),
@@ -182,10 +188,12 @@ class Ilu0DD:
 
     ``row_ptr``, ``col``, ``val`` are host arrays of the natural-order BSR
     matrix (``val`` of shape (nnzb, 3, 3) or flat); ``grid`` = (nx, ny, nz),
-    ``sub`` = (sx, sy, sz) are the inputs of Algorithm 2.
+    ``sub`` = (sx, sy, sz) are the inputs of Algorithm 2. ``device_setup``
+    factors and packs on the GPU (ilu0_dd_setup_planned with scratch), else on
+    the host; both give the same bits.
     """
 
-    def __init__(self, row_ptr, col, val, grid, sub, *, device=None, stream=None, **opts):
+    def __init__(self, row_ptr, col, val, grid, sub, *, device=None, stream=None, device_setup=True, **opts):
         import torch
         lib = load()
         self._lib = lib
@@ -194,19 +202,30 @@ class Ilu0DD:
         b, keep = _bsr(row_ptr, col, val)
         g = Geom(*grid, *sub)
         self.opts = default_opts(**opts)
-        n = ctypes.c_size_t(0)
-        rc = lib.ilu0_dd_workspace_size(ctypes.byref(b), ctypes.byref(g), ctypes.byref(self.opts), ctypes.byref(n))
+        plan = ctypes.c_void_p()
+        n, ns = ctypes.c_size_t(0), ctypes.c_size_t(0)
+        rc = lib.ilu0dd_plan_create(ctypes.byref(b), ctypes.byref(g), ctypes.byref(self.opts), ctypes.byref(plan),
+                                    ctypes.byref(n), ctypes.byref(ns))
         if rc:
-            raise Ilu0DDError(rc, "ilu0_dd_workspace_size")
-        with torch.cuda.device(self.device):
-            self.workspace = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=self.device)
-            ctx = ctypes.c_void_p()
-            rc = lib.ilu0_dd_setup(ctypes.byref(b), ctypes.byref(g), ctypes.byref(self.opts),
-                                   ctypes.c_void_p(self.workspace.data_ptr()), ctypes.c_size_t(self.workspace.numel()),
-                                   _stream(stream), ctypes.byref(ctx))
+            raise Ilu0DDError(rc, "ilu0dd_plan_create")
+        try:
+            with torch.cuda.device(self.device):
+                self.workspace = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=self.device)
+                # device setup: scratch for the factorisation and packing, released after setup
+                scratch = (torch.empty(max(int(ns.value), 256), dtype=torch.uint8, device=self.device)
+                           if device_setup else None)
+                ctx = ctypes.c_void_p()
+                rc = lib.ilu0_dd_setup_planned(plan, ctypes.byref(b), ctypes.c_void_p(self.workspace.data_ptr()),
+                                               ctypes.c_size_t(self.workspace.numel()),
+                                               ctypes.c_void_p(scratch.data_ptr() if scratch is not None else None),
+                                               ctypes.c_size_t(scratch.numel() if scratch is not None else 0),
+                                               _stream(stream), ctypes.byref(ctx))
+                del scratch
+        finally:
+            lib.ilu0dd_plan_destroy(plan)
         del keep
         if rc:
-            raise Ilu0DDError(rc, "ilu0_dd_setup")
+            raise Ilu0DDError(rc, "ilu0_dd_setup_planned")
         self._ctx = ctx
         self.n = self.query("n")
         self.size = 3 * self.n
@@ -309,7 +328,9 @@ class Ilu0DD:
                 X_PART_PTR: (np.int32, nsub + 1), X_LEVEL_L: (np.int32, n), X_LEVEL_U: (np.int32, n),
                 X_DD_ROW_PTR: (np.int32, n + 1), X_DD_COL: (np.int32, kept), X_L: (np.float64, 9 * kept),
                 X_UT: (np.float64, 9 * kept), X_INVD: (np.float64, 9 * n), X_AP_ROW_PTR: (np.int32, n + 1),
-                X_AP_COL: (np.int32, self.query("nnzb"))}
+                X_AP_COL: (np.int32, self.query("nnzb")), X_STREAM: (np.uint8, self.query("stream_bytes")),
+                X_SELL_COL: (np.int32, 32 * self.query("sell_slots")),
+                X_SELL_VAL: (np.float64, 9 * 32 * self.query("sell_slots"))}
         dt, cnt = spec[what]
         buf = np.empty(cnt, dt)
         self._check(self._lib.ilu0_dd_export(self._ctx, what, buf.ctypes.data, buf.nbytes), "ilu0_dd_export")

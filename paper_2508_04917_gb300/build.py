@@ -1,6 +1,6 @@
 """Build the CUDA library ``libilu0dd.so`` in-tree (sm_103a only).
 
-Three translation units (host setup, kernels, C ABI) compile in parallel with
+The translation units compile in parallel with
 nvcc and link with the static CUDA runtime.  Host code is compiled without
 floating-point contraction so x86-64 and aarch64 hosts give identical setups.
 """
@@ -15,7 +15,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libilu0dd.so")
-SOURCES = ["setup.cpp", "kernels.cu", "capi.cu", "batch.cu", "noalloc.cu"]
+SOURCES = ["setup.cpp", "kernels.cu", "capi.cu", "batch.cu", "noalloc.cu", "setup_dev.cu"]
+# the device setup repeats the host setup's arithmetic bit for bit: no contraction
+EXTRA_FLAGS = {"setup_dev.cu": ["--fmad=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_FLAGS = "-fPIC,-O2,-ffp-contract=off,-fno-fast-math,-Wall,-Wno-unused-function"
 
@@ -49,7 +51,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, src + ".o")
-        cmd = [cc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", HOST_FLAGS,
+        cmd = [cc, *ARCH, "-O3", "-lineinfo", "-std=c++17", *EXTRA_FLAGS.get(src, []), "-Xcompiler", HOST_FLAGS,
                "-Xptxas", "-v" if verbose else "-O3", "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "setup_dev.h"
 
 using namespace ilu0dd;
 
@@ -48,6 +49,169 @@ int max_smem_optin() {
     return 232448;  // sm_103 opt-in limit: lets the structural query run without a device
   }
   return v;
+}
+
+}  // namespace
+
+namespace {
+
+// The numeric half of setup (ILU0, ILDU0, packing, upload) for a context whose
+// plan is in place. d_scratch != nullptr runs ILU0 and the packing on the
+// device (setup_dev.cu); else on the host. Deletes the context on failure.
+int setup_numeric(ilu0dd_ctx* c, const ilu0dd_bsr* A, const ilu0dd_opts& o, void* d_workspace, size_t ws_bytes,
+                  void* d_scratch, size_t scratch_bytes, void* stream, double t0, ilu0dd_ctx** out) {
+  Plan& p = c->plan;
+  if (!d_workspace || ws_bytes < p.lay.total || (reinterpret_cast<uintptr_t>(d_workspace) & 255)) {
+    delete c;
+    return ILU0DD_ERR_WORKSPACE;
+  }
+  const double t1 = wall_seconds();
+  const bool on_device = d_scratch != nullptr;
+  int rc = ILU0DD_OK;
+  int32_t bad = -1;
+  std::vector<double> F, invD;
+  std::vector<uint8_t> sbytes;
+  std::vector<int32_t> sell_col;
+  std::vector<double> sell_val;
+  DeviceSetupResult dres;
+  double t2 = t1, t3 = t1;
+  if (on_device) {
+    rc = setup_on_device(p, A->val, static_cast<unsigned char*>(d_scratch), scratch_bytes,
+                         static_cast<unsigned char*>(d_workspace), reinterpret_cast<cudaStream_t>(stream), &dres);
+    t2 = t3 = wall_seconds();
+    if (rc == ILU0DD_ERR_CUDA) {
+      int r = cuda_fail(c, dres.cuda, "device setup");
+      delete c;
+      return r;
+    }
+    if (rc) {
+      if (rc == ILU0DD_ERR_ZERO_PIVOT) c->why = "zero pivot at reordered row " + std::to_string(dres.bad_row);
+      else if (dres.range_bad) c->why = "a factor magnitude lies outside [2^-70, 2^100], the double-float range";
+      else c->why = "device setup scratch too small or misaligned";
+      if (c->trace) std::fprintf(stderr, "[ilu0dd] setup: %s\n", c->why.c_str());
+      delete c;
+      return rc;
+    }
+  } else {
+    rc = factor_ildu0(p, A->val, &F, &invD, &bad);
+    if (rc) {
+      if (c->trace) std::fprintf(stderr, "[ilu0dd] setup: zero pivot at reordered row %d\n", bad);
+      delete c;
+      return rc;
+    }
+    if (p.factor_prec == ILU0DD_DF64 && !df64_range_ok(F, invD)) {
+      c->why = "a factor magnitude lies outside [2^-70, 2^100], the double-float range";
+      if (c->trace) std::fprintf(stderr, "[ilu0dd] setup: %s\n", c->why.c_str());
+      delete c;
+      return ILU0DD_ERR_INVALID;
+    }
+    t2 = wall_seconds();
+    pack_stream(p, F, invD, &sbytes);
+    pack_sell(p, A->val, &sell_col, &sell_val);
+    t3 = wall_seconds();
+  }
+
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  c->ws = static_cast<unsigned char*>(d_workspace);
+  c->ws_bytes = ws_bytes;
+  c->rtol = o.rtol;
+  c->maxit = o.maxit;
+  c->check_every = o.check_every;
+  c->use_graphs = o.use_graphs != 0;
+  {
+    auto up = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
+      if (!bytes) return cudaSuccess;
+      return cudaMemcpyAsync(c->ws + off, src, bytes, cudaMemcpyHostToDevice, s);
+    };
+    const Plan::Layout& L = p.lay;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (!on_device) {  // the device path wrote these already
+      if (e == cudaSuccess) e = up(L.stream, sbytes.data(), sbytes.size());
+      if (e == cudaSuccess) e = up(L.cta, p.cta.data(), sizeof(CtaDesc) * p.cta.size());
+      if (e == cudaSuccess) e = up(L.pieces, p.pieces.data(), sizeof(PieceDesc) * p.pieces.size());
+      if (e == cudaSuccess) e = up(L.sell_off, p.slice_off.data(), sizeof(int32_t) * p.slice_off.size());
+      if (e == cudaSuccess) e = up(L.sell_col, sell_col.data(), sizeof(int32_t) * sell_col.size());
+      if (e == cudaSuccess) e = up(L.sell_val, sell_val.data(), sizeof(double) * sell_val.size());
+    }
+    if (e == cudaSuccess) e = up(L.perm, p.perm.data(), sizeof(int32_t) * p.perm.size());
+    if (e == cudaSuccess) e = up(L.iperm, p.iperm.data(), sizeof(int32_t) * p.iperm.size());
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.partials, 0, sizeof(double) * 5 * (size_t)p.ntiles_pow2, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.counters, 0, sizeof(uint32_t) * 16, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.scal, 0, sizeof(SolverScalars), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.err, 0, sizeof(int32_t) * 4, s);
+    for (int v = 0; v < kNumVec && e == cudaSuccess; ++v)
+      e = cudaMemsetAsync(c->ws + L.vec[v], 0, sizeof(double) * 3 * (size_t)p.N, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host staging buffers die below
+    if (e != cudaSuccess) {
+      int r = cuda_fail(c, e, "setup upload");
+      delete c;
+      return r;
+    }
+    DevCtx& d = c->dev;
+    SysDesc& S = d.sd;
+    S.stream = c->ws + L.stream;
+    S.cta = reinterpret_cast<const CtaDesc*>(c->ws + L.cta);
+    S.pieces = reinterpret_cast<const PieceDesc*>(c->ws + L.pieces);
+    S.nsub = p.nsub;
+    S.prefetch_bytes = p.prefetch_bytes;
+    S.vec_bytes = (int)(p.smem_bytes - sizeof(PieceDesc) * kDescCache);
+    S.slice_off = reinterpret_cast<const int32_t*>(c->ws + L.sell_off);
+    S.sell_col = reinterpret_cast<const int32_t*>(c->ws + L.sell_col);
+    S.sell_val = reinterpret_cast<const double*>(c->ws + L.sell_val);
+    S.nslices = p.nslices;
+    S.perm = reinterpret_cast<const int32_t*>(c->ws + L.perm);
+    S.iperm = reinterpret_cast<const int32_t*>(c->ws + L.iperm);
+    S.N = p.N;
+    S.ntiles = p.ntiles;
+    S.ntiles_pow2 = p.ntiles_pow2;
+    for (int v = 0; v < kNumVec; ++v) S.vec[v] = reinterpret_cast<double*>(c->ws + L.vec[v]);
+    S.partials = reinterpret_cast<double*>(c->ws + L.partials);
+    S.counters = reinterpret_cast<uint32_t*>(c->ws + L.counters);
+    S.scal = reinterpret_cast<SolverScalars*>(c->ws + L.scal);
+    S.hist = reinterpret_cast<double*>(c->ws + L.hist);
+    S.err = reinterpret_cast<int32_t*>(c->ws + L.err);
+    d.threads = p.threads;
+    d.factor_prec = o.factor_prec;
+    d.smem_bytes = p.smem_bytes;
+    e = apply_configure(d);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      int r = cuda_fail(c, e, "setup configure");
+      if (c->own) cudaStreamDestroy(c->own);
+      delete c;
+      return r;
+    }
+  }
+  if (o.keep_host) {
+    if (on_device) {  // the host copies the ILDU0 post-processing exactly as factor_ildu0 does
+      const int64_t kept = p.dd_rp[p.N];
+      std::vector<double> W(9 * (size_t)kept);
+      invD.resize(9 * (size_t)p.N);
+      cudaError_t e = cudaMemcpy(W.data(), dres.w, sizeof(double) * W.size(), cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(invD.data(), dres.invd, sizeof(double) * invD.size(), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) {
+        int r = cuda_fail(c, e, "setup keep_host download");
+        delete c;
+        return r;
+      }
+      ildu0_from_w(p, W, invD, &F);
+    }
+    c->F.swap(F);
+    c->invD.swap(invD);
+    c->have_factors = true;
+  }
+  const double t4 = wall_seconds();
+  c->setup_s = t4 - t0;
+  if (c->trace)
+    std::fprintf(stderr,
+                 "[ilu0dd] setup (%s): plan %.3fs factor %.3fs pack %.3fs upload %.3fs; N=%d nsub=%d pieces=%lld "
+                 "threads=%d smem=%zu stream=%lld B\n",
+                 on_device ? "device" : "host", t1 - t0, t2 - t1, t3 - t2, t4 - t3, p.N, p.nsub,
+                 (long long)p.n_pieces, p.threads,
+                 p.smem_bytes, (long long)p.stream_bytes);
+  *out = c;
+  return ILU0DD_OK;
 }
 
 }  // namespace
@@ -115,117 +279,46 @@ int ilu0_dd_setup(const ilu0dd_bsr* A, const ilu0dd_geom* geom, const ilu0dd_opt
     delete c;
     return rc;
   }
-  Plan& p = c->plan;
-  if (!d_workspace || ws_bytes < p.lay.total || (reinterpret_cast<uintptr_t>(d_workspace) & 255)) {
-    delete c;
-    return ILU0DD_ERR_WORKSPACE;
-  }
-  const double t1 = wall_seconds();
-  int32_t bad = -1;
-  std::vector<double> F, invD;
-  rc = factor_ildu0(p, A->val, &F, &invD, &bad);
+  return setup_numeric(c, A, o, d_workspace, ws_bytes, nullptr, 0, stream, t0, out);
+}
+
+int ilu0dd_plan_create(const ilu0dd_bsr* A, const ilu0dd_geom* geom, const ilu0dd_opts* opts, ilu0dd_plan** out,
+                       size_t* workspace_bytes, size_t* scratch_bytes) {
+  if (!A || !geom || !out) return ILU0DD_ERR_INVALID;
+  *out = nullptr;
+  ilu0dd_plan* pl = new (std::nothrow) ilu0dd_plan();
+  if (!pl) return ILU0DD_ERR_INVALID;
+  pl->t0 = wall_seconds();
+  pl->opts = resolved(opts);
+  int rc = make_plan(A, geom, &pl->opts, max_smem_optin(), &pl->plan, &pl->why);
   if (rc) {
-    if (c->trace) std::fprintf(stderr, "[ilu0dd] setup: zero pivot at reordered row %d\n", bad);
-    delete c;
+    if (pl->opts.trace) std::fprintf(stderr, "[ilu0dd] plan: %s\n", pl->why.c_str());
+    delete pl;
     return rc;
   }
-  if (p.factor_prec == ILU0DD_DF64 && !df64_range_ok(F, invD)) {
-    c->why = "a factor magnitude lies outside [2^-70, 2^100], the double-float range";
-    if (c->trace) std::fprintf(stderr, "[ilu0dd] setup: %s\n", c->why.c_str());
-    delete c;
-    return ILU0DD_ERR_INVALID;
-  }
-  const double t2 = wall_seconds();
-  std::vector<uint8_t> sbytes;
-  pack_stream(p, F, invD, &sbytes);
-  std::vector<int32_t> sell_col;
-  std::vector<double> sell_val;
-  pack_sell(p, A->val, &sell_col, &sell_val);
-  const double t3 = wall_seconds();
+  pl->scratch_bytes = device_setup_scratch_bytes(pl->plan);
+  if (workspace_bytes) *workspace_bytes = pl->plan.lay.total;
+  if (scratch_bytes) *scratch_bytes = pl->scratch_bytes;
+  *out = pl;
+  return ILU0DD_OK;
+}
 
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  c->ws = static_cast<unsigned char*>(d_workspace);
-  c->ws_bytes = ws_bytes;
-  c->rtol = o.rtol;
-  c->maxit = o.maxit;
-  c->check_every = o.check_every;
-  c->use_graphs = o.use_graphs != 0;
-  {
-    auto up = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
-      if (!bytes) return cudaSuccess;
-      return cudaMemcpyAsync(c->ws + off, src, bytes, cudaMemcpyHostToDevice, s);
-    };
-    const Plan::Layout& L = p.lay;
-    cudaError_t e = cudaGetDevice(&c->device);
-    if (e == cudaSuccess) e = up(L.stream, sbytes.data(), sbytes.size());
-    if (e == cudaSuccess) e = up(L.cta, p.cta.data(), sizeof(CtaDesc) * p.cta.size());
-    if (e == cudaSuccess) e = up(L.pieces, p.pieces.data(), sizeof(PieceDesc) * p.pieces.size());
-    if (e == cudaSuccess) e = up(L.sell_off, p.slice_off.data(), sizeof(int32_t) * p.slice_off.size());
-    if (e == cudaSuccess) e = up(L.sell_col, sell_col.data(), sizeof(int32_t) * sell_col.size());
-    if (e == cudaSuccess) e = up(L.sell_val, sell_val.data(), sizeof(double) * sell_val.size());
-    if (e == cudaSuccess) e = up(L.perm, p.perm.data(), sizeof(int32_t) * p.perm.size());
-    if (e == cudaSuccess) e = up(L.iperm, p.iperm.data(), sizeof(int32_t) * p.iperm.size());
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.partials, 0, sizeof(double) * 5 * (size_t)p.ntiles_pow2, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.counters, 0, sizeof(uint32_t) * 16, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.scal, 0, sizeof(SolverScalars), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.err, 0, sizeof(int32_t) * 4, s);
-    for (int v = 0; v < kNumVec && e == cudaSuccess; ++v)
-      e = cudaMemsetAsync(c->ws + L.vec[v], 0, sizeof(double) * 3 * (size_t)p.N, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host staging buffers die below
-    if (e != cudaSuccess) {
-      int r = cuda_fail(c, e, "setup upload");
-      delete c;
-      return r;
-    }
-    DevCtx& d = c->dev;
-    SysDesc& S = d.sd;
-    S.stream = c->ws + L.stream;
-    S.cta = reinterpret_cast<const CtaDesc*>(c->ws + L.cta);
-    S.pieces = reinterpret_cast<const PieceDesc*>(c->ws + L.pieces);
-    S.nsub = p.nsub;
-    S.prefetch_bytes = p.prefetch_bytes;
-    S.vec_bytes = (int)(p.smem_bytes - sizeof(PieceDesc) * kDescCache);
-    S.slice_off = reinterpret_cast<const int32_t*>(c->ws + L.sell_off);
-    S.sell_col = reinterpret_cast<const int32_t*>(c->ws + L.sell_col);
-    S.sell_val = reinterpret_cast<const double*>(c->ws + L.sell_val);
-    S.nslices = p.nslices;
-    S.perm = reinterpret_cast<const int32_t*>(c->ws + L.perm);
-    S.iperm = reinterpret_cast<const int32_t*>(c->ws + L.iperm);
-    S.N = p.N;
-    S.ntiles = p.ntiles;
-    S.ntiles_pow2 = p.ntiles_pow2;
-    for (int v = 0; v < kNumVec; ++v) S.vec[v] = reinterpret_cast<double*>(c->ws + L.vec[v]);
-    S.partials = reinterpret_cast<double*>(c->ws + L.partials);
-    S.counters = reinterpret_cast<uint32_t*>(c->ws + L.counters);
-    S.scal = reinterpret_cast<SolverScalars*>(c->ws + L.scal);
-    S.hist = reinterpret_cast<double*>(c->ws + L.hist);
-    S.err = reinterpret_cast<int32_t*>(c->ws + L.err);
-    d.threads = p.threads;
-    d.factor_prec = o.factor_prec;
-    d.smem_bytes = p.smem_bytes;
-    e = apply_configure(d);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
-    if (e != cudaSuccess) {
-      int r = cuda_fail(c, e, "setup configure");
-      if (c->own) cudaStreamDestroy(c->own);
-      delete c;
-      return r;
-    }
-  }
-  if (o.keep_host) {
-    c->F.swap(F);
-    c->invD.swap(invD);
-    c->have_factors = true;
-  }
-  const double t4 = wall_seconds();
-  c->setup_s = t4 - t0;
-  if (c->trace)
-    std::fprintf(stderr,
-                 "[ilu0dd] setup: plan %.3fs factor %.3fs pack %.3fs upload %.3fs; N=%d nsub=%d pieces=%lld "
-                 "threads=%d smem=%zu stream=%lld B\n",
-                 t1 - t0, t2 - t1, t3 - t2, t4 - t3, p.N, p.nsub, (long long)p.n_pieces, p.threads,
-                 p.smem_bytes, (long long)p.stream_bytes);
-  *out = c;
+int ilu0_dd_setup_planned(ilu0dd_plan* plan, const ilu0dd_bsr* A, void* d_workspace, size_t ws_bytes,
+                          void* d_scratch, size_t scratch_bytes, void* stream, ilu0dd_ctx** out) {
+  if (!plan || !A || !out || plan->consumed) return ILU0DD_ERR_INVALID;
+  *out = nullptr;
+  if (A->n_brows != plan->plan.N || A->nnzb != plan->plan.nnzb || (plan->plan.nnzb > 0 && !A->val))
+    return ILU0DD_ERR_INVALID;
+  ilu0dd_ctx* c = new (std::nothrow) ilu0dd_ctx();
+  if (!c) return ILU0DD_ERR_INVALID;
+  c->trace = plan->opts.trace != 0;
+  c->plan = std::move(plan->plan);
+  plan->consumed = true;
+  return setup_numeric(c, A, plan->opts, d_workspace, ws_bytes, d_scratch, scratch_bytes, stream, plan->t0, out);
+}
+
+int ilu0dd_plan_destroy(ilu0dd_plan* plan) {
+  delete plan;
   return ILU0DD_OK;
 }
 
@@ -465,6 +558,17 @@ int ilu0_dd_export(const ilu0dd_ctx* c, int what, void* dst, size_t bytes) {
     case ILU0DD_X_DD_COL: return put(p.dd_col.data(), 4 * p.dd_col.size());
     case ILU0DD_X_AP_ROW_PTR: return put(p.ap_rp.data(), 4 * p.ap_rp.size());
     case ILU0DD_X_AP_COL: return put(p.ap_col.data(), 4 * p.ap_col.size());
+    case ILU0DD_X_STREAM:
+    case ILU0DD_X_SELL_COL:
+    case ILU0DD_X_SELL_VAL: {  // device copies, read back
+      size_t off = p.lay.stream, n = (size_t)p.stream_bytes;
+      if (what == ILU0DD_X_SELL_COL) off = p.lay.sell_col, n = sizeof(int32_t) * (size_t)p.sell_slots * kSlice;
+      if (what == ILU0DD_X_SELL_VAL) off = p.lay.sell_val, n = sizeof(double) * 9 * (size_t)p.sell_slots * kSlice;
+      if (n != bytes) return ILU0DD_ERR_INVALID;
+      if (!n) return ILU0DD_OK;
+      cudaError_t e = cudaMemcpy(dst, c->ws + off, n, cudaMemcpyDeviceToHost);
+      return e == cudaSuccess ? ILU0DD_OK : ILU0DD_ERR_CUDA;
+    }
     case ILU0DD_X_INVD:
       if (!c->have_factors) return ILU0DD_ERR_INVALID;
       return put(c->invD.data(), 8 * c->invD.size());
@@ -504,6 +608,7 @@ int ilu0_dd_query(const ilu0dd_ctx* c, int what, int64_t* v) {
     case ILU0DD_Q_WORKSPACE: *v = (int64_t)p.lay.total; break;
     case ILU0DD_Q_APPLY_KERNELS: *v = 1; break;
     case ILU0DD_Q_ITER_KERNELS: *v = 5; break;
+    case ILU0DD_Q_SELL_SLOTS: *v = p.sell_slots; break;
     default: return ILU0DD_ERR_INVALID;
   }
   return ILU0DD_OK;

@@ -35,3 +35,12 @@ struct ilu0dd_ctx {
   bool have_factors = false;
 };
 
+// Host-side plan object behind the opaque ilu0dd_plan of the C ABI.
+struct ilu0dd_plan {
+  Plan plan;
+  ilu0dd_opts opts{};
+  std::string why;
+  size_t scratch_bytes = 0;
+  double t0 = 0.0;        // start of planning (setup time counts from here)
+  bool consumed = false;  // moved into a context by ilu0_dd_setup_planned
+};

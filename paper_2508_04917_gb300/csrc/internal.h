@@ -156,6 +156,12 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
 int factor_ildu0(const Plan& plan, const double* aval, std::vector<double>* F,
                  std::vector<double>* invD, int32_t* bad_row);
 
+// F from the factored working rows: L at strictly-lower positions, U~ = D^-1 U
+// at strictly-upper ones (the last step of factor_ildu0), from W (L below,
+// U on and above the diagonal, indexed like plan.dd_col) and invD.
+void ildu0_from_w(const Plan& plan, const std::vector<double>& W, const std::vector<double>& invD,
+                  std::vector<double>* F);
+
 // Pack the factor stream (bytes) in the plan's precision.
 // DF64 mode: every nonzero factor magnitude within [2^-70, 2^100], so both
 // floats of a pair stay normal after the split.

@@ -508,6 +508,22 @@ int factor_ildu0(const Plan& p, const double* aval, std::vector<double>* Fp, std
   return ILU0DD_OK;
 }
 
+void ildu0_from_w(const Plan& p, const std::vector<double>& W, const std::vector<double>& invD,
+                  std::vector<double>* Fp) {
+  std::vector<double>& F = *Fp;
+  F.assign(W.size(), 0.0);
+  parallel_for(p.N, [&](int64_t i) {
+    for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1]; ++q) {
+      double* dst = &F[9 * (size_t)q];
+      if (p.dd_col[q] < i) {
+        std::memcpy(dst, &W[9 * (size_t)q], 9 * sizeof(double));
+      } else if (p.dd_col[q] > i) {
+        mul3(&invD[9 * (size_t)i], &W[9 * (size_t)q], dst);
+      }
+    }
+  });
+}
+
 bool df64_range_ok(const std::vector<double>& F, const std::vector<double>& invD) {
   const double lo = std::ldexp(1.0, -70), hi = std::ldexp(1.0, 100);
   auto ok = [&](const std::vector<double>& v) {
