@@ -4,6 +4,8 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <memory>
+#include <utility>
 #include <vector>
 
 #include "../../include/ilu0dd.h"
@@ -102,6 +104,30 @@ enum ApplyMode : int {
   kModeS = 2,       // s <- r - alpha v;            smem <- s
 };
 
+// Allocator that leaves new elements of trivial types uninitialised, so the
+// large plan arrays are first touched (and paged in) by the parallel loops
+// that fill them rather than by a serial zero-fill.
+template <typename T>
+struct NoInitAlloc : std::allocator<T> {
+  template <typename U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  NoInitAlloc() = default;
+  template <typename U>
+  NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+  template <typename U>
+  void construct(U* p) noexcept {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <typename U, typename... A>
+  void construct(U* p, A&&... a) {
+    ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+  }
+};
+template <typename T>
+using RawVec = std::vector<T, NoInitAlloc<T>>;
+
 // Host-side plan: everything derived from the pattern (no values).
 struct Plan {
   int32_t N = 0;
@@ -111,11 +137,13 @@ struct Plan {
   int32_t nsub = 0;
   std::vector<int32_t> part_id, perm, iperm, part_ptr;
   // reordered full matrix
-  std::vector<int32_t> ap_rp, ap_col;
-  std::vector<int64_t> ap_src;      // source block of each reordered block
+  std::vector<int32_t> ap_rp;
+  RawVec<int32_t> ap_col;
+  RawVec<int64_t> ap_src;           // source block of each reordered block
   // dropped matrix (pattern, and position of each kept block in ap)
-  std::vector<int32_t> dd_rp, dd_col;
-  std::vector<int64_t> dd_ap;       // index into ap blocks
+  std::vector<int32_t> dd_rp;
+  RawVec<int32_t> dd_col;
+  RawVec<int64_t> dd_ap;            // index into ap blocks
   int64_t nL = 0, nU = 0;
   std::vector<int32_t> lev_l, lev_u;
   int32_t max_levels = 0;
@@ -129,8 +157,8 @@ struct Plan {
   int64_t n_pieces = 0;
   std::vector<CtaDesc> cta;
   std::vector<PieceDesc> pieces;
-  std::vector<std::vector<int32_t>> piece_rows;   // local rows of each piece, stream order
-  std::vector<int64_t> piece_record_bytes;
+  RawVec<int32_t> piece_rows;                     // local rows of every piece, stream order
+  std::vector<int64_t> piece_rows_off;            // [n_pieces+1] start of each piece's rows
   int64_t stream_bytes = 0;
   // SpMV packing
   int64_t nslices = 0, sell_slots = 0;            // sell_slots = sum of slice widths

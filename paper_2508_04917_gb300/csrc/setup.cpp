@@ -4,7 +4,9 @@
 // contraction so x86-64 and aarch64 hosts produce the same bits.
 #include <algorithm>
 #include <chrono>
+#include <atomic>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <numeric>
 #include <thread>
@@ -140,48 +142,96 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
     *why = "row_ptr[0] must be 0 and row_ptr[N] must equal nnzb";
     return ILU0DD_ERR_INVALID;
   }
-  for (int32_t i = 0; i < N; ++i) {
-    if (rp[i + 1] < rp[i]) { *why = "row_ptr not monotone"; return ILU0DD_ERR_INVALID; }
-    bool diag = false;
-    for (int64_t q = rp[i]; q < rp[i + 1]; ++q) {
-      if (ci[q] < 0 || ci[q] >= N) { *why = "column out of range"; return ILU0DD_ERR_INVALID; }
-      if (q > rp[i] && ci[q] <= ci[q - 1]) { *why = "columns not strictly ascending"; return ILU0DD_ERR_INVALID; }
-      diag |= ci[q] == i;
+  {
+    // pattern checks in parallel; the first bad row (lowest index) is reported
+    std::atomic<int32_t> bad_row{INT32_MAX};
+    parallel_for(N, [&](int64_t i) {
+      int kind = 0;
+      if (rp[i + 1] < rp[i]) {
+        kind = 1;
+      } else {
+        bool diag = false;
+        for (int64_t q = rp[i]; q < rp[i + 1] && !kind; ++q) {
+          if (ci[q] < 0 || ci[q] >= N) kind = 2;
+          else if (q > rp[i] && ci[q] <= ci[q - 1]) kind = 3;
+          diag |= ci[q] == i;
+        }
+        if (!kind && !diag) kind = 4;
+      }
+      if (kind) {
+        int32_t cur = bad_row.load();
+        while ((int32_t)i < cur && !bad_row.compare_exchange_weak(cur, (int32_t)i)) {
+        }
+      }
+    });
+    if (bad_row.load() != INT32_MAX) {
+      const int32_t i = bad_row.load();
+      int kind = 0;  // re-check the reported row alone for its message
+      if (rp[i + 1] < rp[i]) kind = 1;
+      for (int64_t q = rp[i]; !kind && q < rp[i + 1]; ++q) {
+        if (ci[q] < 0 || ci[q] >= N) kind = 2;
+        else if (q > rp[i] && ci[q] <= ci[q - 1]) kind = 3;
+      }
+      *why = kind == 1 ? "row_ptr not monotone"
+             : kind == 2 ? "column out of range"
+             : kind == 3 ? "columns not strictly ascending"
+                         : "missing diagonal block in row " + std::to_string(i);
+      return ILU0DD_ERR_INVALID;
     }
-    if (!diag) { *why = "missing diagonal block in row " + std::to_string(i); return ILU0DD_ERR_INVALID; }
   }
   Plan& p = *P;
   p = Plan();
+  // per-phase wall times (opts.trace)
+  double tprev = wall_seconds();
+  std::string tlog;
+  auto tmark = [&](const char* what) {
+    if (!o->trace) return;
+    const double t = wall_seconds();
+    tlog += std::string(" ") + what + " " + std::to_string((int)((t - tprev) * 1e3)) + "ms";
+    tprev = t;
+  };
   p.N = N;
   p.nnzb = A->nnzb;
   p.geom = *g;
   p.opts = *o;
 
+  tmark("check");
   // ---- Algorithm 2: labels from geometric cuts (ceil-division at the edges)
   const int bx = ceil_div(g->nx, g->sx), by = ceil_div(g->ny, g->sy), bz = ceil_div(g->nz, g->sz);
   p.nsub = bx * by * bz;
   p.part_id.resize(N);
-  for (int k = 0; k < g->nz; ++k)
+  parallel_for(g->nz, [&](int64_t k) {
     for (int j = 0; j < g->ny; ++j)
       for (int i = 0; i < g->nx; ++i)
         p.part_id[(int64_t)i + (int64_t)g->nx * (j + (int64_t)g->ny * k)] =
-            i / g->sx + bx * (j / g->sy + by * (k / g->sz));
+            i / g->sx + bx * (j / g->sy + by * ((int)k / g->sz));
+  });
 
-  // ---- Section 3.1: stable grouping by label (perm[new] = old)
+  // ---- Section 3.1: stable grouping by label (perm[new] = old). A label's
+  // cells in natural order are its box's cells in (k, j, i) order, so each
+  // subdomain's slice of perm is filled independently.
   p.part_ptr.assign(p.nsub + 1, 0);
-  for (int32_t r = 0; r < N; ++r) p.part_ptr[p.part_id[r] + 1]++;
-  for (int s = 0; s < p.nsub; ++s) p.part_ptr[s + 1] += p.part_ptr[s];
-  {
-    std::vector<int32_t> next(p.part_ptr.begin(), p.part_ptr.end() - 1);
-    p.perm.resize(N);
-    p.iperm.resize(N);
-    for (int32_t r = 0; r < N; ++r) {
-      int32_t nr = next[p.part_id[r]]++;
-      p.perm[nr] = r;
-      p.iperm[r] = nr;
-    }
+  auto box_side = [](int n, int sd, int b) { return std::min(sd, n - b * sd); };
+  for (int s = 0; s < p.nsub; ++s) {
+    const int ib = s % bx, jb = (s / bx) % by, kb = s / (bx * by);
+    p.part_ptr[s + 1] = p.part_ptr[s] + box_side(g->nx, g->sx, ib) * box_side(g->ny, g->sy, jb) *
+                                            box_side(g->nz, g->sz, kb);
   }
+  p.perm.resize(N);
+  p.iperm.resize(N);
+  parallel_for(p.nsub, [&](int64_t s) {
+    const int ib = (int)(s % bx), jb = (int)((s / bx) % by), kb = (int)(s / ((int64_t)bx * by));
+    int32_t nr = p.part_ptr[s];
+    for (int k = kb * g->sz; k < std::min(g->nz, (kb + 1) * g->sz); ++k)
+      for (int j = jb * g->sy; j < std::min(g->ny, (jb + 1) * g->sy); ++j)
+        for (int i = ib * g->sx; i < std::min(g->nx, (ib + 1) * g->sx); ++i) {
+          const int32_t r = (int32_t)((int64_t)i + (int64_t)g->nx * (j + (int64_t)g->ny * k));
+          p.perm[nr] = r;
+          p.iperm[r] = nr++;
+        }
+  });
 
+  tmark("label+perm");
   // ---- Algorithm 3 on BSR: reorder rows and columns, sort each row
   p.ap_rp.resize(N + 1);
   p.ap_rp[0] = 0;
@@ -203,15 +253,17 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
     }
   });
 
+  tmark("reorder");
   // ---- Section 3.2: drop blocks whose row and column lie in different subdomains
   std::vector<int32_t> label(N);
-  for (int32_t i = 0; i < N; ++i) label[i] = p.part_id[p.perm[i]];
+  parallel_for(N, [&](int64_t i) { label[i] = p.part_id[p.perm[i]]; });
   p.dd_rp.assign(N + 1, 0);
-  for (int32_t i = 0; i < N; ++i) {
+  parallel_for(N, [&](int64_t i) {
     int32_t c = 0;
     for (int64_t q = p.ap_rp[i]; q < p.ap_rp[i + 1]; ++q) c += label[p.ap_col[q]] == label[i];
-    p.dd_rp[i + 1] = p.dd_rp[i] + c;
-  }
+    p.dd_rp[i + 1] = c;
+  });
+  for (int32_t i = 0; i < N; ++i) p.dd_rp[i + 1] += p.dd_rp[i];
   int64_t kept = p.dd_rp[N];
   p.dd_col.resize(kept);
   p.dd_ap.resize(kept);
@@ -223,12 +275,22 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
         p.dd_ap[d++] = q;
       }
   });
-  for (int32_t i = 0; i < N; ++i)
-    for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1]; ++q) {
-      p.nL += p.dd_col[q] < i;
-      p.nU += p.dd_col[q] > i;
+  {
+    std::vector<int64_t> nl(p.nsub, 0), nu(p.nsub, 0);
+    parallel_for(p.nsub, [&](int64_t s) {
+      for (int32_t i = p.part_ptr[s]; i < p.part_ptr[s + 1]; ++i)
+        for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1]; ++q) {
+          nl[s] += p.dd_col[q] < i;
+          nu[s] += p.dd_col[q] > i;
+        }
+    });
+    for (int s = 0; s < p.nsub; ++s) {
+      p.nL += nl[s];
+      p.nU += nu[s];
     }
+  }
 
+  tmark("drop");
   // ---- Algorithm 5 (level sets of each subdomain's L and U DAG)
   p.lev_l.assign(N, 0);
   p.lev_u.assign(N, 0);
@@ -253,6 +315,7 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
     nlev_u[s] = r1 > r0 ? mu : 0;
   });
 
+  tmark("levels");
   // ---- apply configuration
   const int fp = o->factor_prec;
   if (fp != ILU0DD_F64 && fp != ILU0DD_F32 && fp != ILU0DD_BF16 && fp != ILU0DD_DF64) {
@@ -301,31 +364,47 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   // ---- pieces: per subdomain, L levels 1.. then U levels 0.., rows of a level
   // sorted by block count (longest first), split by the block's row capacity
   p.cta.resize(p.nsub);
-  std::vector<std::vector<std::vector<int32_t>>> sub_pieces(p.nsub);
-  std::vector<std::vector<int64_t>> sub_bytes(p.nsub);
+  // blocks on each side of the diagonal per row (the jagged-diagonal sort key)
+  std::vector<int32_t> nlo(N), nup(N);
+  parallel_for(N, [&](int64_t i) {
+    int32_t lo = 0, up = 0;
+    for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1]; ++q) {
+      lo += p.dd_col[q] < i;
+      up += p.dd_col[q] > i;
+    }
+    nlo[i] = lo;
+    nup[i] = up;
+  });
+  std::vector<std::vector<int32_t>> sub_rows(p.nsub);  // local rows, piece after piece
   std::vector<std::vector<PieceDesc>> sub_desc(p.nsub);
+  std::vector<int64_t> sub_len(p.nsub, 0);
   std::vector<int> sub_fail(p.nsub, 0);
   parallel_for(p.nsub, [&](int64_t s) {
-    int32_t r0 = p.part_ptr[s], r1 = p.part_ptr[s + 1];
-    auto nblk = [&](int32_t i, int kind) {
-      int32_t c = 0;
-      for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1]; ++q)
-        c += kind ? (p.dd_col[q] > i) : (p.dd_col[q] < i);
-      return c;
-    };
+    const int32_t r0 = p.part_ptr[s], r1 = p.part_ptr[s + 1];
+    std::vector<int32_t>& out = sub_rows[s];
+    out.reserve(2 * (size_t)(r1 - r0));
+    std::vector<int32_t> start, byl;
+    std::vector<std::pair<int32_t, int32_t>> key;  // (-blocks, row)
     uint32_t off = 0;
     for (int kind = 0; kind < 2; ++kind) {
-      int32_t nl = kind ? nlev_u[s] : nlev_l[s];
-      std::vector<std::vector<int32_t>> by_level(nl);
-      for (int32_t i = r0; i < r1; ++i) {
-        int32_t l = kind ? p.lev_u[i] : p.lev_l[i];
-        if (kind == 0 && l == 0) continue;
-        by_level[l].push_back(i);
+      const int32_t nl = kind ? nlev_u[s] : nlev_l[s];
+      const std::vector<int32_t>& lev = kind ? p.lev_u : p.lev_l;
+      // rows grouped by level (counting sort, ascending rows within a level)
+      start.assign((size_t)nl + 1, 0);
+      for (int32_t i = r0; i < r1; ++i) start[lev[i] + 1]++;
+      for (int32_t l = 0; l < nl; ++l) start[l + 1] += start[l];
+      byl.resize((size_t)(r1 - r0));
+      {
+        std::vector<int32_t> next(start.begin(), start.end() - 1);
+        for (int32_t i = r0; i < r1; ++i) byl[next[lev[i]]++] = i;
       }
-      for (auto& rows : by_level) {
-        if (rows.empty()) continue;
-        std::vector<std::pair<int32_t, int32_t>> key;  // (-blocks, row)
-        for (int32_t i : rows) key.push_back({-nblk(i, kind), i});
+      for (int32_t l = kind ? 0 : 1; l < nl; ++l) {
+        if (start[l + 1] == start[l]) continue;
+        key.clear();
+        for (int32_t x = start[l]; x < start[l + 1]; ++x) {
+          const int32_t i = byl[x];
+          key.push_back({-(kind ? nup[i] : nlo[i]), i});
+        }
         std::sort(key.begin(), key.end());
         size_t a = 0;
         while (a < key.size()) {
@@ -343,8 +422,7 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
           int64_t voff;
           int64_t bytes = record_bytes(n, w, nb, kind, p.factor_elem, &voff);
           if (bytes > cap || w > 255) sub_fail[s] = 1;
-          std::vector<int32_t> pr;
-          for (size_t t = a; t < b; ++t) pr.push_back(key[t].second - r0);
+          for (size_t t = a; t < b; ++t) out.push_back(key[t].second - r0);
           PieceDesc d{};
           d.off = off;
           d.meta = (uint32_t)n | ((uint32_t)w << 16) | ((uint32_t)kind << 24);
@@ -356,8 +434,7 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
             d.cnt[sl] = (uint16_t)c;
           }
           sub_desc[s].push_back(d);
-          sub_pieces[s].push_back(std::move(pr));
-          sub_bytes[s].push_back(bytes);
+          sub_len[s] += bytes;
           off += (uint32_t)bytes;
           a = b;
         }
@@ -369,11 +446,11 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
       *why = "a piece record exceeds 1 GiB or has more than 255 blocks per row";
       return ILU0DD_ERR_SMEM;
     }
-  int64_t soff = 0;
+  int64_t soff = 0, npc = 0, nrw = 0;
+  std::vector<int64_t> row_at(p.nsub);
   for (int s = 0; s < p.nsub; ++s) {
     CtaDesc& c = p.cta[s];
-    int64_t len = 0;
-    for (int64_t b : sub_bytes[s]) len += b;
+    const int64_t len = sub_len[s];
     if (len >= (1ll << 31)) {
       *why = "subdomain stream exceeds 2 GiB";
       return ILU0DD_ERR_INVALID;
@@ -382,15 +459,29 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
     c.stream_len = (int32_t)len;
     c.row0 = p.part_ptr[s];
     c.nrows = p.part_ptr[s + 1] - p.part_ptr[s];
-    c.piece0 = (int32_t)p.pieces.size();
+    c.piece0 = (int32_t)npc;
     c.npieces = (int32_t)sub_desc[s].size();
     c.pad = 0;
     p.max_pieces = std::max(p.max_pieces, c.npieces);
-    for (auto& d : sub_desc[s]) p.pieces.push_back(d);
-    for (auto& r : sub_pieces[s]) p.piece_rows.push_back(std::move(r));
-    for (auto b : sub_bytes[s]) p.piece_record_bytes.push_back(b);
+    row_at[s] = nrw;
+    npc += c.npieces;
+    nrw += (int64_t)sub_rows[s].size();
     soff = align_up(soff + len, 128);
   }
+  p.pieces.resize((size_t)npc);
+  p.piece_rows.resize((size_t)nrw);
+  p.piece_rows_off.resize((size_t)npc + 1);
+  p.piece_rows_off[npc] = nrw;
+  parallel_for(p.nsub, [&](int64_t s) {
+    const CtaDesc& c = p.cta[s];
+    std::copy(sub_desc[s].begin(), sub_desc[s].end(), p.pieces.begin() + c.piece0);
+    std::copy(sub_rows[s].begin(), sub_rows[s].end(), p.piece_rows.begin() + row_at[s]);
+    int64_t at = row_at[s];
+    for (int32_t k = 0; k < c.npieces; ++k) {
+      p.piece_rows_off[c.piece0 + k] = at;
+      at += (int64_t)(sub_desc[s][k].meta & 0xFFFFu);
+    }
+  });
   p.stream_bytes = soff;
   p.n_pieces = (int64_t)p.pieces.size();
   p.smem_bytes = (size_t)align_up(3ll * p.rmax * p.vec_elem, 128) + sizeof(PieceDesc) * kDescCache;
@@ -401,15 +492,17 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
     return ILU0DD_ERR_SMEM;
   }
 
+  tmark("pieces");
   // ---- sliced ELL for the SpMV
   p.nslices = (N + kSlice - 1) / kSlice;
   p.slice_off.assign(p.nslices + 1, 0);
-  for (int64_t k = 0; k < p.nslices; ++k) {
+  parallel_for(p.nslices, [&](int64_t k) {
     int32_t w = 0;
     for (int64_t r = k * kSlice; r < std::min<int64_t>(N, (k + 1) * kSlice); ++r)
       w = std::max(w, p.ap_rp[r + 1] - p.ap_rp[r]);
-    p.slice_off[k + 1] = p.slice_off[k] + w;
-  }
+    p.slice_off[k + 1] = w;
+  });
+  for (int64_t k = 0; k < p.nslices; ++k) p.slice_off[k + 1] += p.slice_off[k];
   p.sell_slots = p.slice_off[p.nslices];
 
   // ---- dot tiles
@@ -446,6 +539,8 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   // and U + FP64 r in and z out; SpMV: values + columns + row pointers + x, y)
   p.apply_bytes = 9ll * p.factor_elem * (p.nL + p.nU + N) + 4 * (p.nL + p.nU) + 8ll * (N + 1) + 48ll * N;
   p.spmv_bytes = 76ll * p.nnzb + 4ll * (N + 1) + 48ll * N;
+  tmark("sell+layout");
+  if (o->trace) std::fprintf(stderr, "[ilu0dd] plan:%s\n", tlog.c_str());
   return ILU0DD_OK;
 }
 
@@ -545,7 +640,7 @@ void pack_stream(const Plan& p, const std::vector<double>& F, const std::vector<
     const CtaDesc& c = p.cta[s];
     for (int32_t k = 0; k < c.npieces; ++k) {
       const PieceDesc& d = p.pieces[c.piece0 + k];
-      const std::vector<int32_t>& rows = p.piece_rows[c.piece0 + k];
+      const int32_t* rows = &p.piece_rows[p.piece_rows_off[c.piece0 + k]];
       const int n = (int)(d.meta & 0xFFFF), w = (int)((d.meta >> 16) & 0xFF), kind = (int)(d.meta >> 24);
       uint8_t* rec = S.data() + c.stream_off + d.off;
       // blocks of each row (ascending column), strictly lower (kind 0) or upper (kind 1)

@@ -85,11 +85,7 @@ int64_t total_levels_of(const Plan& p) {
   return t;
 }
 
-int64_t total_prows_of(const Plan& p) {
-  int64_t t = 0;
-  for (const auto& r : p.piece_rows) t += (int64_t)r.size();
-  return t;
-}
+int64_t total_prows_of(const Plan& p) { return (int64_t)p.piece_rows.size(); }
 
 // ---------------------------------------------------------------- kernels
 
@@ -319,7 +315,7 @@ int setup_on_device(const Plan& p, const double* aval_host, unsigned char* scrat
   const int64_t kept = p.dd_rp[p.N];
 
   // ---- host: index arrays the kernels read
-  std::vector<int64_t> dd_src((size_t)kept);
+  RawVec<int64_t> dd_src((size_t)kept);
   host_parallel_for(kept, [&](int64_t q) { dd_src[q] = p.ap_src[p.dd_ap[q]]; });
   std::vector<int32_t> order((size_t)p.N), lev_off((size_t)p.nsub + 1), lptr((size_t)(total_levels + p.nsub));
   {
@@ -343,12 +339,8 @@ int setup_on_device(const Plan& p, const double* aval_host, unsigned char* scrat
       for (int32_t i = r0; i < r1; ++i) order[next[p.lev_l[i]]++] = i;  // stable within a level
     });
   }
-  std::vector<int32_t> prow_off((size_t)p.n_pieces + 1), prows((size_t)total_prows), piece_sub((size_t)p.n_pieces);
-  prow_off[0] = 0;
-  for (int64_t k = 0; k < p.n_pieces; ++k) prow_off[k + 1] = prow_off[k] + (int32_t)p.piece_rows[k].size();
-  host_parallel_for(p.n_pieces, [&](int64_t k) {
-    std::copy(p.piece_rows[k].begin(), p.piece_rows[k].end(), prows.begin() + prow_off[k]);
-  });
+  std::vector<int32_t> prow_off((size_t)p.n_pieces + 1), piece_sub((size_t)p.n_pieces);
+  for (int64_t k = 0; k <= p.n_pieces; ++k) prow_off[k] = (int32_t)p.piece_rows_off[k];
   for (int sub = 0; sub < p.nsub; ++sub)
     for (int32_t k = 0; k < p.cta[sub].npieces; ++k) piece_sub[p.cta[sub].piece0 + k] = sub;
 
@@ -368,7 +360,7 @@ int setup_on_device(const Plan& p, const double* aval_host, unsigned char* scrat
   up(L.lev_off, lev_off.data(), sizeof(int32_t) * lev_off.size());
   up(L.lptr, lptr.data(), sizeof(int32_t) * lptr.size());
   up(L.prow_off, prow_off.data(), sizeof(int32_t) * prow_off.size());
-  up(L.prows, prows.data(), sizeof(int32_t) * prows.size());
+  up(L.prows, p.piece_rows.data(), sizeof(int32_t) * p.piece_rows.size());
   up(L.piece_sub, piece_sub.data(), sizeof(int32_t) * piece_sub.size());
   if (e == cudaSuccess) e = cudaMemcpyAsync(ws + p.lay.cta, p.cta.data(), sizeof(CtaDesc) * p.cta.size(),
                                             cudaMemcpyHostToDevice, s);
