@@ -303,10 +303,21 @@ def run_ours(args):
             err = float((x.cpu().numpy() - s.xstar).__abs__().max() / np.abs(s.xstar).max())
             zp = torch.empty_like(r)
             ams = time_apply_warm(c, r, zp, 20)  # the factor stream exceeds L2
+            # fusion ablation: the same apply as two launches (L, then D^-1 and U~)
+            for _ in range(3):
+                c.apply_unfused(r, zp)
+            u0, u1 = _events()
+            u0.record()
+            for _ in range(20):
+                c.apply_unfused(r, zp)
+            u1.record()
+            torch.cuda.synchronize()
+            ums = u0.elapsed_time(u1) / 20
             solves[prec] = {"s": round(wall, 5), "iterations": info["iterations"], "restarts": info["restarts"],
                             "rel_res_true": info["rel_res_true"], "setup_s": round(su, 3),
                             "max_rel_err_vs_xstar": err, "status": info["status"],
-                            "apply_ms": round(ams, 5), "apply_bytes": c.query("apply_bytes"),
+                            "apply_ms": round(ams, 5), "apply_unfused_ms": round(ums, 5),
+                            "fusion_speedup": round(ums / ams, 3), "apply_bytes": c.query("apply_bytes"),
                             "apply_gbs": round(c.query("apply_bytes") / ams / 1e6, 1)}
             c.close()
         if "f64" in solves:

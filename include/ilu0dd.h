@@ -177,6 +177,17 @@ int ilu0dd_plan_destroy(ilu0dd_plan* plan);
 int ilu0_dd_apply(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream);
 
 /*
+ * The same z = M^-1 r as ilu0_dd_apply, unfused: two launches, the L sweep
+ * (r -> z) and then the D^-1 and U~ sweep (z -> z in place), each loading
+ * the subdomain vector into shared memory; the separate-kernel variant of
+ * the paper's preconditioner-application comparison (Section 5, Table 4),
+ * kept to measure what the fusion of Section 4.4 saves. Same arguments,
+ * results bit-identical to ilu0_dd_apply for FP64, FP32 and BF16 factors
+ * (DF64 rescales between the launches: equal to rounding).
+ */
+int ilu0_dd_apply_unfused(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream);
+
+/*
  * y = A_p x with the full reordered matrix (all inter-subdomain blocks kept,
  * Section 3.2 last paragraph). Device vectors in the reordered numbering,
  * 3*N doubles each, not overlapping. Asynchronous on `stream`.

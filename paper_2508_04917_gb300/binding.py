@@ -97,6 +97,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                       ctypes.c_int),
             "ilu0dd_plan_destroy": ([vp], ctypes.c_int),
             "ilu0_dd_apply": ([vp, vp, vp, vp], ctypes.c_int),
+            "ilu0_dd_apply_unfused": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_spmv": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_dot": ([vp, vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_permute": ([vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
@@ -256,6 +257,13 @@ class Ilu0DD:
         z = self._new() if z is None else z
         self._check(self._lib.ilu0_dd_apply(self._ctx, _dptr(r, self.size, "r"), _dptr(z, self.size, "z"),
                                             _stream(stream)), "ilu0_dd_apply")
+        return z
+
+    def apply_unfused(self, r, z=None, stream=None):
+        """z = M^-1 r in two launches (L sweep, then D^-1 and U~ sweep)."""
+        z = self._new() if z is None else z
+        self._check(self._lib.ilu0_dd_apply_unfused(self._ctx, _dptr(r, self.size, "r"), _dptr(z, self.size, "z"),
+                                                    _stream(stream)), "ilu0_dd_apply_unfused")
         return z
 
     def spmv(self, x, y=None, stream=None):

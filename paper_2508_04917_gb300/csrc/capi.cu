@@ -333,6 +333,17 @@ int ilu0_dd_apply(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* s
   return ILU0DD_OK;
 }
 
+int ilu0_dd_apply_unfused(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream) {
+  if (!ctx || (ctx->plan.N > 0 && (!d_r || !d_z))) return ILU0DD_ERR_INVALID;
+  const size_t n = 3 * (size_t)ctx->plan.N * sizeof(double);
+  const char* r = reinterpret_cast<const char*>(d_r);
+  const char* z = reinterpret_cast<const char*>(d_z);
+  if (r < z + n && z < r + n) return ILU0DD_ERR_INVALID;  // overlapping vectors
+  cudaError_t e = launch_apply_unfused(ctx->dev, d_r, d_z, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(const_cast<ilu0dd_ctx*>(ctx), e, "unfused apply launch");
+  return ILU0DD_OK;
+}
+
 int ilu0_dd_spmv(const ilu0dd_ctx* ctx, const double* d_x, double* d_y, void* stream) {
   if (!ctx || (ctx->plan.N > 0 && (!d_x || !d_y)) || d_x == d_y) return ILU0DD_ERR_INVALID;
   cudaError_t e = launch_spmv(ctx->dev, 0, d_x, d_y, reinterpret_cast<cudaStream_t>(stream));

@@ -60,7 +60,7 @@ struct CtaDesc {            // 32 bytes, one per subdomain
   int32_t nrows;            // rows of the subdomain
   int32_t piece0;           // first PieceDesc
   int32_t npieces;
-  int32_t pad;
+  int32_t npieces_l;        // the first npieces_l pieces are the L sweep's
 };
 
 // Device-resident BiCGSTAB scalars (Algorithm 1). Written by the last block of

@@ -57,7 +57,9 @@ __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 // the FP32 exponent range never limits it.
 // Modes: plain z = M^-1 r; P: p <- r + beta (p - omega v), z = M^-1 p;
 // S: s <- r - alpha v, z = M^-1 s. Modes P and S skip a finished solve.
-template <typename TF, int MODE>
+// PART 0 runs every piece (the fused apply); 1 only the L sweep, 2 only the
+// D^-1 and U~ sweep (the two launches of the unfused apply).
+template <typename TF, int MODE, int PART = 0>
 __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const double* r, double* z) {
   using TV = typename FactorLoad<TF>::compute;
   constexpr uint32_t FE = sizeof(TF);
@@ -71,7 +73,9 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
   const uint32_t len = (uint32_t)cd.stream_len;
   const uint32_t dist = (uint32_t)S.prefetch_bytes;
   constexpr uint32_t kPf = 16384;  // bytes per L2 prefetch instruction
-  uint32_t pf_end = 0;             // prefetched prefix of the stream (thread 0)
+  const int k0 = PART == 2 ? cd.npieces_l : 0;             // pieces [k0, k1) run here
+  const int k1 = PART == 1 ? cd.npieces_l : cd.npieces;
+  uint32_t pf_end = PART == 2 && k0 < k1 ? S.pieces[cd.piece0 + k0].off : 0;  // prefetched prefix
   auto prefetch_upto = [&](uint32_t upto) {
     upto = min(upto, len);
     while (pf_end < upto) {
@@ -83,7 +87,7 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
   // L2 prefetches come from lane 0 of the last warp, which has rows only in the
   // widest levels, so the issue cost stays off the other warps' paths
   const bool pf_thread = tid == (int)blockDim.x - 32;
-  if (pf_thread) prefetch_upto(dist);
+  if (pf_thread) prefetch_upto(pf_end + dist);
 
   // subdomain vector -> shared memory (with the fused BiCGSTAB update)
   const int64_t base = 3ll * cd.row0;
@@ -141,16 +145,16 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
 
   // piece descriptors are staged in shared memory, kDescCache at a time
   PieceDesc* dsm = reinterpret_cast<PieceDesc*>(smem + S.vec_bytes);
-  for (int k = 0; k < cd.npieces; ++k) {
-    if (k % kDescCache == 0) {
-      if (k > 0) __syncthreads();
-      const int cnt = min(kDescCache, cd.npieces - k);
+  for (int k = k0; k < k1; ++k) {
+    if ((k - k0) % kDescCache == 0) {
+      if (k > k0) __syncthreads();
+      const int cnt = min(kDescCache, k1 - k);
       const uint4* src = reinterpret_cast<const uint4*>(S.pieces + cd.piece0 + k);
       uint4* dst = reinterpret_cast<uint4*>(dsm);
       for (int q = tid; q < 2 * cnt; q += blockDim.x) dst[q] = __ldg(src + q);
       __syncthreads();
     }
-    const PieceDesc pd = dsm[k % kDescCache];
+    const PieceDesc pd = dsm[(k - k0) % kDescCache];
     if (pf_thread) prefetch_upto(pd.off + dist);
     const int n = (int)(pd.meta & 0xFFFFu);
     const int w = (int)((pd.meta >> 16) & 0xFFu);
@@ -253,6 +257,14 @@ __global__ void __launch_bounds__(kMaxApplyThreads, ApplyMinBlocks<TF>::value)
   apply_block<TF, MODE>(S, blockIdx.x, r, z);
 }
 
+// The unfused apply's two launches (plain mode): PART 1 = L sweep, r -> z;
+// PART 2 = D^-1 and U~ sweep, z -> z in place.
+template <typename TF, int PART>
+__global__ void __launch_bounds__(kMaxApplyThreads, ApplyMinBlocks<TF>::value)
+    ildu0_apply_part_kernel(SysDesc S, const double* r, double* z) {
+  apply_block<TF, kModePlain, PART>(S, blockIdx.x, r, z);
+}
+
 // Batched apply (modes P and S): persistent blocks walk (system, subdomain) items.
 template <typename TF, int MODE>
 __global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
@@ -271,6 +283,10 @@ static cudaError_t configure_one(size_t smem) {
                                        (int)smem);
   if (e == cudaSuccess && MODE != kModePlain)
     e = cudaFuncSetAttribute(ildu0_apply_batched<TF, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && MODE == kModePlain)
+    e = cudaFuncSetAttribute(ildu0_apply_part_kernel<TF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && MODE == kModePlain)
+    e = cudaFuncSetAttribute(ildu0_apply_part_kernel<TF, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return e;
 }
 
@@ -318,6 +334,24 @@ cudaError_t launch_apply(const DevCtx& d, int mode, const double* r, double* z, 
   if (d.factor_prec == ILU0DD_F32) return launch_apply_t<float>(d, mode, r, z, s);
   if (d.factor_prec == ILU0DD_DF64) return launch_apply_t<df64s>(d, mode, r, z, s);
   return launch_apply_t<bf16s>(d, mode, r, z, s);
+}
+
+template <typename TF>
+static cudaError_t launch_unfused_t(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
+  dim3 grid(d.sd.nsub), block(d.threads);
+  ildu0_apply_part_kernel<TF, 1><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ildu0_apply_part_kernel<TF, 2><<<grid, block, d.smem_bytes, s>>>(d.sd, z, z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_unfused(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
+  if (d.sd.nsub == 0) return cudaSuccess;
+  if (d.factor_prec == ILU0DD_F64) return launch_unfused_t<double>(d, r, z, s);
+  if (d.factor_prec == ILU0DD_F32) return launch_unfused_t<float>(d, r, z, s);
+  if (d.factor_prec == ILU0DD_DF64) return launch_unfused_t<df64s>(d, r, z, s);
+  return launch_unfused_t<bf16s>(d, r, z, s);
 }
 
 template <typename TF>

@@ -53,6 +53,10 @@ cudaError_t apply_configure(const DevCtx& d);
 // z = M^-1 r (mode plain), or the fused BiCGSTAB variants (modes P and S).
 cudaError_t launch_apply(const DevCtx& d, int mode, const double* r, double* z, cudaStream_t s);
 
+// The same z = M^-1 r in two launches (L sweep r -> z, then D^-1 and U~ sweep
+// z -> z in place), the unfused variant of the fusion ablation.
+cudaError_t launch_apply_unfused(const DevCtx& d, const double* r, double* z, cudaStream_t s);
+
 // y = A_p x; kind 0 plain, 1: v = A ph with (rh.v) -> alpha, 2: t = A sh with (t.s),(t.t) -> omega.
 cudaError_t launch_spmv(const DevCtx& d, int kind, const double* x, double* y, cudaStream_t s);
 

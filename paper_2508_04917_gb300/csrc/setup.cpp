@@ -461,7 +461,8 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
     c.nrows = p.part_ptr[s + 1] - p.part_ptr[s];
     c.piece0 = (int32_t)npc;
     c.npieces = (int32_t)sub_desc[s].size();
-    c.pad = 0;
+    c.npieces_l = 0;
+    for (const PieceDesc& d : sub_desc[s]) c.npieces_l += (d.meta >> 24) == 0;
     p.max_pieces = std::max(p.max_pieces, c.npieces);
     row_at[s] = nrw;
     npc += c.npieces;
