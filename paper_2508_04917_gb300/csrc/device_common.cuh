@@ -242,6 +242,41 @@ __device__ __forceinline__ void fold_strided(const double* const (&part)[NV], do
   }
 }
 
+// The same levels for K >= 16 with O(log K) registers, evaluated depth first.
+// With R(k, h) the value at index k after the levels of stride >= h,
+// R(k, h) = R(k, 2h) + R(k + h, 2h) and R(k, K) = the k-th partial, so the
+// result R(0, 1) is built by visiting the partials in bit-reversed order and
+// merging each finished pair of equal subtrees, left (smaller index) operand
+// first: the same additions on the same operands as the halving loops. Loads
+// are issued eight at a time (a compiler barrier between batches) so only a
+// few are live at once.
+template <int K, int NV>
+__device__ __forceinline__ void fold_strided_deep(const double* const (&part)[NV], double (&q)[NV]) {
+  constexpr int LOG = K <= 1 ? 0 : K <= 2 ? 1 : K <= 4 ? 2 : K <= 8 ? 3 : K <= 16 ? 4 : K <= 32 ? 5 : 6;
+  static_assert((1 << LOG) == K, "K must be a power of two up to 64");
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double stack[LOG + 1];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      int k = 0;  // bit reversal of j over LOG bits
+#pragma unroll
+      for (int b = 0; b < LOG; ++b) k |= ((j >> b) & 1) << (LOG - 1 - b);
+      double val = __ldcg(part[v] + t + k * kDotTile);
+      int l = 0;
+#pragma unroll
+      for (; l < LOG; ++l) {
+        if (!((j >> l) & 1)) break;
+        val = stack[l] + val;
+      }
+      stack[l] = val;
+      if ((j & 7) == 7) asm volatile("" ::: "memory");
+    }
+    q[v] = stack[LOG];
+  }
+}
+
 // Same for larger K: the partial sums are updated in place in global memory
 // (only the block that owns the final reduction runs this).
 template <int NV>
@@ -274,9 +309,9 @@ __device__ __forceinline__ void final_halving_sum(const double* const (&part)[NV
       case 2: fold_strided<2, NV>(part, q); break;
       case 4: fold_strided<4, NV>(part, q); break;
       case 8: fold_strided<8, NV>(part, q); break;
-      case 16: fold_strided<16, NV>(part, q); break;
-      case 32: fold_strided<32, NV>(part, q); break;
-      case 64: fold_strided<64, NV>(part, q); break;
+      case 16: fold_strided_deep<16, NV>(part, q); break;
+      case 32: fold_strided_deep<32, NV>(part, q); break;
+      case 64: fold_strided_deep<64, NV>(part, q); break;
       default: fold_strided_global<NV>(part, m / kDotTile, q); break;
     }
   } else {
