@@ -152,6 +152,32 @@ int ilu0dd_plan_create(const ilu0dd_bsr* A, const ilu0dd_geom* geom, const ilu0d
                        ilu0dd_plan** out, size_t* workspace_bytes, size_t* scratch_bytes);
 
 /*
+ * As ilu0dd_plan_create for a matrix without a grid: the subdomains are the
+ * parts of a given partition (Section 3.1's graph-partition path) instead of
+ * Algorithm 2's boxes. part_id: HOST array of n_brows labels in [0, nparts)
+ * (any partition, e.g. from ilu0dd_partition_bfs or an external graph
+ * partitioner); every part must fit the shared-memory limit of the apply.
+ * Rows of a part keep their relative order (Section 3.1's stable grouping).
+ * Errors: INVALID (pattern, labels out of range), SMEM (a part too large).
+ */
+int ilu0dd_plan_create_partitioned(const ilu0dd_bsr* A, const int32_t* part_id, int32_t nparts,
+                                   const ilu0dd_opts* opts, ilu0dd_plan** out, size_t* workspace_bytes,
+                                   size_t* scratch_bytes);
+
+/*
+ * Graph partition of A's pattern into parts of part_rows rows (the last may
+ * be smaller), the project's stand-in for the METIS partition the paper uses
+ * for matrices without a grid (Section 3.1, equal-size parts as in Section
+ * 5): the vertices in breadth-first order over the pattern of A + A^T
+ * (neighbours ascending), component by component, each component's order
+ * started at the last vertex that a first search from its smallest vertex
+ * reaches; part_id[order[t]] = t / part_rows. Host only, deterministic.
+ * part_id: HOST array of n_brows int32 (written); *nparts receives the number
+ * of parts. Errors: INVALID (null arrays, part_rows <= 0, column out of range).
+ */
+int ilu0dd_partition_bfs(const ilu0dd_bsr* A, int32_t part_rows, int32_t* part_id, int32_t* nparts);
+
+/*
  * The numeric half: as ilu0_dd_setup, for a matrix with the pattern given to
  * ilu0dd_plan_create (n_brows and nnzb are checked, the pattern is not).
  * With d_scratch (device, >= *scratch_bytes of the plan, 256-byte aligned)

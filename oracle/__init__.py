@@ -66,6 +66,8 @@ def _load():
             I, L, D = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
             lib.oracle_partition.argtypes = [ctypes.c_int] * 6 + [i32p]
             lib.oracle_partition.restype = None
+            lib.oracle_partition_bfs.argtypes = [I, i32p, i32p, I, i32p]
+            lib.oracle_partition_bfs.restype = I
             lib.oracle_permutation.argtypes = [I, I, i32p, i32p, i32p, i32p]
             lib.oracle_permutation.restype = None
             lib.oracle_reorder.argtypes = [I, i32p, i32p, vp, i32p, i32p, i32p, i32p, vp]
@@ -126,6 +128,17 @@ def partition(grid, sub) -> np.ndarray:
 
 def nparts(grid, sub) -> int:
     return int(np.prod([-(-g // s) for g, s in zip(grid, sub)]))
+
+
+def partition_bfs(row_ptr, col, part_rows: int):
+    """Graph partition into parts of part_rows rows cut from a breadth-first order
+    (the stand-in for Section 3.1's METIS partition). Returns (part_id, nparts)."""
+    rp = np.ascontiguousarray(row_ptr, np.int32)
+    cl = np.ascontiguousarray(col, np.int32)
+    n = len(rp) - 1
+    part = np.empty(max(n, 1), np.int32)
+    k = int(_load().oracle_partition_bfs(n, rp, cl, part_rows, part))
+    return part[:n], k
 
 
 def permutation(part_id: np.ndarray, nparts_: int):
@@ -245,8 +258,14 @@ class Decomposition:
 
 def decompose(row_ptr, col, val, grid, sub, factor: bool = True) -> Decomposition:
     """Partition (Alg. 2), reorder (Alg. 3), drop (Section 3.2), ILU0 (Alg. 7)."""
-    part = partition(grid, sub)
-    np_ = nparts(grid, sub)
+    return decompose_labeled(row_ptr, col, val, partition(grid, sub), nparts(grid, sub), factor=factor,
+                             grid=grid, sub=sub)
+
+
+def decompose_labeled(row_ptr, col, val, part, np_, factor: bool = True, grid=None, sub=None) -> Decomposition:
+    """Reorder (Alg. 3), drop (Section 3.2) and ILU0 (Alg. 7) for given labels
+    (any partition, e.g. partition_bfs for matrices without a grid)."""
+    part = np.ascontiguousarray(part, np.int32)
     perm, iperm, pp = permutation(part, np_)
     A = BSR(np.ascontiguousarray(row_ptr, np.int32), np.ascontiguousarray(col, np.int32),
             None if val is None else np.ascontiguousarray(val, np.float64).reshape(-1, 3, 3))
@@ -257,4 +276,5 @@ def decompose(row_ptr, col, val, grid, sub, factor: bool = True) -> Decompositio
     if factor and Add.val is not None:
         lu, st = ilu0(Add)
         LU = BSR(Add.row_ptr, Add.col, lu)
-    return Decomposition(tuple(grid), tuple(sub), part, perm, iperm, pp, Ap, Add, LU, st)
+    return Decomposition(tuple(grid) if grid is not None else None, tuple(sub) if sub is not None else None, part,
+                         perm, iperm, pp, Ap, Add, LU, st)

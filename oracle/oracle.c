@@ -50,6 +50,113 @@ void oracle_partition(int nx, int ny, int nz, int sx, int sy, int sz, int32_t* p
 }
 
 /*
+ * Graph partition for matrices without a grid (Section 3.1 partitions those
+ * with METIS into parts of equal size; this is a plain stand-in with the same
+ * output form): parts of part_rows rows (the last one may be smaller) cut from
+ * a breadth-first order of the vertices. The graph is the pattern of A + A^T
+ * without the diagonal; neighbours are visited in ascending index order. The
+ * order is built component by component: u = the smallest vertex not yet
+ * ordered; a first search from u over unordered vertices ends at its last
+ * visited vertex v (a far vertex of the component); a second search from v
+ * appends its visiting order. part_id[order[t]] = t / part_rows. Returns the
+ * number of parts. Pinned in the CPU tests against its definition on small
+ * graphs (paths, grids, disconnected graphs).
+ */
+int32_t oracle_partition_bfs(int32_t n, const int32_t* row_ptr, const int32_t* col, int32_t part_rows,
+                             int32_t* part_id) {
+  if (n <= 0 || part_rows <= 0) return 0;
+  /* adjacency of A + A^T without the diagonal: count, fill, sort, drop duplicates */
+  int64_t* deg = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  for (int32_t i = 0; i < n; ++i)
+    for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+      int32_t j = col[q];
+      if (j == i) continue;
+      deg[i + 1] += 1;
+      deg[j + 1] += 1;
+    }
+  for (int32_t i = 0; i < n; ++i) deg[i + 1] += deg[i];
+  int32_t* adj = (int32_t*)malloc(sizeof(int32_t) * (size_t)(deg[n] > 0 ? deg[n] : 1));
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  for (int32_t i = 0; i < n; ++i) fill[i] = deg[i];
+  for (int32_t i = 0; i < n; ++i)
+    for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+      int32_t j = col[q];
+      if (j == i) continue;
+      adj[fill[i]++] = j;
+      adj[fill[j]++] = i;
+    }
+  int64_t* start = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
+  int64_t* end = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t* a = adj + deg[i];
+    int64_t m = deg[i + 1] - deg[i];
+    for (int64_t x = 1; x < m; ++x) /* insertion sort */
+      for (int64_t y = x; y > 0 && a[y - 1] > a[y]; --y) {
+        int32_t t = a[y];
+        a[y] = a[y - 1];
+        a[y - 1] = t;
+      }
+    int64_t u = 0;
+    for (int64_t x = 0; x < m; ++x)
+      if (x == 0 || a[x] != a[x - 1]) a[u++] = a[x];
+    start[i] = deg[i];
+    end[i] = deg[i] + u;
+  }
+  char* ordered = (char*)calloc((size_t)n, 1);
+  int32_t* stamp = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  for (int32_t i = 0; i < n; ++i) stamp[i] = -1;
+  int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t placed = 0, search = 0;
+  for (int32_t u = 0; u < n; ++u) {
+    if (ordered[u]) continue;
+    /* first search: from u, remember the last vertex visited */
+    int32_t head = 0, tail = 0, v = u;
+    queue[tail++] = u;
+    stamp[u] = search;
+    while (head < tail) {
+      int32_t w = queue[head++];
+      v = w;
+      for (int64_t q = start[w]; q < end[w]; ++q) {
+        int32_t x = adj[q];
+        if (!ordered[x] && stamp[x] != search) {
+          stamp[x] = search;
+          queue[tail++] = x;
+        }
+      }
+    }
+    ++search;
+    /* second search: from v, its visiting order is the component's order */
+    head = 0;
+    tail = 0;
+    queue[tail++] = v;
+    stamp[v] = search;
+    while (head < tail) {
+      int32_t w = queue[head++];
+      ordered[w] = 1;
+      part_id[w] = placed / part_rows;
+      ++placed;
+      for (int64_t q = start[w]; q < end[w]; ++q) {
+        int32_t x = adj[q];
+        if (!ordered[x] && stamp[x] != search) {
+          stamp[x] = search;
+          queue[tail++] = x;
+        }
+      }
+    }
+    ++search;
+  }
+  free(deg);
+  free(adj);
+  free(fill);
+  free(start);
+  free(end);
+  free(ordered);
+  free(stamp);
+  free(queue);
+  return (n + part_rows - 1) / part_rows;
+}
+
+/*
  * Section 3.1: rows grouped by label, in label order; inside a label the
  * original order is kept. perm[new] = old, iperm[old] = new, and
  * part_ptr[p] .. part_ptr[p+1] is the new row range of label p.

@@ -96,6 +96,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "ilu0_dd_setup_planned": ([vp, ctypes.POINTER(Bsr), vp, sz, vp, sz, vp, ctypes.POINTER(vp)],
                                       ctypes.c_int),
             "ilu0dd_plan_destroy": ([vp], ctypes.c_int),
+            "ilu0dd_plan_create_partitioned": ([ctypes.POINTER(Bsr), vp, i32, ctypes.POINTER(Opts),
+                                                ctypes.POINTER(vp), ctypes.POINTER(sz), ctypes.POINTER(sz)],
+                                               ctypes.c_int),
+            "ilu0dd_partition_bfs": ([ctypes.POINTER(Bsr), i32, vp, ctypes.POINTER(i32)], ctypes.c_int),
             "ilu0_dd_apply": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_apply_unfused": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_spmv": ([vp, vp, vp, vp], ctypes.c_int),
@@ -155,6 +159,19 @@ def _bsr(row_ptr, col, val):
     return b, (rp, ci, va)
 
 
+def partition_bfs(row_ptr, col, part_rows: int):
+    """ilu0dd_partition_bfs: (part_id, nparts), parts of part_rows rows cut from a
+    breadth-first order of the pattern (for matrices without a grid)."""
+    b, keep = _bsr(row_ptr, col, None)
+    part = np.empty(max(b.n_brows, 1), np.int32)
+    k = ctypes.c_int32(0)
+    rc = load().ilu0dd_partition_bfs(ctypes.byref(b), part_rows, part.ctypes.data, ctypes.byref(k))
+    del keep
+    if rc:
+        raise Ilu0DDError(rc, "ilu0dd_partition_bfs")
+    return part[:b.n_brows], int(k.value)
+
+
 def workspace_size(row_ptr, col, val, grid, sub, **opts) -> int:
     """Structural query (host only): workspace bytes, or raises Ilu0DDError."""
     b, keep = _bsr(row_ptr, col, val)
@@ -194,19 +211,34 @@ class Ilu0DD:
     the host; both give the same bits.
     """
 
-    def __init__(self, row_ptr, col, val, grid, sub, *, device=None, stream=None, device_setup=True, **opts):
+    def __init__(self, row_ptr, col, val, grid=None, sub=None, *, part_id=None, nparts=None, device=None,
+                 stream=None, device_setup=True, **opts):
         import torch
         lib = load()
         self._lib = lib
-        self.grid, self.sub = tuple(grid), tuple(sub)
+        self.grid = tuple(grid) if grid is not None else None
+        self.sub = tuple(sub) if sub is not None else None
+        if part_id is None and (grid is None or sub is None):
+            raise ValueError("give grid and sub (Algorithm 2) or part_id and nparts (a graph partition)")
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         b, keep = _bsr(row_ptr, col, val)
-        g = Geom(*grid, *sub)
         self.opts = default_opts(**opts)
         plan = ctypes.c_void_p()
         n, ns = ctypes.c_size_t(0), ctypes.c_size_t(0)
-        rc = lib.ilu0dd_plan_create(ctypes.byref(b), ctypes.byref(g), ctypes.byref(self.opts), ctypes.byref(plan),
-                                    ctypes.byref(n), ctypes.byref(ns))
+        if part_id is not None:
+            labels = np.ascontiguousarray(part_id, np.int32)
+            if labels.shape != (b.n_brows,):
+                raise ValueError("part_id must hold one label per block row")
+            if nparts is None:
+                nparts = int(labels.max()) + 1 if labels.size else 0
+            rc = lib.ilu0dd_plan_create_partitioned(ctypes.byref(b), labels.ctypes.data, int(nparts),
+                                                    ctypes.byref(self.opts), ctypes.byref(plan), ctypes.byref(n),
+                                                    ctypes.byref(ns))
+            keep = keep + (labels,)
+        else:
+            g = Geom(*grid, *sub)
+            rc = lib.ilu0dd_plan_create(ctypes.byref(b), ctypes.byref(g), ctypes.byref(self.opts),
+                                        ctypes.byref(plan), ctypes.byref(n), ctypes.byref(ns))
         if rc:
             raise Ilu0DDError(rc, "ilu0dd_plan_create")
         try:

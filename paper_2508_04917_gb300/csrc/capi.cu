@@ -303,6 +303,32 @@ int ilu0dd_plan_create(const ilu0dd_bsr* A, const ilu0dd_geom* geom, const ilu0d
   return ILU0DD_OK;
 }
 
+int ilu0dd_plan_create_partitioned(const ilu0dd_bsr* A, const int32_t* part_id, int32_t nparts,
+                                   const ilu0dd_opts* opts, ilu0dd_plan** out, size_t* workspace_bytes,
+                                   size_t* scratch_bytes) {
+  if (!A || !out || (A->n_brows > 0 && !part_id)) return ILU0DD_ERR_INVALID;
+  *out = nullptr;
+  ilu0dd_plan* pl = new (std::nothrow) ilu0dd_plan();
+  if (!pl) return ILU0DD_ERR_INVALID;
+  pl->t0 = wall_seconds();
+  pl->opts = resolved(opts);
+  int rc = make_plan(A, nullptr, &pl->opts, max_smem_optin(), &pl->plan, &pl->why, part_id, nparts);
+  if (rc) {
+    if (pl->opts.trace) std::fprintf(stderr, "[ilu0dd] plan: %s\n", pl->why.c_str());
+    delete pl;
+    return rc;
+  }
+  pl->scratch_bytes = device_setup_scratch_bytes(pl->plan);
+  if (workspace_bytes) *workspace_bytes = pl->plan.lay.total;
+  if (scratch_bytes) *scratch_bytes = pl->scratch_bytes;
+  *out = pl;
+  return ILU0DD_OK;
+}
+
+int ilu0dd_partition_bfs(const ilu0dd_bsr* A, int32_t part_rows, int32_t* part_id, int32_t* nparts) {
+  return partition_bfs(A, part_rows, part_id, nparts);
+}
+
 int ilu0_dd_setup_planned(ilu0dd_plan* plan, const ilu0dd_bsr* A, void* d_workspace, size_t ws_bytes,
                           void* d_scratch, size_t scratch_bytes, void* stream, ilu0dd_ctx** out) {
   if (!plan || !A || !out || plan->consumed) return ILU0DD_ERR_INVALID;

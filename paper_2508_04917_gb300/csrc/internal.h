@@ -173,8 +173,15 @@ struct Plan {
   int64_t apply_bytes = 0, spmv_bytes = 0;
 };
 
+// The structural setup. Labels come from the geometry g (Algorithm 2) or,
+// when `labels` is non-null, from the caller (a graph partition with nlabels
+// parts; g is then unused and may be null).
 int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, int max_smem,
-              Plan* plan, std::string* why);
+              Plan* plan, std::string* why, const int32_t* labels = nullptr, int32_t nlabels = 0);
+
+// Breadth-first graph partition into parts of part_rows rows (the stand-in for
+// the paper's METIS partition of matrices without a grid): ilu0dd_partition_bfs.
+int partition_bfs(const ilu0dd_bsr* A, int32_t part_rows, int32_t* part_id, int32_t* nparts);
 
 // Numeric setup (host, FP64): block ILU0 of the dropped matrix per subdomain
 // and the ILDU0 post-processing. F is indexed like plan.dd_col: L_ij at

@@ -120,15 +120,19 @@ void put_factor(uint8_t* dst, int prec, double v) {
 }  // namespace
 
 int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, int max_smem,
-              Plan* P, std::string* why) {
-  if (!A || !g || !o || !P) return ILU0DD_ERR_INVALID;
-  if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0 || g->sx <= 0 || g->sy <= 0 || g->sz <= 0) {
+              Plan* P, std::string* why, const int32_t* labels, int32_t nlabels) {
+  if (!A || !o || !P || (!g && !labels)) return ILU0DD_ERR_INVALID;
+  if (!labels && (g->nx <= 0 || g->ny <= 0 || g->nz <= 0 || g->sx <= 0 || g->sy <= 0 || g->sz <= 0)) {
     *why = "grid and subdomain sides must be positive";
     return ILU0DD_ERR_INVALID;
   }
-  int64_t N64 = (int64_t)g->nx * g->ny * g->nz;
-  if (N64 != A->n_brows || N64 >= (1ll << 31)) {
+  int64_t N64 = labels ? (int64_t)A->n_brows : (int64_t)g->nx * g->ny * g->nz;
+  if (N64 != A->n_brows || N64 < 0 || N64 >= (1ll << 31)) {
     *why = "n_brows must equal nx*ny*nz (< 2^31)";
+    return ILU0DD_ERR_INVALID;
+  }
+  if (labels && nlabels <= 0 && N64 > 0) {
+    *why = "nparts must be positive";
     return ILU0DD_ERR_INVALID;
   }
   if (!A->row_ptr || !A->col_idx || (A->nnzb > 0 && !A->val)) {
@@ -192,45 +196,69 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   };
   p.N = N;
   p.nnzb = A->nnzb;
-  p.geom = *g;
+  if (g) p.geom = *g;
   p.opts = *o;
 
   tmark("check");
-  // ---- Algorithm 2: labels from geometric cuts (ceil-division at the edges)
-  const int bx = ceil_div(g->nx, g->sx), by = ceil_div(g->ny, g->sy), bz = ceil_div(g->nz, g->sz);
-  p.nsub = bx * by * bz;
-  p.part_id.resize(N);
-  parallel_for(g->nz, [&](int64_t k) {
-    for (int j = 0; j < g->ny; ++j)
-      for (int i = 0; i < g->nx; ++i)
-        p.part_id[(int64_t)i + (int64_t)g->nx * (j + (int64_t)g->ny * k)] =
-            i / g->sx + bx * (j / g->sy + by * ((int)k / g->sz));
-  });
+  if (labels) {
+    // ---- given labels (a graph partition): Section 3.1's stable grouping
+    std::atomic<int> bad{0};
+    parallel_for(N, [&](int64_t r) {
+      if (labels[r] < 0 || labels[r] >= nlabels) bad = 1;
+    });
+    if (bad) {
+      *why = "part_id out of [0, nparts)";
+      return ILU0DD_ERR_INVALID;
+    }
+    p.nsub = nlabels;
+    p.part_id.assign(labels, labels + N);
+    p.part_ptr.assign(p.nsub + 1, 0);
+    for (int32_t r = 0; r < N; ++r) p.part_ptr[p.part_id[r] + 1]++;
+    for (int s = 0; s < p.nsub; ++s) p.part_ptr[s + 1] += p.part_ptr[s];
+    std::vector<int32_t> next(p.part_ptr.begin(), p.part_ptr.end() - 1);
+    p.perm.resize(N);
+    p.iperm.resize(N);
+    for (int32_t r = 0; r < N; ++r) {
+      const int32_t nr = next[p.part_id[r]]++;
+      p.perm[nr] = r;
+      p.iperm[r] = nr;
+    }
+  } else {
+    // ---- Algorithm 2: labels from geometric cuts (ceil-division at the edges)
+    const int bx = ceil_div(g->nx, g->sx), by = ceil_div(g->ny, g->sy), bz = ceil_div(g->nz, g->sz);
+    p.nsub = bx * by * bz;
+    p.part_id.resize(N);
+    parallel_for(g->nz, [&](int64_t k) {
+      for (int j = 0; j < g->ny; ++j)
+        for (int i = 0; i < g->nx; ++i)
+          p.part_id[(int64_t)i + (int64_t)g->nx * (j + (int64_t)g->ny * k)] =
+              i / g->sx + bx * (j / g->sy + by * ((int)k / g->sz));
+    });
 
-  // ---- Section 3.1: stable grouping by label (perm[new] = old). A label's
-  // cells in natural order are its box's cells in (k, j, i) order, so each
-  // subdomain's slice of perm is filled independently.
-  p.part_ptr.assign(p.nsub + 1, 0);
-  auto box_side = [](int n, int sd, int b) { return std::min(sd, n - b * sd); };
-  for (int s = 0; s < p.nsub; ++s) {
-    const int ib = s % bx, jb = (s / bx) % by, kb = s / (bx * by);
-    p.part_ptr[s + 1] = p.part_ptr[s] + box_side(g->nx, g->sx, ib) * box_side(g->ny, g->sy, jb) *
-                                            box_side(g->nz, g->sz, kb);
+    // ---- Section 3.1: stable grouping by label (perm[new] = old). A label's
+    // cells in natural order are its box's cells in (k, j, i) order, so each
+    // subdomain's slice of perm is filled independently.
+    p.part_ptr.assign(p.nsub + 1, 0);
+    auto box_side = [](int n, int sd, int b) { return std::min(sd, n - b * sd); };
+    for (int s = 0; s < p.nsub; ++s) {
+      const int ib = s % bx, jb = (s / bx) % by, kb = s / (bx * by);
+      p.part_ptr[s + 1] = p.part_ptr[s] + box_side(g->nx, g->sx, ib) * box_side(g->ny, g->sy, jb) *
+                                              box_side(g->nz, g->sz, kb);
+    }
+    p.perm.resize(N);
+    p.iperm.resize(N);
+    parallel_for(p.nsub, [&](int64_t s) {
+      const int ib = (int)(s % bx), jb = (int)((s / bx) % by), kb = (int)(s / ((int64_t)bx * by));
+      int32_t nr = p.part_ptr[s];
+      for (int k = kb * g->sz; k < std::min(g->nz, (kb + 1) * g->sz); ++k)
+        for (int j = jb * g->sy; j < std::min(g->ny, (jb + 1) * g->sy); ++j)
+          for (int i = ib * g->sx; i < std::min(g->nx, (ib + 1) * g->sx); ++i) {
+            const int32_t r = (int32_t)((int64_t)i + (int64_t)g->nx * (j + (int64_t)g->ny * k));
+            p.perm[nr] = r;
+            p.iperm[r] = nr++;
+          }
+    });
   }
-  p.perm.resize(N);
-  p.iperm.resize(N);
-  parallel_for(p.nsub, [&](int64_t s) {
-    const int ib = (int)(s % bx), jb = (int)((s / bx) % by), kb = (int)(s / ((int64_t)bx * by));
-    int32_t nr = p.part_ptr[s];
-    for (int k = kb * g->sz; k < std::min(g->nz, (kb + 1) * g->sz); ++k)
-      for (int j = jb * g->sy; j < std::min(g->ny, (jb + 1) * g->sy); ++j)
-        for (int i = ib * g->sx; i < std::min(g->nx, (ib + 1) * g->sx); ++i) {
-          const int32_t r = (int32_t)((int64_t)i + (int64_t)g->nx * (j + (int64_t)g->ny * k));
-          p.perm[nr] = r;
-          p.iperm[r] = nr++;
-        }
-  });
-
   tmark("label+perm");
   // ---- Algorithm 3 on BSR: reorder rows and columns, sort each row
   p.ap_rp.resize(N + 1);
@@ -542,6 +570,78 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   p.spmv_bytes = 76ll * p.nnzb + 4ll * (N + 1) + 48ll * N;
   tmark("sell+layout");
   if (o->trace) std::fprintf(stderr, "[ilu0dd] plan:%s\n", tlog.c_str());
+  return ILU0DD_OK;
+}
+
+int partition_bfs(const ilu0dd_bsr* A, int32_t part_rows, int32_t* part_id, int32_t* nparts) {
+  if (!A || !part_id || !nparts || part_rows <= 0 || A->n_brows < 0 || !A->row_ptr || !A->col_idx)
+    return ILU0DD_ERR_INVALID;
+  const int32_t N = A->n_brows;
+  const int32_t* rp = A->row_ptr;
+  const int32_t* ci = A->col_idx;
+  for (int32_t i = 0; i < N; ++i)
+    for (int64_t q = rp[i]; q < rp[i + 1]; ++q)
+      if (ci[q] < 0 || ci[q] >= N) return ILU0DD_ERR_INVALID;
+  // neighbours: the pattern of A + A^T without the diagonal, ascending, unique
+  std::vector<int64_t> off((size_t)N + 1, 0);
+  for (int32_t i = 0; i < N; ++i)
+    for (int64_t q = rp[i]; q < rp[i + 1]; ++q)
+      if (ci[q] != i) {
+        off[i + 1]++;
+        off[ci[q] + 1]++;
+      }
+  for (int32_t i = 0; i < N; ++i) off[i + 1] += off[i];
+  RawVec<int32_t> nb((size_t)off[N]);
+  {
+    std::vector<int64_t> at(off.begin(), off.end() - 1);
+    for (int32_t i = 0; i < N; ++i)
+      for (int64_t q = rp[i]; q < rp[i + 1]; ++q)
+        if (ci[q] != i) {
+          nb[at[i]++] = ci[q];
+          nb[at[ci[q]]++] = i;
+        }
+  }
+  std::vector<int64_t> len((size_t)N);
+  parallel_for(N, [&](int64_t i) {
+    int32_t* b = nb.data() + off[i];
+    int32_t* e = nb.data() + off[i + 1];
+    std::sort(b, e);
+    len[i] = std::unique(b, e) - b;
+  });
+  // breadth-first order, component by component; the second search of a
+  // component starts at the last vertex the first one reached
+  std::vector<uint8_t> done((size_t)N, 0);
+  std::vector<int32_t> mark((size_t)N, -1), queue((size_t)N);
+  int32_t placed = 0, pass = 0;
+  auto bfs = [&](int32_t from, bool place) {
+    size_t h = 0, t = 0;
+    queue[t++] = from;
+    mark[from] = pass;
+    int32_t last = from;
+    while (h < t) {
+      const int32_t w = queue[h++];
+      last = w;
+      if (place) {
+        done[w] = 1;
+        part_id[w] = placed++ / part_rows;
+      }
+      for (int64_t q = off[w]; q < off[w] + len[w]; ++q) {
+        const int32_t x = nb[q];
+        if (!done[x] && mark[x] != pass) {
+          mark[x] = pass;
+          queue[t++] = x;
+        }
+      }
+    }
+    ++pass;
+    return last;
+  };
+  for (int32_t u = 0; u < N; ++u) {
+    if (done[u]) continue;
+    const int32_t far = bfs(u, false);
+    bfs(far, true);
+  }
+  *nparts = (N + part_rows - 1) / part_rows;
   return ILU0DD_OK;
 }
 

@@ -63,6 +63,11 @@ def _load():
             lib.synth_system.restype = ctypes.c_int64
             lib.synth_system.argtypes = ([ctypes.c_int] * 4 + [ctypes.c_uint64, i32p, i32p, f64p,
                                                                 f64p, f64p])
+            lib.synth_unstructured_nnzb.restype = ctypes.c_int64
+            lib.synth_unstructured_nnzb.argtypes = [ctypes.c_int] * 3 + [ctypes.c_uint64]
+            lib.synth_unstructured.restype = ctypes.c_int64
+            lib.synth_unstructured.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_uint64, i32p, i32p, f64p, f64p, f64p,
+                                                                    i32p])
             lib.synth_sides.restype = None
             lib.synth_sides.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, i32p]
             _lib = lib
@@ -115,6 +120,23 @@ def system(nx: int, ny: int, nz: int, seed: int, model: int = MODEL_LAPLACE) -> 
     xs = np.empty(3 * n, np.float64)
     b = np.empty(3 * n, np.float64)
     lib.synth_system(model, nx, ny, nz, seed, rp, col, val, xs, b)
+    return System(nx, ny, nz, rp, col, val.reshape(m, 3, 3), xs, b)
+
+
+def unstructured(nx: int, ny: int, nz: int, seed: int) -> System:
+    """The unstructured system (irregular 27-point pattern, cells renumbered at
+    random): a stand-in for graph-partitioned matrices. ``nx, ny, nz`` only size
+    the underlying cell grid; the row order carries no geometry."""
+    lib = _load()
+    n = nx * ny * nz
+    m = lib.synth_unstructured_nnzb(nx, ny, nz, seed)
+    rp = np.empty(n + 1, np.int32)
+    col = np.empty(m, np.int32)
+    val = np.empty(m * 9, np.float64)
+    xs = np.empty(3 * n, np.float64)
+    b = np.empty(3 * n, np.float64)
+    scratch = np.empty(2 * n, np.int32)
+    lib.synth_unstructured(nx, ny, nz, seed, rp, col, val, xs, b, scratch)
     return System(nx, ny, nz, rp, col, val.reshape(m, 3, 3), xs, b)
 
 

@@ -24,15 +24,23 @@
  * x* ~ U(-1,1) per unknown; b = A x* (per scalar row, blocks in ascending
  * column order, entries c = 0..2, fused multiply-add from 0).
  *
+ * A third, unstructured input (synth_unstructured) stands in for the paper's
+ * graph-partitioned matrices: a grid of cells where every face neighbour and,
+ * with probability 0.35 per pair, each edge or corner neighbour of the
+ * 27-point neighbourhood is coupled, renumbered by a seeded random
+ * permutation so that the matrix order carries no geometry.
+ *
  * Build: gcc -O2 -ffp-contract=off -shared -fPIC (no fast-math), so the same
  * source gives the same bits on x86-64 and aarch64 apart from libm's exp,
  * log and cos (used by the layered model only).
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
-enum { STREAM_DIAG = 1, STREAM_OFF = 2, STREAM_XSTAR = 3, STREAM_FIELD = 4, STREAM_SIDES = 5 };
+enum { STREAM_DIAG = 1, STREAM_OFF = 2, STREAM_XSTAR = 3, STREAM_FIELD = 4, STREAM_SIDES = 5, STREAM_PERM = 6,
+       STREAM_EDGE = 7 };
 
 static inline uint64_t sm64_out(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
@@ -165,4 +173,119 @@ int64_t synth_system(int model, int nx, int ny, int nz, uint64_t seed, int32_t* 
 void synth_sides(uint64_t seed, int lo, int hi, int32_t* sides) {
   for (int a = 0; a < 3; ++a)
     sides[a] = lo + (int)(synth_unit(seed, STREAM_SIDES, (uint64_t)a) * (double)(hi - lo + 1));
+}
+
+/* ---- unstructured input ------------------------------------------------ */
+
+/* Offset o in [0, 27) of the 27-point neighbourhood: (di, dj, dk) in {-1,0,1}^3. */
+static inline void off27(int o, int* di, int* dj, int* dk) {
+  *di = o % 3 - 1;
+  *dj = (o / 3) % 3 - 1;
+  *dk = o / 9 - 1;
+}
+
+/* Whether cells g (at i, j, k) and its neighbour at offset o are coupled: face
+ * neighbours always, the others with probability 0.35, drawn once per
+ * unordered pair (from the smaller cell's side) so the pattern is symmetric. */
+static int coupled(uint64_t seed, int nx, int ny, int nz, int i, int j, int k, int o, int64_t* out) {
+  int di, dj, dk;
+  off27(o, &di, &dj, &dk);
+  if (o == 13) return 0;
+  int a = i + di, b = j + dj, c = k + dk;
+  if (a < 0 || a >= nx || b < 0 || b >= ny || c < 0 || c >= nz) return 0;
+  int64_t g = (int64_t)i + (int64_t)nx * (j + (int64_t)ny * k);
+  int64_t h = (int64_t)a + (int64_t)nx * (b + (int64_t)ny * c);
+  *out = h;
+  if (abs(di) + abs(dj) + abs(dk) == 1) return 1;
+  int64_t lo = g < h ? g : h;
+  int olo = g < h ? o : 26 - o; /* the same pair seen from the smaller cell */
+  return synth_unit(seed, STREAM_EDGE, (uint64_t)(27 * lo + olo)) < 0.35;
+}
+
+/* Renumbering: new_of_old[g] from a Fisher-Yates shuffle driven by the counter generator. */
+static void renumber(uint64_t seed, int64_t n, int32_t* new_of_old) {
+  int32_t* old_of_new = new_of_old; /* built in place, then inverted */
+  for (int64_t t = 0; t < n; ++t) old_of_new[t] = (int32_t)t;
+  for (int64_t t = n - 1; t > 0; --t) {
+    int64_t r = (int64_t)(synth_bits(seed, STREAM_PERM, (uint64_t)t) % (uint64_t)(t + 1));
+    int32_t tmp = old_of_new[t];
+    old_of_new[t] = old_of_new[r];
+    old_of_new[r] = tmp;
+  }
+}
+
+/* Blocks of the unstructured system (call before synth_unstructured). */
+int64_t synth_unstructured_nnzb(int nx, int ny, int nz, uint64_t seed) {
+  int64_t m = 0, h;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        m += 1;
+        for (int o = 0; o < 27; ++o) m += coupled(seed, nx, ny, nz, i, j, k, o, &h);
+      }
+  return m;
+}
+
+/*
+ * The unstructured system in its renumbered order: row_ptr[N+1], col[nnzb]
+ * (ascending per row), val[9*nnzb], xstar[3N], b[3N]; `scratch` holds 2N
+ * int32. Off-diagonal blocks -0.05*I + U(-0.02, 0.02) (drawn per directed
+ * coupling), diagonal blocks 6.5*I + U(-0.1, 0.1). Returns nnzb.
+ */
+int64_t synth_unstructured(int nx, int ny, int nz, uint64_t seed, int32_t* row_ptr, int32_t* col, double* val,
+                           double* xstar, double* b, int32_t* scratch) {
+  int64_t n = (int64_t)nx * ny * nz;
+  int32_t* old_of_new = scratch;
+  int32_t* new_of_old = scratch + n;
+  renumber(seed, n, old_of_new);
+  for (int64_t t = 0; t < n; ++t) new_of_old[old_of_new[t]] = (int32_t)t;
+  /* row lengths in the new order */
+  row_ptr[0] = 0;
+  for (int64_t t = 0; t < n; ++t) {
+    int64_t g = old_of_new[t], h;
+    int i = (int)(g % nx), j = (int)((g / nx) % ny), k = (int)(g / ((int64_t)nx * ny));
+    int len = 1;
+    for (int o = 0; o < 27; ++o) len += coupled(seed, nx, ny, nz, i, j, k, o, &h);
+    row_ptr[t + 1] = row_ptr[t] + len;
+  }
+  for (int64_t t = 0; t < n; ++t) {
+    int64_t g = old_of_new[t], h;
+    int i = (int)(g % nx), j = (int)((g / nx) % ny), k = (int)(g / ((int64_t)nx * ny));
+    /* (new column, source) pairs; source -1 = diagonal, else offset o */
+    int32_t cc[28], src[28];
+    int len = 0;
+    cc[len] = (int32_t)t;
+    src[len++] = -1;
+    for (int o = 0; o < 27; ++o)
+      if (coupled(seed, nx, ny, nz, i, j, k, o, &h)) {
+        cc[len] = new_of_old[h];
+        src[len++] = o;
+      }
+    for (int x = 1; x < len; ++x) /* insertion sort by column */
+      for (int y = x; y > 0 && cc[y - 1] > cc[y]; --y) {
+        int32_t tc = cc[y]; cc[y] = cc[y - 1]; cc[y - 1] = tc;
+        int32_t ts = src[y]; src[y] = src[y - 1]; src[y - 1] = ts;
+      }
+    for (int x = 0; x < len; ++x) {
+      int64_t p = row_ptr[t] + x;
+      col[p] = cc[x];
+      double* blk = val + 9 * p;
+      for (int e = 0; e < 9; ++e) {
+        if (src[x] < 0)
+          blk[e] = (e % 4 == 0 ? 6.5 : 0.0) + unif(seed, STREAM_DIAG, (uint64_t)(9 * g + e), -0.1, 0.1);
+        else
+          blk[e] = (e % 4 == 0 ? -0.05 : 0.0) + unif(seed, STREAM_OFF, (uint64_t)((27 * g + src[x]) * 9 + e), -0.02, 0.02);
+      }
+    }
+  }
+  for (int64_t t = 0; t < n; ++t)
+    for (int a = 0; a < 3; ++a) xstar[3 * t + a] = unif(seed, STREAM_XSTAR, (uint64_t)(3 * t + a), -1.0, 1.0);
+  for (int64_t t = 0; t < n; ++t)
+    for (int a = 0; a < 3; ++a) {
+      double acc = 0.0;
+      for (int64_t p = row_ptr[t]; p < row_ptr[t + 1]; ++p)
+        for (int c = 0; c < 3; ++c) acc = fma(val[9 * p + 3 * a + c], xstar[3 * (int64_t)col[p] + c], acc);
+      b[3 * t + a] = acc;
+    }
+  return row_ptr[n];
 }
