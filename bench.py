@@ -19,6 +19,7 @@ timed region. The JSON line also reports the whole-iteration throughput, the
 per-kernel breakdown, BiCGSTAB time to relative residual 1e-8 with FP64, FP32
 and BF16 factors, the FP64-pipe roof of the apply, the 64^3 subdomain-size and
 factor-precision sweeps, the cuSPARSE global-ILU0 context on the same system,
+an unstructured system on the graph-partition path,
 the batched solve of 64 ragged systems, the CPU oracle's throughput and the
 clocks seen.
 
@@ -282,10 +283,11 @@ def run_ours(args):
     del ctx
 
     # ---- context: the cuSPARSE global ILU0 on the same system; the 64^3 sweeps
-    vendor = sweep = None
+    vendor = sweep = unstructured = None
     if not args.no_context and rank == 0:
         vendor = run_vendor(s, w, dev, plain_ms)
         sweep = run_sweep(dev)
+        unstructured = run_unstructured(dev)
 
     # ---- BiCGSTAB time to relative residual 1e-8: FP64 vs FP32 / BF16 factors
     solves = {}
@@ -371,6 +373,7 @@ def run_ours(args):
         "bicgstab": solves,
         "sweep_64cubed": sweep,
         "vendor_context": vendor,
+        "unstructured": unstructured,
         "batched": batched,
         "setup_s": round(setup_s, 3),
         "cpu_baseline": cpu,
@@ -569,6 +572,45 @@ def run_vendor(s, w, dev, ours_apply_ms, reps=20):
             "apply_ms": round(ams, 4), "apply_bytes": apply_bytes, "apply_gbs": round(apply_bytes / ams / 1e6, 1),
             "spmv_ms": round(sms, 4), "ours_apply_ms": round(ours_apply_ms, 5),
             "apply_speedup_ours_vs_vendor": round(ams / ours_apply_ms, 2)}
+
+
+def run_unstructured(dev, cells=(100, 100, 100), part_rows=2048, reps=20):
+    """Matrices without a grid (Section 3.1's graph-partition path): the seeded
+    unstructured system (irregular 27-point block pattern, cells renumbered at
+    random) split by the breadth-first partition into parts of part_rows rows;
+    FP64 and DF64 apply GB/s, dropped blocks, BiCGSTAB iterations and time to
+    1e-8. For contrast, the same system cut into contiguous chunks of its
+    (scrambled) row order."""
+    import torch
+
+    import paper_2508_04917_gb300 as pkg
+    import synth
+    s = synth.unstructured(*cells, 6)
+    t0 = time.perf_counter()
+    part, nparts = pkg.partition_bfs(s.row_ptr, s.col, part_rows)
+    part_s = time.perf_counter() - t0
+    b = torch.from_numpy(s.b).to(dev)
+    r = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, 3 * s.n)).to(dev)
+    z = torch.empty_like(r)
+    out = {"cells": s.n, "blocks": s.nnzb, "part_rows": part_rows, "parts": nparts, "partition_s": round(part_s, 3)}
+    for name, labels in (("bfs", part), ("chunks", (np.arange(s.n) // part_rows).astype(np.int32))):
+        for prec in (("f64", "df64") if name == "bfs" else ("f64",)):
+            t0 = time.perf_counter()
+            ctx = pkg.Ilu0DD(s.row_ptr, s.col, s.val, part_id=labels, nparts=nparts, factor_prec=prec)
+            torch.cuda.synchronize()
+            su = time.perf_counter() - t0
+            ams = time_apply_warm(ctx, r, z, reps)
+            sec, x, info = timed_solve(ctx, b)
+            xs = torch.from_numpy(s.xstar).to(dev)
+            out[f"{name}_{prec}"] = {
+                "setup_s": round(su, 3),
+                "dropped_blocks_pct": round(100.0 * (1 - ctx.query("kept") / ctx.query("nnzb")), 2),
+                "apply_ms": round(ams, 5), "apply_bytes": ctx.query("apply_bytes"),
+                "apply_gbs": round(ctx.query("apply_bytes") / ams / 1e6, 1), "iterations": info["iterations"],
+                "solve_s": round(sec, 5), "status": info["status"],
+                "max_rel_err_vs_xstar": float((x - xs).abs().max() / xs.abs().max())}
+            ctx.close()
+    return out
 
 
 def oracle_apply_baseline(s, grid, sub, apply_bytes, budget_s=15.0):

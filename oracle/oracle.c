@@ -52,15 +52,19 @@ void oracle_partition(int nx, int ny, int nz, int sx, int sy, int sz, int32_t* p
 /*
  * Graph partition for matrices without a grid (Section 3.1 partitions those
  * with METIS into parts of equal size; this is a plain stand-in with the same
- * output form): parts of part_rows rows (the last one may be smaller) cut from
- * a breadth-first order of the vertices. The graph is the pattern of A + A^T
- * without the diagonal; neighbours are visited in ascending index order. The
- * order is built component by component: u = the smallest vertex not yet
- * ordered; a first search from u over unordered vertices ends at its last
- * visited vertex v (a far vertex of the component); a second search from v
- * appends its visiting order. part_id[order[t]] = t / part_rows. Returns the
- * number of parts. Pinned in the CPU tests against its definition on small
- * graphs (paths, grids, disconnected graphs).
+ * output form): parts of part_rows rows (the last may be smaller) grown as
+ * breadth-first balls. The graph is the pattern of A + A^T without the
+ * diagonal; neighbours are visited in ascending index order.
+ *  1. A seed order O: component by component, u = the smallest vertex not yet
+ *     in O; a first search from u ends at its last visited vertex v (a far
+ *     vertex of the component); a second search from v appends its visiting
+ *     order to O.
+ *  2. Parts one after another: the part's next seed is the first vertex of O
+ *     not yet assigned; a search from it over unassigned vertices assigns
+ *     them in visiting order until the part holds part_rows rows; if the
+ *     search runs out first, the next seed of O continues the same part.
+ * Returns the number of parts. Pinned in the CPU tests against this
+ * definition on small graphs (paths, disconnected graphs, grids).
  */
 int32_t oracle_partition_bfs(int32_t n, const int32_t* row_ptr, const int32_t* col, int32_t part_rows,
                              int32_t* part_id) {
@@ -85,7 +89,6 @@ int32_t oracle_partition_bfs(int32_t n, const int32_t* row_ptr, const int32_t* c
       adj[fill[i]++] = j;
       adj[fill[j]++] = i;
     }
-  int64_t* start = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
   int64_t* end = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
   for (int32_t i = 0; i < n; ++i) {
     int32_t* a = adj + deg[i];
@@ -99,45 +102,43 @@ int32_t oracle_partition_bfs(int32_t n, const int32_t* row_ptr, const int32_t* c
     int64_t u = 0;
     for (int64_t x = 0; x < m; ++x)
       if (x == 0 || a[x] != a[x - 1]) a[u++] = a[x];
-    start[i] = deg[i];
     end[i] = deg[i] + u;
   }
-  char* ordered = (char*)calloc((size_t)n, 1);
   int32_t* stamp = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
   for (int32_t i = 0; i < n; ++i) stamp[i] = -1;
   int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  char* in_order = (char*)calloc((size_t)n, 1);
   int32_t placed = 0, search = 0;
+  /* 1. seed order */
   for (int32_t u = 0; u < n; ++u) {
-    if (ordered[u]) continue;
-    /* first search: from u, remember the last vertex visited */
+    if (in_order[u]) continue;
     int32_t head = 0, tail = 0, v = u;
     queue[tail++] = u;
     stamp[u] = search;
     while (head < tail) {
       int32_t w = queue[head++];
       v = w;
-      for (int64_t q = start[w]; q < end[w]; ++q) {
+      for (int64_t q = deg[w]; q < end[w]; ++q) {
         int32_t x = adj[q];
-        if (!ordered[x] && stamp[x] != search) {
+        if (!in_order[x] && stamp[x] != search) {
           stamp[x] = search;
           queue[tail++] = x;
         }
       }
     }
     ++search;
-    /* second search: from v, its visiting order is the component's order */
     head = 0;
     tail = 0;
     queue[tail++] = v;
     stamp[v] = search;
     while (head < tail) {
       int32_t w = queue[head++];
-      ordered[w] = 1;
-      part_id[w] = placed / part_rows;
-      ++placed;
-      for (int64_t q = start[w]; q < end[w]; ++q) {
+      in_order[w] = 1;
+      order[placed++] = w;
+      for (int64_t q = deg[w]; q < end[w]; ++q) {
         int32_t x = adj[q];
-        if (!ordered[x] && stamp[x] != search) {
+        if (!in_order[x] && stamp[x] != search) {
           stamp[x] = search;
           queue[tail++] = x;
         }
@@ -145,14 +146,42 @@ int32_t oracle_partition_bfs(int32_t n, const int32_t* row_ptr, const int32_t* c
     }
     ++search;
   }
+  /* 2. parts grown as breadth-first balls from seeds taken in that order */
+  for (int32_t i = 0; i < n; ++i) part_id[i] = -1;
+  int32_t part = 0, size = 0, next_seed = 0, assigned = 0;
+  while (assigned < n) {
+    while (part_id[order[next_seed]] >= 0) ++next_seed;
+    int32_t seed = order[next_seed];
+    int32_t head = 0, tail = 0;
+    queue[tail++] = seed;
+    stamp[seed] = search;
+    while (head < tail && size < part_rows) {
+      int32_t w = queue[head++];
+      part_id[w] = part;
+      ++size;
+      ++assigned;
+      for (int64_t q = deg[w]; q < end[w]; ++q) {
+        int32_t x = adj[q];
+        if (part_id[x] < 0 && stamp[x] != search) {
+          stamp[x] = search;
+          queue[tail++] = x;
+        }
+      }
+    }
+    ++search;
+    if (size == part_rows) {
+      ++part;
+      size = 0;
+    }
+  }
   free(deg);
   free(adj);
   free(fill);
-  free(start);
   free(end);
-  free(ordered);
   free(stamp);
   free(queue);
+  free(order);
+  free(in_order);
   return (n + part_rows - 1) / part_rows;
 }
 

@@ -608,11 +608,12 @@ int partition_bfs(const ilu0dd_bsr* A, int32_t part_rows, int32_t* part_id, int3
     std::sort(b, e);
     len[i] = std::unique(b, e) - b;
   });
-  // breadth-first order, component by component; the second search of a
-  // component starts at the last vertex the first one reached
+  // 1. seed order: breadth-first, component by component; a component's order
+  //    starts at the last vertex that a first search from its smallest vertex reaches
   std::vector<uint8_t> done((size_t)N, 0);
-  std::vector<int32_t> mark((size_t)N, -1), queue((size_t)N);
-  int32_t placed = 0, pass = 0;
+  std::vector<int32_t> mark((size_t)N, -1), queue((size_t)N), order;
+  order.reserve((size_t)N);
+  int32_t pass = 0;
   auto bfs = [&](int32_t from, bool place) {
     size_t h = 0, t = 0;
     queue[t++] = from;
@@ -623,7 +624,7 @@ int partition_bfs(const ilu0dd_bsr* A, int32_t part_rows, int32_t* part_id, int3
       last = w;
       if (place) {
         done[w] = 1;
-        part_id[w] = placed++ / part_rows;
+        order.push_back(w);
       }
       for (int64_t q = off[w]; q < off[w] + len[w]; ++q) {
         const int32_t x = nb[q];
@@ -640,6 +641,36 @@ int partition_bfs(const ilu0dd_bsr* A, int32_t part_rows, int32_t* part_id, int3
     if (done[u]) continue;
     const int32_t far = bfs(u, false);
     bfs(far, true);
+  }
+  // 2. parts grown one after another as breadth-first balls over unassigned
+  //    vertices, each from the first unassigned vertex of the seed order; a
+  //    ball that runs out continues the part from the next seed
+  for (int32_t i = 0; i < N; ++i) part_id[i] = -1;
+  int32_t part = 0, size = 0, assigned = 0;
+  size_t next = 0;
+  while (assigned < N) {
+    while (part_id[order[next]] >= 0) ++next;
+    size_t h = 0, t = 0;
+    queue[t++] = order[next];
+    mark[order[next]] = pass;
+    while (h < t && size < part_rows) {
+      const int32_t w = queue[h++];
+      part_id[w] = part;
+      ++size;
+      ++assigned;
+      for (int64_t q = off[w]; q < off[w] + len[w]; ++q) {
+        const int32_t x = nb[q];
+        if (part_id[x] < 0 && mark[x] != pass) {
+          mark[x] = pass;
+          queue[t++] = x;
+        }
+      }
+    }
+    ++pass;
+    if (size == part_rows) {
+      ++part;
+      size = 0;
+    }
   }
   *nparts = (N + part_rows - 1) / part_rows;
   return ILU0DD_OK;

@@ -229,8 +229,10 @@ int64_t synth_unstructured_nnzb(int nx, int ny, int nz, uint64_t seed) {
 /*
  * The unstructured system in its renumbered order: row_ptr[N+1], col[nnzb]
  * (ascending per row), val[9*nnzb], xstar[3N], b[3N]; `scratch` holds 2N
- * int32. Off-diagonal blocks -0.05*I + U(-0.02, 0.02) (drawn per directed
- * coupling), diagonal blocks 6.5*I + U(-0.1, 0.1). Returns nnzb.
+ * int32. A coupling of weight w (1 across a face, 0.5 across an edge or a
+ * corner) gives the off-diagonal block -w*(I + P), P ~ U(-0.1, 0.1) per entry
+ * and directed coupling; the diagonal block is (sum of the row's weights +
+ * 0.5)*I + U(-0.1, 0.1) per entry, a Laplacian-like system. Returns nnzb.
  */
 int64_t synth_unstructured(int nx, int ny, int nz, uint64_t seed, int32_t* row_ptr, int32_t* col, double* val,
                            double* xstar, double* b, int32_t* scratch) {
@@ -266,15 +268,26 @@ int64_t synth_unstructured(int nx, int ny, int nz, uint64_t seed, int32_t* row_p
         int32_t tc = cc[y]; cc[y] = cc[y - 1]; cc[y - 1] = tc;
         int32_t ts = src[y]; src[y] = src[y - 1]; src[y - 1] = ts;
       }
+    double wsum = 0.0; /* coupling weights of the row: 1 per face, 0.5 per edge or corner */
+    for (int x = 0; x < len; ++x)
+      if (src[x] >= 0) {
+        int di, dj, dk;
+        off27(src[x], &di, &dj, &dk);
+        wsum += abs(di) + abs(dj) + abs(dk) == 1 ? 1.0 : 0.5;
+      }
     for (int x = 0; x < len; ++x) {
       int64_t p = row_ptr[t] + x;
       col[p] = cc[x];
       double* blk = val + 9 * p;
-      for (int e = 0; e < 9; ++e) {
-        if (src[x] < 0)
-          blk[e] = (e % 4 == 0 ? 6.5 : 0.0) + unif(seed, STREAM_DIAG, (uint64_t)(9 * g + e), -0.1, 0.1);
-        else
-          blk[e] = (e % 4 == 0 ? -0.05 : 0.0) + unif(seed, STREAM_OFF, (uint64_t)((27 * g + src[x]) * 9 + e), -0.02, 0.02);
+      if (src[x] < 0) {
+        for (int e = 0; e < 9; ++e)
+          blk[e] = (e % 4 == 0 ? wsum + 0.5 : 0.0) + unif(seed, STREAM_DIAG, (uint64_t)(9 * g + e), -0.1, 0.1);
+      } else {
+        int di, dj, dk;
+        off27(src[x], &di, &dj, &dk);
+        double w = abs(di) + abs(dj) + abs(dk) == 1 ? 1.0 : 0.5;
+        for (int e = 0; e < 9; ++e)
+          blk[e] = -w * ((e % 4 == 0 ? 1.0 : 0.0) + unif(seed, STREAM_OFF, (uint64_t)((27 * g + src[x]) * 9 + e), -0.1, 0.1));
       }
     }
   }

@@ -1,6 +1,6 @@
 """The graph-partition path for matrices without a grid (Section 3.1's
-graph-based labels; the paper uses METIS, this project a breadth-first
-partition into equal-size parts as the paper's Section 5 asks of its parts).
+graph-based labels; the paper uses METIS, this project breadth-first balls
+grown to equal-size parts, as the paper's Section 5 balances its parts).
 
 CPU tests: the oracle's partition pinned on graphs whose breadth-first order
 is known in closed form, structural invariants on larger ones, and the
@@ -57,21 +57,31 @@ def test_disconnected_components_in_order():
     assert nparts == 4 and np.array_equal(part, expect)
 
 
-def test_grid_parts_follow_distance_from_far_corner():
+def test_grid_first_part_is_a_ball_around_the_far_corner():
     """A 2D grid (5-point pattern): from corner 0 the farthest vertex is the
-    opposite corner alone, so the order is by graph distance from it; labels
-    never decrease with that distance, and every part but the last is full."""
-    nx, ny, k = 7, 5, 6
+    opposite corner alone, which starts the seed order; the first part is the
+    first part_rows vertices of a breadth-first search from it, i.e. every
+    vertex closer than the part's farthest member and nothing farther. Every
+    part but the last is full."""
+    nx, ny, k = 7, 5, 9
     rp, col = synth.pattern(nx, ny, 1)
     part, nparts = oracle.partition_bfs(rp, col, k)
     i, j = np.arange(nx * ny) % nx, np.arange(nx * ny) // nx
     dist = (nx - 1 - i) + (ny - 1 - j)
-    for a in range(nx * ny):
-        for b in range(nx * ny):
-            if dist[a] < dist[b]:
-                assert part[a] <= part[b]
+    first = part == 0
+    dmax = dist[first].max()
+    assert np.all(first[dist < dmax]) and not np.any(first[dist > dmax])
     counts = np.bincount(part, minlength=nparts)
     assert nparts == -(-nx * ny // k) and np.all(counts[:-1] == k) and counts[-1] == nx * ny - k * (nparts - 1)
+
+
+def test_exhausted_ball_continues_from_next_seed():
+    """Path 0..4 plus an isolated vertex 5, parts of 4: seed order 4,3,2,1,0,5;
+    part 0 = {4,3,2,1}; part 1 starts at 0, whose ball ends at once, and
+    continues from seed 5."""
+    rp, col = _union(_path(5), _path(1))
+    part, nparts = oracle.partition_bfs(rp, col, 4)
+    assert nparts == 2 and np.array_equal(part, [1, 0, 0, 0, 0, 1])
 
 
 def test_nonsymmetric_pattern_is_symmetrised():
