@@ -203,6 +203,20 @@ int ilu0dd_plan_destroy(ilu0dd_plan* plan);
 int ilu0_dd_apply(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream);
 
 /*
+ * z = M^-1 r as ilu0_dd_apply, from and to HOST buffers: h_r, h_z hold 3*N
+ * doubles in the reordered numbering (page-locked memory lets the copies
+ * overlap; pageable memory works but serialises them). The subdomains are
+ * split into up to eight contiguous chunks (subdomains are independent:
+ * Section 3.2), each copied in, applied and copied out on its own stream of
+ * the context, so one chunk's copies overlap other chunks' applies. Work is
+ * ordered after earlier work on `stream`, and `stream` waits for all of it;
+ * h_z is valid once `stream` has completed. Uses the context's solver
+ * vectors as device staging: do not overlap with bicgstab_* calls on the same
+ * context. Not const: creates the context's streams on first use.
+ */
+int ilu0_dd_apply_host(ilu0dd_ctx* ctx, const double* h_r, double* h_z, void* stream);
+
+/*
  * The same z = M^-1 r as ilu0_dd_apply, unfused: two launches, the L sweep
  * (r -> z) and then the D^-1 and U~ sweep (z -> z in place), each loading
  * the subdomain vector into shared memory; the separate-kernel variant of

@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "ilu0dd_partition_bfs": ([ctypes.POINTER(Bsr), i32, vp, ctypes.POINTER(i32)], ctypes.c_int),
             "ilu0_dd_apply": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_apply_unfused": ([vp, vp, vp, vp], ctypes.c_int),
+            "ilu0_dd_apply_host": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_spmv": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_dot": ([vp, vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_permute": ([vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
@@ -289,6 +290,30 @@ class Ilu0DD:
         z = self._new() if z is None else z
         self._check(self._lib.ilu0_dd_apply(self._ctx, _dptr(r, self.size, "r"), _dptr(z, self.size, "z"),
                                             _stream(stream)), "ilu0_dd_apply")
+        return z
+
+    def apply_host(self, r, z=None, stream=None, sync=True):
+        """z = M^-1 r with HOST buffers (CPU tensors or numpy arrays, float64, 3N
+        entries, reordered numbering); copies and applies pipelined by chunks of
+        subdomains. Pinned CPU tensors let the copies overlap. Returns z once the
+        stream has completed."""
+        import torch
+        def host_ptr(a, what):
+            if isinstance(a, torch.Tensor):
+                if a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != self.size:
+                    raise TypeError(f"{what} must be a contiguous float64 CPU tensor of {self.size} entries")
+                return a.data_ptr()
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+                    and a.size == self.size):
+                raise TypeError(f"{what} must be a contiguous float64 array of {self.size} entries")
+            return a.ctypes.data
+        if z is None:
+            z = np.empty(self.size, np.float64)
+        st = _stream(stream)
+        self._check(self._lib.ilu0_dd_apply_host(self._ctx, ctypes.c_void_p(host_ptr(r, "r")),
+                                                 ctypes.c_void_p(host_ptr(z, "z")), st), "ilu0_dd_apply_host")
+        if sync:
+            (torch.cuda.current_stream() if stream is None else stream).synchronize()
         return z
 
     def apply_unfused(self, r, z=None, stream=None):

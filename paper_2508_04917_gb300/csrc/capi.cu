@@ -359,6 +359,39 @@ int ilu0_dd_apply(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* s
   return ILU0DD_OK;
 }
 
+int ilu0_dd_apply_host(ilu0dd_ctx* ctx, const double* h_r, double* h_z, void* stream) {
+  if (!ctx || (ctx->plan.N > 0 && (!h_r || !h_z))) return ILU0DD_ERR_INVALID;
+  const Plan& p = ctx->plan;
+  if (p.N == 0) return ILU0DD_OK;
+  constexpr int kChunks = 8;
+  const int nch = std::min(kChunks, p.nsub);
+  if ((int)ctx->hstreams.size() != nch) {
+    for (cudaStream_t x : ctx->hstreams) cudaStreamDestroy(x);
+    for (cudaEvent_t x : ctx->hevents) cudaEventDestroy(x);
+    ctx->hstreams.assign(nch, nullptr);
+    ctx->hevents.assign(nch + 1, nullptr);
+    for (int i = 0; i < nch; ++i) CK(ctx, cudaStreamCreateWithFlags(&ctx->hstreams[i], cudaStreamNonBlocking));
+    for (int i = 0; i <= nch; ++i) CK(ctx, cudaEventCreateWithFlags(&ctx->hevents[i], cudaEventDisableTiming));
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // staging: the solver's s and t vectors (not in use outside bicgstab_* calls)
+  double* dr = ctx->dev.sd.vec[kVecS];
+  double* dz = ctx->dev.sd.vec[kVecT];
+  CK(ctx, cudaEventRecord(ctx->hevents[0], s));  // after the caller's earlier work
+  for (int i = 0; i < nch; ++i) {
+    const int s0 = (int)((int64_t)p.nsub * i / nch), s1 = (int)((int64_t)p.nsub * (i + 1) / nch);
+    const size_t r0 = 3 * (size_t)p.part_ptr[s0], r1 = 3 * (size_t)p.part_ptr[s1];
+    cudaStream_t cs = ctx->hstreams[i];
+    CK(ctx, cudaStreamWaitEvent(cs, ctx->hevents[0], 0));
+    CK(ctx, cudaMemcpyAsync(dr + r0, h_r + r0, sizeof(double) * (r1 - r0), cudaMemcpyHostToDevice, cs));
+    CK(ctx, launch_apply_range(ctx->dev, kModePlain, dr, dz, s0, s1 - s0, cs));
+    CK(ctx, cudaMemcpyAsync(h_z + r0, dz + r0, sizeof(double) * (r1 - r0), cudaMemcpyDeviceToHost, cs));
+    CK(ctx, cudaEventRecord(ctx->hevents[1 + i], cs));
+  }
+  for (int i = 0; i < nch; ++i) CK(ctx, cudaStreamWaitEvent(s, ctx->hevents[1 + i], 0));
+  return ILU0DD_OK;
+}
+
 int ilu0_dd_apply_unfused(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream) {
   if (!ctx || (ctx->plan.N > 0 && (!d_r || !d_z))) return ILU0DD_ERR_INVALID;
   const size_t n = 3 * (size_t)ctx->plan.N * sizeof(double);
@@ -663,6 +696,8 @@ int ilu0_dd_device_error(const ilu0dd_ctx* c, int32_t* code) {
 void ilu0_dd_destroy(ilu0dd_ctx* c) {
   if (!c) return;
   for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+  for (cudaStream_t x : c->hstreams) cudaStreamDestroy(x);
+  for (cudaEvent_t e : c->hevents) cudaEventDestroy(e);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->own) cudaStreamDestroy(c->own);
   delete c;

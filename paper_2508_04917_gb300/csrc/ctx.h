@@ -30,6 +30,9 @@ struct ilu0dd_ctx {
   cudaError_t last_cuda = cudaSuccess;
   std::string why;
   std::vector<cudaEvent_t> events;  // bicgstab_iterate timing
+  // ilu0_dd_apply_host: one stream per chunk of subdomains, and its events
+  std::vector<cudaStream_t> hstreams;
+  std::vector<cudaEvent_t> hevents;  // [0] caller's stream, [1 + i] chunk i done
   // host copies for ilu0_dd_export (opts.keep_host)
   std::vector<double> F, invD;
   bool have_factors = false;

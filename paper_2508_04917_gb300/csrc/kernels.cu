@@ -253,8 +253,8 @@ struct ApplyMinBlocks<df64s> {  // pairs need FP64-sized registers
 
 template <typename TF, int MODE>
 __global__ void __launch_bounds__(kMaxApplyThreads, ApplyMinBlocks<TF>::value)
-    ildu0_apply_kernel(SysDesc S, const double* r, double* z) {
-  apply_block<TF, MODE>(S, blockIdx.x, r, z);
+    ildu0_apply_kernel(SysDesc S, const double* r, double* z, int sub0) {
+  apply_block<TF, MODE>(S, sub0 + blockIdx.x, r, z);
 }
 
 // The unfused apply's two launches (plain mode): PART 1 = L sweep, r -> z;
@@ -317,23 +317,29 @@ cudaError_t apply_configure(const DevCtx& d) {
 }
 
 template <typename TF>
-static cudaError_t launch_apply_t(const DevCtx& d, int mode, const double* r, double* z, cudaStream_t s) {
-  dim3 grid(d.sd.nsub), block(d.threads);
+static cudaError_t launch_apply_t(const DevCtx& d, int mode, const double* r, double* z, int sub0, int nsub,
+                                  cudaStream_t s) {
+  dim3 grid(nsub), block(d.threads);
   if (mode == kModePlain)
-    ildu0_apply_kernel<TF, kModePlain><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z);
+    ildu0_apply_kernel<TF, kModePlain><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
   else if (mode == kModeP)
-    ildu0_apply_kernel<TF, kModeP><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z);
+    ildu0_apply_kernel<TF, kModeP><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
   else
-    ildu0_apply_kernel<TF, kModeS><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z);
+    ildu0_apply_kernel<TF, kModeS><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
   return cudaGetLastError();
 }
 
+cudaError_t launch_apply_range(const DevCtx& d, int mode, const double* r, double* z, int sub0, int nsub,
+                               cudaStream_t s) {
+  if (nsub <= 0) return cudaSuccess;
+  if (d.factor_prec == ILU0DD_F64) return launch_apply_t<double>(d, mode, r, z, sub0, nsub, s);
+  if (d.factor_prec == ILU0DD_F32) return launch_apply_t<float>(d, mode, r, z, sub0, nsub, s);
+  if (d.factor_prec == ILU0DD_DF64) return launch_apply_t<df64s>(d, mode, r, z, sub0, nsub, s);
+  return launch_apply_t<bf16s>(d, mode, r, z, sub0, nsub, s);
+}
+
 cudaError_t launch_apply(const DevCtx& d, int mode, const double* r, double* z, cudaStream_t s) {
-  if (d.sd.nsub == 0) return cudaSuccess;
-  if (d.factor_prec == ILU0DD_F64) return launch_apply_t<double>(d, mode, r, z, s);
-  if (d.factor_prec == ILU0DD_F32) return launch_apply_t<float>(d, mode, r, z, s);
-  if (d.factor_prec == ILU0DD_DF64) return launch_apply_t<df64s>(d, mode, r, z, s);
-  return launch_apply_t<bf16s>(d, mode, r, z, s);
+  return launch_apply_range(d, mode, r, z, 0, d.sd.nsub, s);
 }
 
 template <typename TF>

@@ -53,6 +53,11 @@ cudaError_t apply_configure(const DevCtx& d);
 // z = M^-1 r (mode plain), or the fused BiCGSTAB variants (modes P and S).
 cudaError_t launch_apply(const DevCtx& d, int mode, const double* r, double* z, cudaStream_t s);
 
+// The same for subdomains [sub0, sub0 + nsub) only (r and z are full vectors;
+// other subdomains' entries are neither read nor written).
+cudaError_t launch_apply_range(const DevCtx& d, int mode, const double* r, double* z, int sub0, int nsub,
+                               cudaStream_t s);
+
 // The same z = M^-1 r in two launches (L sweep r -> z, then D^-1 and U~ sweep
 // z -> z in place), the unfused variant of the fusion ablation.
 cudaError_t launch_apply_unfused(const DevCtx& d, const double* r, double* z, cudaStream_t s);
