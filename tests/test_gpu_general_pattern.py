@@ -91,3 +91,22 @@ def test_wide_rows_bicgstab(grid, sub):
         assert nrel(x.cpu().numpy(), xo) <= 1e-12
     finally:
         ctx.close()
+
+
+def test_wide_rows_batched_equals_single():
+    """27-point systems (rows beyond the descriptor's slot counts): the batched
+    solve gives the single-system solve's bits."""
+    systems = [stencil27(8, 8, 8, seed=31), stencil27(9, 7, 5, seed=32)]
+    grids = [((8, 8, 8), (4, 4, 4)), ((9, 7, 5), (9, 7, 5))]
+    ctxs = [g.Ilu0DD(rp, col, val, grid, sub) for (rp, col, val, b, n), (grid, sub) in zip(systems, grids)]
+    bs = [torch.from_numpy(b).cuda() for (rp, col, val, b, n) in systems]
+    try:
+        singles = [c.solve(b) for c, b in zip(ctxs, bs)]
+        batch = g.Batch(ctxs)
+        xs, infos = batch.solve(bs)
+        for (x1, i1), x2, i2 in zip(singles, xs, infos):
+            assert i1["iterations"] == i2["iterations"] and torch.equal(x1, x2)
+        batch.close()
+    finally:
+        for c in ctxs:
+            c.close()
