@@ -572,7 +572,7 @@ def run_vendor(s, w, dev, ours_apply_ms, reps=20):
             "apply_speedup_ours_vs_vendor": round(ams / ours_apply_ms, 2)}
 
 
-def run_unstructured(dev, cells=(100, 100, 100), part_rows=2048, reps=20):
+def run_unstructured(dev, cells=(128, 128, 128), part_rows=2048, reps=20):
     """Matrices without a grid (Section 3.1's graph-partition path): the seeded
     unstructured system (irregular 27-point block pattern, cells renumbered at
     random) split by the breadth-first partition into parts of part_rows rows;
