@@ -70,23 +70,23 @@ def _load():
             lib.oracle_partition_bfs.restype = I
             lib.oracle_permutation.argtypes = [I, I, i32p, i32p, i32p, i32p]
             lib.oracle_permutation.restype = None
-            lib.oracle_reorder.argtypes = [I, i32p, i32p, vp, i32p, i32p, i32p, i32p, vp]
+            lib.oracle_reorder.argtypes = [I, ctypes.c_int, i32p, i32p, vp, i32p, i32p, i32p, i32p, vp]
             lib.oracle_reorder.restype = None
-            lib.oracle_drop.argtypes = [I, i32p, i32p, vp, i32p, vp, vp, vp]
+            lib.oracle_drop.argtypes = [I, ctypes.c_int, i32p, i32p, vp, i32p, vp, vp, vp]
             lib.oracle_drop.restype = L
-            lib.oracle_ilu0.argtypes = [I, i32p, i32p, f64p, f64p]
+            lib.oracle_ilu0.argtypes = [I, ctypes.c_int, i32p, i32p, f64p, f64p]
             lib.oracle_ilu0.restype = ctypes.c_int
             lib.oracle_levels_lower.argtypes = [I, i32p, i32p, i32p]
             lib.oracle_levels_lower.restype = I
             lib.oracle_levels_upper.argtypes = [I, i32p, i32p, i32p]
             lib.oracle_levels_upper.restype = I
-            lib.oracle_apply.argtypes = [I, i32p, i32p, f64p, f64p, f64p]
+            lib.oracle_apply.argtypes = [I, ctypes.c_int, i32p, i32p, f64p, f64p, f64p]
             lib.oracle_apply.restype = ctypes.c_int
-            lib.oracle_spmv.argtypes = [I, i32p, i32p, f64p, f64p, f64p]
+            lib.oracle_spmv.argtypes = [I, ctypes.c_int, i32p, i32p, f64p, f64p, f64p]
             lib.oracle_spmv.restype = None
-            lib.oracle_dot.argtypes = [I, f64p, f64p]
+            lib.oracle_dot.argtypes = [I, ctypes.c_int, f64p, f64p]
             lib.oracle_dot.restype = D
-            lib.oracle_bicgstab.argtypes = [I, i32p, i32p, f64p, i32p, i32p, f64p, f64p, f64p, I, D,
+            lib.oracle_bicgstab.argtypes = [I, ctypes.c_int, i32p, i32p, f64p, i32p, i32p, f64p, f64p, f64p, I, D,
                                             ctypes.POINTER(_Info), vp]
             lib.oracle_bicgstab.restype = ctypes.c_int
             _lib = lib
@@ -103,11 +103,17 @@ def _f64(a):
 
 @dataclass
 class BSR:
-    """Block sparse rows; ``val`` has shape (nnzb, 3, 3) or is None (pattern only)."""
+    """Block sparse rows; ``val`` has shape (nnzb, bs, bs) or is None (pattern
+    only). bs = 3 for the BSR inputs, 1 for scalar CSR."""
 
     row_ptr: np.ndarray
     col: np.ndarray
     val: np.ndarray | None
+    block: int = 3  # bs when val is None
+
+    @property
+    def bs(self) -> int:
+        return int(self.val.shape[1]) if self.val is not None and self.val.ndim == 3 else self.block
 
     @property
     def n(self) -> int:
@@ -153,32 +159,34 @@ def permutation(part_id: np.ndarray, nparts_: int):
 
 def reorder(A: BSR, perm, iperm) -> BSR:
     """Algorithm 3 on BSR."""
-    n = A.n
+    n, bs = A.n, A.bs
     rp = np.empty(n + 1, np.int32)
     col = np.empty(A.nnzb, np.int32)
-    val = None if A.val is None else np.empty((A.nnzb, 3, 3), np.float64)
+    val = None if A.val is None else np.empty((A.nnzb, bs, bs), np.float64)
     src = None if A.val is None else np.ascontiguousarray(A.val, np.float64)
-    _load().oracle_reorder(n, A.row_ptr, A.col, _ptr(src), perm, iperm, rp, col, _ptr(val))
-    return BSR(rp, col, val)
+    _load().oracle_reorder(n, bs, A.row_ptr, A.col, _ptr(src), perm, iperm, rp, col, _ptr(val))
+    return BSR(rp, col, val, bs)
 
 
 def drop(A: BSR, label: np.ndarray) -> BSR:
     """Section 3.2: keep blocks whose row and column carry the same label."""
     lib = _load()
+    bs = A.bs
     label = np.ascontiguousarray(label, np.int32)
-    kept = lib.oracle_drop(A.n, A.row_ptr, A.col, None, label, None, None, None)
+    kept = lib.oracle_drop(A.n, bs, A.row_ptr, A.col, None, label, None, None, None)
     rp = np.empty(A.n + 1, np.int32)
     col = np.empty(kept, np.int32)
-    val = None if A.val is None else np.empty((kept, 3, 3), np.float64)
+    val = None if A.val is None else np.empty((kept, bs, bs), np.float64)
     src = None if A.val is None else np.ascontiguousarray(A.val, np.float64)
-    lib.oracle_drop(A.n, A.row_ptr, A.col, _ptr(src), label, _ptr(rp), _ptr(col), _ptr(val))
-    return BSR(rp, col, val)
+    lib.oracle_drop(A.n, bs, A.row_ptr, A.col, _ptr(src), label, _ptr(rp), _ptr(col), _ptr(val))
+    return BSR(rp, col, val, bs)
 
 
 def ilu0(Add: BSR):
     """Algorithm 7 (block ILU0).  Returns (lu values, status)."""
-    lu = np.empty((Add.nnzb, 3, 3), np.float64)
-    st = _load().oracle_ilu0(Add.n, Add.row_ptr, Add.col, _f64(Add.val), lu.reshape(-1))
+    bs = Add.bs
+    lu = np.empty((Add.nnzb, bs, bs), np.float64)
+    st = _load().oracle_ilu0(Add.n, bs, Add.row_ptr, Add.col, _f64(Add.val), lu.reshape(-1))
     return lu, int(st)
 
 
@@ -196,25 +204,28 @@ def levels_upper(M: BSR):
 
 def apply(LU: BSR, r: np.ndarray) -> np.ndarray:
     """z = U^-1 L^-1 r (sequential substitution, ILU0 form)."""
-    z = np.empty(3 * LU.n, np.float64)
-    st = _load().oracle_apply(LU.n, LU.row_ptr, LU.col, _f64(LU.val), _f64(r), z)
+    bs = LU.bs
+    z = np.empty(bs * LU.n, np.float64)
+    st = _load().oracle_apply(LU.n, bs, LU.row_ptr, LU.col, _f64(LU.val), _f64(r), z)
     if st:
         raise ArithmeticError(f"singular pivot block at row {-st - 1}")
     return z
 
 
 def spmv(A: BSR, x: np.ndarray) -> np.ndarray:
-    y = np.empty(3 * A.n, np.float64)
-    _load().oracle_spmv(A.n, A.row_ptr, A.col, _f64(A.val), _f64(x), y)
+    bs = A.bs
+    y = np.empty(bs * A.n, np.float64)
+    _load().oracle_spmv(A.n, bs, A.row_ptr, A.col, _f64(A.val), _f64(x), y)
     return y
 
 
-def dot(x: np.ndarray, y: np.ndarray) -> float:
-    """Dot product in the project's fixed order (block rows, 256-row tiles, halving sums)."""
+def dot(x: np.ndarray, y: np.ndarray, bs: int = 3) -> float:
+    """Dot product in the project's fixed order (block rows of bs entries,
+    256-row tiles, halving sums)."""
     x = _f64(x)
     y = _f64(y)
-    assert len(x) == len(y) and len(x) % 3 == 0
-    return float(_load().oracle_dot(len(x) // 3, x, y))
+    assert len(x) == len(y) and len(x) % bs == 0
+    return float(_load().oracle_dot(len(x) // bs, bs, x, y))
 
 
 @dataclass
@@ -230,10 +241,11 @@ class SolveResult:
 
 def bicgstab(A: BSR, LU: BSR, b: np.ndarray, maxit: int = 10000, rtol: float = 1e-8) -> SolveResult:
     """Algorithm 1 with M = LU; vectors in the reordered numbering."""
-    x = np.empty(3 * A.n, np.float64)
+    bs = A.bs
+    x = np.empty(bs * A.n, np.float64)
     hist = np.zeros(maxit + 1, np.float64)
     info = _Info()
-    _load().oracle_bicgstab(A.n, A.row_ptr, A.col, _f64(A.val), LU.row_ptr, LU.col, _f64(LU.val),
+    _load().oracle_bicgstab(A.n, bs, A.row_ptr, A.col, _f64(A.val), LU.row_ptr, LU.col, _f64(LU.val),
                             _f64(b), x, maxit, rtol, ctypes.byref(info), _ptr(hist))
     it = info.iterations
     return SolveResult(x, info.status, it, info.restarts, info.rel_res_recurrence,
@@ -262,19 +274,26 @@ def decompose(row_ptr, col, val, grid, sub, factor: bool = True) -> Decompositio
                              grid=grid, sub=sub)
 
 
-def decompose_labeled(row_ptr, col, val, part, np_, factor: bool = True, grid=None, sub=None) -> Decomposition:
+def decompose_labeled(row_ptr, col, val, part, np_, factor: bool = True, grid=None, sub=None,
+                      bs: int | None = None) -> Decomposition:
     """Reorder (Alg. 3), drop (Section 3.2) and ILU0 (Alg. 7) for given labels
-    (any partition, e.g. partition_bfs for matrices without a grid)."""
+    (any partition, e.g. partition_bfs for matrices without a grid). bs is
+    taken from val (bs*bs entries per block) unless given (pattern only)."""
     part = np.ascontiguousarray(part, np.int32)
     perm, iperm, pp = permutation(part, np_)
-    A = BSR(np.ascontiguousarray(row_ptr, np.int32), np.ascontiguousarray(col, np.int32),
-            None if val is None else np.ascontiguousarray(val, np.float64).reshape(-1, 3, 3))
+    rp = np.ascontiguousarray(row_ptr, np.int32)
+    if val is not None and bs is None:
+        nnzb = int(rp[-1])
+        bs = int(round((np.size(val) / max(nnzb, 1)) ** 0.5)) if nnzb else 3
+    bs = 3 if bs is None else bs
+    A = BSR(rp, np.ascontiguousarray(col, np.int32),
+            None if val is None else np.ascontiguousarray(val, np.float64).reshape(-1, bs, bs), bs)
     Ap = reorder(A, perm, iperm)
     label = part[perm]
     Add = drop(Ap, label)
-    LU, st = BSR(Add.row_ptr, Add.col, None), 0
+    LU, st = BSR(Add.row_ptr, Add.col, None, bs), 0
     if factor and Add.val is not None:
         lu, st = ilu0(Add)
-        LU = BSR(Add.row_ptr, Add.col, lu)
+        LU = BSR(Add.row_ptr, Add.col, lu, bs)
     return Decomposition(tuple(grid) if grid is not None else None, tuple(sub) if sub is not None else None, part,
                          perm, iperm, pp, Ap, Add, LU, st)

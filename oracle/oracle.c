@@ -6,7 +6,9 @@
  *
  * Plain FP64 loops, written for reading, not for speed. Every function says
  * which part of the paper it follows. Indices are int32 (rows, columns) and
- * int64 (block positions). Blocks are 3x3 row-major, nine doubles each.
+ * int64 (block positions). Blocks are bs x bs row-major (bs*bs doubles each)
+ * with bs = 3 (the BSR inputs: 3 unknowns per cell) or bs = 1 (scalar CSR,
+ * the paper's other input format).
  *
  * Readings of passages the paper leaves open (the same list is kept with the
  * design notes of the project):
@@ -210,9 +212,10 @@ void oracle_permutation(int32_t n, int32_t nparts, const int32_t* part_id, int32
  * their columns renamed by iperm and are then sorted by new column.
  * val may be NULL (pattern only).
  */
-void oracle_reorder(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* val,
+void oracle_reorder(int32_t n, int bs, const int32_t* row_ptr, const int32_t* col, const double* val,
                     const int32_t* perm, const int32_t* iperm, int32_t* out_row_ptr,
                     int32_t* out_col, double* out_val) {
+  const int bb = bs * bs;
   out_row_ptr[0] = 0;
   for (int32_t i = 0; i < n; ++i) {
     int32_t k = perm[i];
@@ -224,22 +227,22 @@ void oracle_reorder(int32_t n, const int32_t* row_ptr, const int32_t* col, const
     int64_t dst = out_row_ptr[i];
     for (int64_t q = row_ptr[m]; q < row_ptr[m + 1]; ++q, ++dst) {
       out_col[dst] = iperm[col[q]];
-      if (val) memcpy(out_val + 9 * dst, val + 9 * q, 9 * sizeof(double));
+      if (val) memcpy(out_val + bb * dst, val + bb * q, bb * sizeof(double));
     }
     /* sort the row by new column (insertion sort; rows are short) */
     int64_t lo = out_row_ptr[i], hi = out_row_ptr[i + 1];
     for (int64_t a = lo + 1; a < hi; ++a) {
       int32_t c = out_col[a];
       double blk[9];
-      if (val) memcpy(blk, out_val + 9 * a, sizeof blk);
+      if (val) memcpy(blk, out_val + bb * a, bb * sizeof(double));
       int64_t b = a - 1;
       while (b >= lo && out_col[b] > c) {
         out_col[b + 1] = out_col[b];
-        if (val) memcpy(out_val + 9 * (b + 1), out_val + 9 * b, sizeof blk);
+        if (val) memcpy(out_val + bb * (b + 1), out_val + bb * b, bb * sizeof(double));
         --b;
       }
       out_col[b + 1] = c;
-      if (val) memcpy(out_val + 9 * (b + 1), blk, sizeof blk);
+      if (val) memcpy(out_val + bb * (b + 1), blk, bb * sizeof(double));
     }
   }
 }
@@ -249,8 +252,9 @@ void oracle_reorder(int32_t n, const int32_t* row_ptr, const int32_t* col, const
  * subdomain. label[i] is the subdomain of (new) row i. With out_col == NULL
  * only the number of kept blocks is returned.
  */
-int64_t oracle_drop(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* val,
+int64_t oracle_drop(int32_t n, int bs, const int32_t* row_ptr, const int32_t* col, const double* val,
                     const int32_t* label, int32_t* out_row_ptr, int32_t* out_col, double* out_val) {
+  const int bb = bs * bs;
   int64_t kept = 0;
   if (out_row_ptr) out_row_ptr[0] = 0;
   for (int32_t i = 0; i < n; ++i) {
@@ -258,7 +262,7 @@ int64_t oracle_drop(int32_t n, const int32_t* row_ptr, const int32_t* col, const
       if (label[col[q]] != label[i]) continue;
       if (out_col) {
         out_col[kept] = col[q];
-        if (val && out_val) memcpy(out_val + 9 * kept, val + 9 * q, 9 * sizeof(double));
+        if (val && out_val) memcpy(out_val + bb * kept, val + bb * q, bb * sizeof(double));
       }
       ++kept;
     }
@@ -268,50 +272,50 @@ int64_t oracle_drop(int32_t n, const int32_t* row_ptr, const int32_t* col, const
 }
 
 /* ------------------------------------------------------------------------ */
-/* 3x3 dense helpers                                                         */
+/* bs x bs dense helpers (bs <= 3)                                            */
 /* ------------------------------------------------------------------------ */
 
 /*
- * Solve M y = f for a 3x3 row-major M by Gaussian elimination with partial
- * pivoting. Returns 0, or -1 for a zero or non-finite pivot.
+ * Solve M y = f for a bs x bs row-major M by Gaussian elimination with
+ * partial pivoting. Returns 0, or -1 for a zero or non-finite pivot.
  */
-static int solve3(const double* M, const double* f, double* y) {
+static int solve_bs(int bs, const double* M, const double* f, double* y) {
   double a[3][4];
-  for (int r = 0; r < 3; ++r) {
-    for (int c = 0; c < 3; ++c) a[r][c] = M[3 * r + c];
-    a[r][3] = f[r];
+  for (int r = 0; r < bs; ++r) {
+    for (int c = 0; c < bs; ++c) a[r][c] = M[bs * r + c];
+    a[r][bs] = f[r];
   }
-  for (int c = 0; c < 3; ++c) {
+  for (int c = 0; c < bs; ++c) {
     int piv = c;
-    for (int r = c + 1; r < 3; ++r)
+    for (int r = c + 1; r < bs; ++r)
       if (fabs(a[r][c]) > fabs(a[piv][c])) piv = r;
     if (!(fabs(a[piv][c]) > 0.0) || !isfinite(a[piv][c])) return -1;
     if (piv != c)
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q <= bs; ++q) {
         double t = a[c][q];
         a[c][q] = a[piv][q];
         a[piv][q] = t;
       }
-    for (int r = c + 1; r < 3; ++r) {
+    for (int r = c + 1; r < bs; ++r) {
       double m = a[r][c] / a[c][c];
-      for (int q = c; q < 4; ++q) a[r][q] = a[r][q] - m * a[c][q];
+      for (int q = c; q <= bs; ++q) a[r][q] = a[r][q] - m * a[c][q];
     }
   }
-  for (int r = 2; r >= 0; --r) {
-    double s = a[r][3];
-    for (int q = r + 1; q < 3; ++q) s = s - a[r][q] * y[q];
+  for (int r = bs - 1; r >= 0; --r) {
+    double s = a[r][bs];
+    for (int q = r + 1; q < bs; ++q) s = s - a[r][q] * y[q];
     y[r] = s / a[r][r];
   }
   return 0;
 }
 
 /* X = W * U^-1, i.e. solve X U = W row by row: U^T x_r = w_r. */
-static int right_divide3(const double* W, const double* U, double* X) {
+static int right_divide_bs(int bs, const double* W, const double* U, double* X) {
   double Ut[9];
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) Ut[3 * r + c] = U[3 * c + r];
-  for (int r = 0; r < 3; ++r)
-    if (solve3(Ut, W + 3 * r, X + 3 * r)) return -1;
+  for (int r = 0; r < bs; ++r)
+    for (int c = 0; c < bs; ++c) Ut[bs * r + c] = U[bs * c + r];
+  for (int r = 0; r < bs; ++r)
+    if (solve_bs(bs, Ut, W + bs * r, X + bs * r)) return -1;
   return 0;
 }
 
@@ -325,9 +329,10 @@ static int right_divide3(const double* W, const double* U, double* X) {
  * (diagonal and upper blocks) in the pattern of the input. Returns 0, or
  * -(row+1) for a singular pivot block.
  */
-int oracle_ilu0(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* val, double* lu) {
+int oracle_ilu0(int32_t n, int bs, const int32_t* row_ptr, const int32_t* col, const double* val, double* lu) {
+  const int bb = bs * bs;
   int64_t nnzb = row_ptr[n];
-  memcpy(lu, val, (size_t)nnzb * 9 * sizeof(double));
+  memcpy(lu, val, (size_t)nnzb * bb * sizeof(double));
   int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
   int64_t* diag = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
   for (int32_t c = 0; c < n; ++c) pos[c] = -1;
@@ -342,27 +347,28 @@ int oracle_ilu0(int32_t n, const int32_t* row_ptr, const int32_t* col, const dou
     for (int64_t q = row_ptr[i]; q < row_ptr[i + 1] && col[q] < i; ++q) {
       int32_t j = col[q];
       double Lij[9];
-      if (right_divide3(lu + 9 * q, lu + 9 * diag[j], Lij)) { status = -(j + 1); break; }
-      memcpy(lu + 9 * q, Lij, sizeof Lij);
+      if (right_divide_bs(bs, lu + bb * q, lu + bb * diag[j], Lij)) { status = -(j + 1); break; }
+      memcpy(lu + bb * q, Lij, bb * sizeof(double));
       /* W_ik -= L_ij U_jk for every k > j present in both rows i and j */
       for (int64_t t = row_ptr[j]; t < row_ptr[j + 1]; ++t) {
         int32_t k = col[t];
         if (k <= j || pos[k] < 0) continue;
-        double* W = lu + 9 * pos[k];
-        const double* Ujk = lu + 9 * t;
-        for (int a = 0; a < 3; ++a)
-          for (int c = 0; c < 3; ++c) {
+        double* W = lu + bb * pos[k];
+        const double* Ujk = lu + bb * t;
+        for (int a = 0; a < bs; ++a)
+          for (int c = 0; c < bs; ++c) {
             double s = 0.0;
-            for (int b = 0; b < 3; ++b) s = s + Lij[3 * a + b] * Ujk[3 * b + c];
-            W[3 * a + c] = W[3 * a + c] - s;
+            for (int b = 0; b < bs; ++b) s = s + Lij[bs * a + b] * Ujk[bs * b + c];
+            W[bs * a + c] = W[bs * a + c] - s;
           }
       }
     }
     for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) pos[col[q]] = -1;
     if (status == 0) {
       /* the pivot block of row i must be invertible for later rows */
-      double probe[9], eye[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
-      if (right_divide3(eye, lu + 9 * diag[i], probe)) status = -(i + 1);
+      double probe[9], eye[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      for (int a = 0; a < bs; ++a) eye[bs * a + a] = 1.0;
+      if (right_divide_bs(bs, eye, lu + bb * diag[i], probe)) status = -(i + 1);
     }
   }
   free(pos);
@@ -407,48 +413,50 @@ int32_t oracle_levels_upper(int32_t n, const int32_t* row_ptr, const int32_t* co
 /*
  * z = U^-1 L^-1 r by plain sequential substitution over all rows (Section
  * 4.2.2 computes the same result level by level). L has a unit block
- * diagonal; each U diagonal block is applied through a 3x3 solve. Within a
- * row, blocks are taken in ascending column order and, per output entry,
- * block entries c = 0..2 with a fused multiply-add.
+ * diagonal; each U diagonal block is applied through a bs x bs solve. Within
+ * a row, blocks are taken in ascending column order and, per output entry,
+ * block entries c = 0..bs-1 with a fused multiply-add.
  */
-int oracle_apply(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* lu,
+int oracle_apply(int32_t n, int bs, const int32_t* row_ptr, const int32_t* col, const double* lu,
                  const double* r, double* z) {
-  double* y = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+  const int bb = bs * bs;
+  double* y = (double*)malloc(sizeof(double) * bs * (size_t)(n > 0 ? n : 1));
   for (int32_t i = 0; i < n; ++i)
-    for (int a = 0; a < 3; ++a) {
-      double acc = r[3 * (int64_t)i + a];
+    for (int a = 0; a < bs; ++a) {
+      double acc = r[bs * (int64_t)i + a];
       for (int64_t q = row_ptr[i]; q < row_ptr[i + 1] && col[q] < i; ++q)
-        for (int c = 0; c < 3; ++c) acc = fma(-lu[9 * q + 3 * a + c], y[3 * (int64_t)col[q] + c], acc);
-      y[3 * (int64_t)i + a] = acc;
+        for (int c = 0; c < bs; ++c) acc = fma(-lu[bb * q + bs * a + c], y[bs * (int64_t)col[q] + c], acc);
+      y[bs * (int64_t)i + a] = acc;
     }
   int status = 0;
   for (int32_t i = n - 1; i >= 0; --i) {
     double w[3];
     int64_t d = -1;
-    for (int a = 0; a < 3; ++a) {
-      double acc = y[3 * (int64_t)i + a];
+    for (int a = 0; a < bs; ++a) {
+      double acc = y[bs * (int64_t)i + a];
       for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
         if (col[q] == i) d = q;
         if (col[q] <= i) continue;
-        for (int c = 0; c < 3; ++c) acc = fma(-lu[9 * q + 3 * a + c], z[3 * (int64_t)col[q] + c], acc);
+        for (int c = 0; c < bs; ++c) acc = fma(-lu[bb * q + bs * a + c], z[bs * (int64_t)col[q] + c], acc);
       }
       w[a] = acc;
     }
-    if (d < 0 || solve3(lu + 9 * d, w, z + 3 * (int64_t)i)) status = -(i + 1);
+    if (d < 0 || solve_bs(bs, lu + bb * d, w, z + bs * (int64_t)i)) status = -(i + 1);
   }
   free(y);
   return status;
 }
 
-/* y = A x: per scalar row, blocks in ascending column order, c = 0..2, FMA from 0. */
-void oracle_spmv(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* val,
+/* y = A x: per scalar row, blocks in ascending column order, c = 0..bs-1, FMA from 0. */
+void oracle_spmv(int32_t n, int bs, const int32_t* row_ptr, const int32_t* col, const double* val,
                  const double* x, double* y) {
+  const int bb = bs * bs;
   for (int32_t i = 0; i < n; ++i)
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < bs; ++a) {
       double acc = 0.0;
       for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q)
-        for (int c = 0; c < 3; ++c) acc = fma(val[9 * q + 3 * a + c], x[3 * (int64_t)col[q] + c], acc);
-      y[3 * (int64_t)i + a] = acc;
+        for (int c = 0; c < bs; ++c) acc = fma(val[bb * q + bs * a + c], x[bs * (int64_t)col[q] + c], acc);
+      y[bs * (int64_t)i + a] = acc;
     }
 }
 
@@ -463,12 +471,13 @@ static double halving_sum(double* s, int64_t m) {
 }
 
 /*
- * x . y over n block rows (3n scalars) in one fixed order:
- *  1. per block row: q_i = fma(x2, y2, fma(x1, y1, x0 * y0));
+ * x . y over n block rows (bs*n scalars) in one fixed order:
+ *  1. per block row: q_i = x0 * y0, then q_i = fma(xc, yc, q_i) for c = 1..bs-1
+ *     (for bs = 3: fma(x2, y2, fma(x1, y1, x0 * y0)));
  *  2. per tile of 256 block rows (missing rows count as 0): halving sum;
  *  3. over the tile sums, padded with zeros to a power of two: halving sum.
  */
-double oracle_dot(int32_t n, const double* x, const double* y) {
+double oracle_dot(int32_t n, int bs, const double* x, const double* y) {
   int64_t ntiles = (n + DOT_TILE - 1) / DOT_TILE;
   if (ntiles == 0) return 0.0;
   int64_t m = 1;
@@ -479,7 +488,10 @@ double oracle_dot(int32_t n, const double* x, const double* y) {
     for (int r = 0; r < DOT_TILE; ++r) {
       int64_t i = t * DOT_TILE + r;
       q[r] = 0.0;
-      if (i < n) q[r] = fma(x[3 * i + 2], y[3 * i + 2], fma(x[3 * i + 1], y[3 * i + 1], x[3 * i] * y[3 * i]));
+      if (i < n) {
+        q[r] = x[bs * i] * y[bs * i];
+        for (int c = 1; c < bs; ++c) q[r] = fma(x[bs * i + c], y[bs * i + c], q[r]);
+      }
     }
     tile[t] = halving_sum(q, DOT_TILE);
   }
@@ -512,16 +524,16 @@ static double rel_of(double rr, double bb) { return sqrt(rr) / sqrt(bb); }
  * vectors are in the reordered numbering. hist (optional, maxit + 1 entries)
  * receives ||r_j|| / ||b|| with hist[0] = 1.
  */
-int oracle_bicgstab(int32_t n, const int32_t* arp, const int32_t* acol, const double* aval,
+int oracle_bicgstab(int32_t n, int bs, const int32_t* arp, const int32_t* acol, const double* aval,
                     const int32_t* lrp, const int32_t* lcol, const double* lu, const double* b,
                     double* x, int32_t maxit, double rtol, oracle_info* info, double* hist) {
-  size_t m = 3 * (size_t)(n > 0 ? n : 1);
+  size_t m = bs * (size_t)(n > 0 ? n : 1);
   double *r = calloc(m, 8), *rh = calloc(m, 8), *p = calloc(m, 8), *v = calloc(m, 8);
   double *s = calloc(m, 8), *t = calloc(m, 8), *ph = calloc(m, 8), *sh = calloc(m, 8);
-  int64_t len = 3 * (int64_t)n;
+  int64_t len = bs * (int64_t)n;
   memset(info, 0, sizeof *info);
   for (int64_t e = 0; e < len; ++e) x[e] = 0.0;
-  double bb = oracle_dot(n, b, b);
+  double bb = oracle_dot(n, bs, b, b);
   int status = ORC_NOT_CONVERGED;
   if (!(bb > 0.0)) {
     status = ORC_OK; /* b = 0: x = 0 is exact */
@@ -532,31 +544,31 @@ int oracle_bicgstab(int32_t n, const int32_t* arp, const int32_t* acol, const do
   int j = 0;
   for (int restart = 0; restart < 2; ++restart) {
     for (int64_t e = 0; e < len; ++e) rh[e] = r[e], p[e] = r[e];
-    double rho = oracle_dot(n, rh, r);
+    double rho = oracle_dot(n, bs, rh, r);
     int converged = 0;
     for (; j < maxit; ++j) {
-      if (oracle_apply(n, lrp, lcol, lu, p, ph)) { status = ORC_ZERO_PIVOT; goto done; }
-      oracle_spmv(n, arp, acol, aval, ph, v);
-      double rv = oracle_dot(n, rh, v);
+      if (oracle_apply(n, bs, lrp, lcol, lu, p, ph)) { status = ORC_ZERO_PIVOT; goto done; }
+      oracle_spmv(n, bs, arp, acol, aval, ph, v);
+      double rv = oracle_dot(n, bs, rh, v);
       if (rv == 0.0 || !isfinite(rv)) { status = ORC_BREAKDOWN; goto done; }
       double alpha = rho / rv;
       for (int64_t e = 0; e < len; ++e) s[e] = fma(-alpha, v[e], r[e]);
-      if (oracle_apply(n, lrp, lcol, lu, s, sh)) { status = ORC_ZERO_PIVOT; goto done; }
-      oracle_spmv(n, arp, acol, aval, sh, t);
-      double ts = oracle_dot(n, t, s);
-      double tt = oracle_dot(n, t, t);
+      if (oracle_apply(n, bs, lrp, lcol, lu, s, sh)) { status = ORC_ZERO_PIVOT; goto done; }
+      oracle_spmv(n, bs, arp, acol, aval, sh, t);
+      double ts = oracle_dot(n, bs, t, s);
+      double tt = oracle_dot(n, bs, t, t);
       double omega = tt == 0.0 ? 0.0 : ts / tt;
       for (int64_t e = 0; e < len; ++e) {
         x[e] = fma(omega, sh[e], fma(alpha, ph[e], x[e]));
         r[e] = fma(-omega, t[e], s[e]);
       }
-      double rr = oracle_dot(n, r, r);
+      double rr = oracle_dot(n, bs, r, r);
       double rel = rel_of(rr, bb);
       info->rel_res_recurrence = rel;
       if (hist) hist[j + 1] = rel;
       if (!isfinite(rel)) { status = ORC_BREAKDOWN; goto done; }
       if (rel < rtol) { ++j; converged = 1; break; }
-      double rho_new = oracle_dot(n, rh, r);
+      double rho_new = oracle_dot(n, bs, rh, r);
       if (rho_new == 0.0 || omega == 0.0 || !isfinite(rho_new)) { status = ORC_BREAKDOWN; goto done; }
       double beta = (alpha / omega) * (rho_new / rho);
       for (int64_t e = 0; e < len; ++e) p[e] = fma(beta, fma(-omega, v[e], p[e]), r[e]);
@@ -565,9 +577,9 @@ int oracle_bicgstab(int32_t n, const int32_t* arp, const int32_t* acol, const do
     info->iterations = j;
     if (!converged) { status = ORC_NOT_CONVERGED; goto done; }
     /* true residual r = b - A x */
-    oracle_spmv(n, arp, acol, aval, x, t);
+    oracle_spmv(n, bs, arp, acol, aval, x, t);
     for (int64_t e = 0; e < len; ++e) r[e] = b[e] - t[e];
-    double rel_true = rel_of(oracle_dot(n, r, r), bb);
+    double rel_true = rel_of(oracle_dot(n, bs, r, r), bb);
     info->rel_res_true = rel_true;
     if (rel_true < rtol) { status = ORC_OK; goto done; }
     if (restart == 0) info->restarts = 1;

@@ -63,6 +63,8 @@ def _load():
             lib.synth_system.restype = ctypes.c_int64
             lib.synth_system.argtypes = ([ctypes.c_int] * 4 + [ctypes.c_uint64, i32p, i32p, f64p,
                                                                 f64p, f64p])
+            lib.synth_system_bs.restype = ctypes.c_int64
+            lib.synth_system_bs.argtypes = ([ctypes.c_int] * 5 + [ctypes.c_uint64, i32p, i32p, f64p, f64p, f64p])
             lib.synth_unstructured_nnzb.restype = ctypes.c_int64
             lib.synth_unstructured_nnzb.argtypes = [ctypes.c_int] * 3 + [ctypes.c_uint64]
             lib.synth_unstructured.restype = ctypes.c_int64
@@ -110,17 +112,19 @@ def pattern(nx: int, ny: int, nz: int):
     return rp, col
 
 
-def system(nx: int, ny: int, nz: int, seed: int, model: int = MODEL_LAPLACE) -> System:
+def system(nx: int, ny: int, nz: int, seed: int, model: int = MODEL_LAPLACE, bs: int = 3) -> System:
+    """The 7-point system with bs x bs blocks: bs = 3 (3 unknowns per cell) or
+    bs = 1 (the scalar CSR form, each value the 3x3 model's (0,0) entry)."""
     lib = _load()
     n = nx * ny * nz
     m = lib.synth_nnzb(nx, ny, nz)
     rp = np.empty(n + 1, np.int32)
     col = np.empty(m, np.int32)
-    val = np.empty(m * 9, np.float64)
-    xs = np.empty(3 * n, np.float64)
-    b = np.empty(3 * n, np.float64)
-    lib.synth_system(model, nx, ny, nz, seed, rp, col, val, xs, b)
-    return System(nx, ny, nz, rp, col, val.reshape(m, 3, 3), xs, b)
+    val = np.empty(m * bs * bs, np.float64)
+    xs = np.empty(bs * n, np.float64)
+    b = np.empty(bs * n, np.float64)
+    lib.synth_system_bs(model, bs, nx, ny, nz, seed, rp, col, val, xs, b)
+    return System(nx, ny, nz, rp, col, val.reshape(m, bs, bs), xs, b)
 
 
 def unstructured(nx: int, ny: int, nz: int, seed: int) -> System:

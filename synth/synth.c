@@ -112,15 +112,18 @@ static double layered_kappa(uint64_t seed, int nx, int ny, int i, int j, int k) 
 }
 
 /*
- * Full system. model 0 = laplace, 1 = layered. Writes row_ptr[N+1],
- * col[nnzb], val[nnzb*9], xstar[3N], b[3N]. Returns the number of blocks.
+ * Full system with bs x bs blocks (bs = 3: the BSR inputs; bs = 1: the scalar
+ * CSR form of the same stencil, whose value is the 3x3 model's (0,0) entry).
+ * model 0 = laplace, 1 = layered. Writes row_ptr[N+1], col[nnzb],
+ * val[nnzb*bs*bs], xstar[bs*N], b[bs*N]. Returns the number of blocks.
  */
-int64_t synth_system(int model, int nx, int ny, int nz, uint64_t seed, int32_t* row_ptr,
-                     int32_t* col, double* val, double* xstar, double* b) {
+int64_t synth_system_bs(int model, int bs, int nx, int ny, int nz, uint64_t seed, int32_t* row_ptr,
+                        int32_t* col, double* val, double* xstar, double* b) {
+  const int bb = bs * bs;
   int64_t n = (int64_t)nx * ny * nz;
   synth_pattern(nx, ny, nz, row_ptr, col);
   for (int64_t g = 0; g < n; ++g)
-    for (int a = 0; a < 3; ++a) xstar[3 * g + a] = unif(seed, STREAM_XSTAR, (uint64_t)(3 * g + a), -1.0, 1.0);
+    for (int a = 0; a < bs; ++a) xstar[bs * g + a] = unif(seed, STREAM_XSTAR, (uint64_t)(bs * g + a), -1.0, 1.0);
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
@@ -129,10 +132,10 @@ int64_t synth_system(int model, int nx, int ny, int nz, uint64_t seed, int32_t* 
         double diag[9];
         double ka = model ? layered_kappa(seed, nx, ny, i, j, k) : 0.0;
         if (model == 0) {
-          for (int e = 0; e < 9; ++e)
-            diag[e] = (e % 4 == 0 ? 6.5 : 0.0) + unif(seed, STREAM_DIAG, (uint64_t)(9 * g + e), -0.1, 0.1);
+          for (int e = 0; e < bb; ++e)
+            diag[e] = (e % (bs + 1) == 0 ? 6.5 : 0.0) + unif(seed, STREAM_DIAG, (uint64_t)(9 * g + e), -0.1, 0.1);
         } else {
-          for (int e = 0; e < 9; ++e) diag[e] = (e % 4 == 0 ? 0.01 : 0.0);
+          for (int e = 0; e < bb; ++e) diag[e] = (e % (bs + 1) == 0 ? 0.01 : 0.0);
         }
         int64_t pdiag = -1;
         for (int o = 0; o < 7; ++o) {
@@ -140,33 +143,38 @@ int64_t synth_system(int model, int nx, int ny, int nz, uint64_t seed, int32_t* 
           if (d < 0) { pdiag = p++; continue; }
           int64_t c = nbr(nx, ny, nz, i, j, k, d);
           if (c < 0) continue;
-          double* blk = val + 9 * p;
+          double* blk = val + bb * p;
           uint64_t base = (uint64_t)(6 * g + d) * 9;
           if (model == 0) {
-            for (int e = 0; e < 9; ++e)
-              blk[e] = (e % 4 == 0 ? -1.0 : 0.0) + unif(seed, STREAM_OFF, base + e, -0.1, 0.1);
+            for (int e = 0; e < bb; ++e)
+              blk[e] = (e % (bs + 1) == 0 ? -1.0 : 0.0) + unif(seed, STREAM_OFF, base + e, -0.1, 0.1);
           } else {
             int ci = (int)(c % nx), cj = (int)((c / nx) % ny), ck = (int)(c / ((int64_t)nx * ny));
             double kb = layered_kappa(seed, nx, ny, ci, cj, ck);
             double h = 2.0 * ka * kb / (ka + kb);
-            for (int e = 0; e < 9; ++e) {
-              double cpl = h * ((e % 4 == 0 ? 1.0 : 0.0) + unif(seed, STREAM_OFF, base + e, -0.1, 0.1));
+            for (int e = 0; e < bb; ++e) {
+              double cpl = h * ((e % (bs + 1) == 0 ? 1.0 : 0.0) + unif(seed, STREAM_OFF, base + e, -0.1, 0.1));
               blk[e] = -cpl;
               diag[e] += cpl;
             }
           }
           ++p;
         }
-        memcpy(val + 9 * pdiag, diag, sizeof diag);
+        memcpy(val + bb * pdiag, diag, bb * sizeof(double));
       }
   for (int64_t g = 0; g < n; ++g)
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < bs; ++a) {
       double acc = 0.0;
       for (int64_t p = row_ptr[g]; p < row_ptr[g + 1]; ++p)
-        for (int c = 0; c < 3; ++c) acc = fma(val[9 * p + 3 * a + c], xstar[3 * (int64_t)col[p] + c], acc);
-      b[3 * g + a] = acc;
+        for (int c = 0; c < bs; ++c) acc = fma(val[bb * p + bs * a + c], xstar[bs * (int64_t)col[p] + c], acc);
+      b[bs * g + a] = acc;
     }
   return row_ptr[n];
+}
+
+int64_t synth_system(int model, int nx, int ny, int nz, uint64_t seed, int32_t* row_ptr, int32_t* col,
+                     double* val, double* xstar, double* b) {
+  return synth_system_bs(model, 3, nx, ny, nz, seed, row_ptr, col, val, xstar, b);
 }
 
 /* Grid sides of one system of a ragged batch: integers uniform in [lo, hi]. */
