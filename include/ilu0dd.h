@@ -61,12 +61,15 @@ extern "C" {
 
 /* ---- inputs ----------------------------------------------------------- */
 
-/* 3x3-block CSR matrix in natural cell order gidx = i + nx*(j + ny*k).
- * HOST pointers: row_ptr[n_brows+1], col_idx[nnzb] (strictly ascending per
- * row, diagonal block present), val[9*nnzb] (row-major 3x3 blocks). */
+/* Block-CSR matrix in natural cell order gidx = i + nx*(j + ny*k) (grid
+ * path) or any order (partitioned path). HOST pointers: row_ptr[n_brows+1],
+ * col_idx[nnzb] (strictly ascending per row, diagonal block present),
+ * val[bs*bs*nnzb] (row-major bs x bs blocks). block_dim = bs: 3 (also 0) for
+ * 3x3 blocks, 1 for a scalar CSR matrix; vectors then hold bs*n_brows
+ * doubles. */
 typedef struct {
   int32_t n_brows;
-  int32_t reserved;
+  int32_t block_dim;
   int64_t nnzb;
   const int32_t* row_ptr;
   const int32_t* col_idx;
@@ -303,7 +306,7 @@ int bicgstab_state(ilu0dd_ctx* ctx, ilu0dd_info* info, void* stream);
 /*
  * Batched BiCGSTAB over many independent systems (the batching pattern; the
  * paper has no batched solver). Each system is an ilu0dd_ctx from
- * ilu0_dd_setup (any grid and subdomain size, all with the same factor_prec,
+ * ilu0_dd_setup (any grid and subdomain size, all with 3x3 blocks and the same factor_prec,
  * on the current device). ilu0dd_batch_create records them in a small device
  * workspace (ilu0dd_batch_workspace_size bytes, 256-byte aligned, caller-owned)
  * and keeps pointers to the contexts: they must outlive the batch, and a
@@ -374,6 +377,7 @@ int ilu0_dd_export(const ilu0dd_ctx* ctx, int what, void* host_dst, size_t bytes
 #define ILU0DD_Q_APPLY_KERNELS 15 /* kernel launches per apply (always 1) */
 #define ILU0DD_Q_ITER_KERNELS 16  /* kernel launches per BiCGSTAB iteration */
 #define ILU0DD_Q_SELL_SLOTS 17    /* slots of the sliced-ELL SpMV matrix (32 entries each) */
+#define ILU0DD_Q_BLOCK_DIM 18     /* block dimension bs (3 or 1); vectors hold bs*N doubles */
 
 int ilu0_dd_query(const ilu0dd_ctx* ctx, int what, int64_t* value);
 

@@ -29,7 +29,7 @@ X_STREAM, X_SELL_COL, X_SELL_VAL = 13, 14, 15
 
 Q = dict(n=0, nnzb=1, kept=2, nsub=3, nl=4, nu=5, apply_bytes=6, spmv_bytes=7, stream_bytes=8,
          threads=9, smem=10, pieces=11, cuda_error=12, max_levels=13, workspace=14,
-         apply_kernels=15, iter_kernels=16, sell_slots=17)
+         apply_kernels=15, iter_kernels=16, sell_slots=17, block_dim=18)
 
 
 class Ilu0DDError(RuntimeError):
@@ -39,7 +39,7 @@ class Ilu0DDError(RuntimeError):
 
 
 class Bsr(ctypes.Structure):
-    _fields_ = [("n_brows", ctypes.c_int32), ("reserved", ctypes.c_int32), ("nnzb", ctypes.c_int64),
+    _fields_ = [("n_brows", ctypes.c_int32), ("block_dim", ctypes.c_int32), ("nnzb", ctypes.c_int64),
                 ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p)]
 
 
@@ -152,11 +152,25 @@ def default_opts(**kw) -> Opts:
     return o
 
 
+def _block_dim(nnzb, val):
+    """bs of a value array: its last dimension, or sqrt(size / nnzb) when flat."""
+    if val is None or nnzb == 0:
+        return 3
+    v = np.asarray(val)
+    if v.ndim == 3:
+        return int(v.shape[-1])
+    bs = int(round((v.size / nnzb) ** 0.5))
+    if bs * bs * nnzb != v.size:
+        raise ValueError("val must hold bs*bs values per block")
+    return bs
+
+
 def _bsr(row_ptr, col, val):
     rp = np.ascontiguousarray(row_ptr, np.int32)
     ci = np.ascontiguousarray(col, np.int32)
+    bs = _block_dim(int(rp[-1]), val)
     va = None if val is None else np.ascontiguousarray(val, np.float64).reshape(-1)
-    b = Bsr(len(rp) - 1, 0, int(rp[-1]), rp.ctypes.data, ci.ctypes.data, None if va is None else va.ctypes.data)
+    b = Bsr(len(rp) - 1, bs, int(rp[-1]), rp.ctypes.data, ci.ctypes.data, None if va is None else va.ctypes.data)
     return b, (rp, ci, va)
 
 
@@ -262,7 +276,8 @@ class Ilu0DD:
             raise Ilu0DDError(rc, "ilu0_dd_setup_planned")
         self._ctx = ctx
         self.n = self.query("n")
-        self.size = 3 * self.n
+        self.bs = self.query("block_dim")
+        self.size = self.bs * self.n
 
     # -- lifetime ---------------------------------------------------------
     def close(self):
@@ -389,13 +404,14 @@ class Ilu0DD:
 
     def export(self, what):
         n, kept, nsub = self.n, self.query("kept"), self.query("nsub")
+        bb = self.bs * self.bs
         spec = {X_PART_ID: (np.int32, n), X_PERM: (np.int32, n), X_IPERM: (np.int32, n),
                 X_PART_PTR: (np.int32, nsub + 1), X_LEVEL_L: (np.int32, n), X_LEVEL_U: (np.int32, n),
-                X_DD_ROW_PTR: (np.int32, n + 1), X_DD_COL: (np.int32, kept), X_L: (np.float64, 9 * kept),
-                X_UT: (np.float64, 9 * kept), X_INVD: (np.float64, 9 * n), X_AP_ROW_PTR: (np.int32, n + 1),
+                X_DD_ROW_PTR: (np.int32, n + 1), X_DD_COL: (np.int32, kept), X_L: (np.float64, bb * kept),
+                X_UT: (np.float64, bb * kept), X_INVD: (np.float64, bb * n), X_AP_ROW_PTR: (np.int32, n + 1),
                 X_AP_COL: (np.int32, self.query("nnzb")), X_STREAM: (np.uint8, self.query("stream_bytes")),
                 X_SELL_COL: (np.int32, 32 * self.query("sell_slots")),
-                X_SELL_VAL: (np.float64, 9 * 32 * self.query("sell_slots"))}
+                X_SELL_VAL: (np.float64, bb * 32 * self.query("sell_slots"))}
         dt, cnt = spec[what]
         buf = np.empty(cnt, dt)
         self._check(self._lib.ilu0_dd_export(self._ctx, what, buf.ctypes.data, buf.nbytes), "ilu0_dd_export")

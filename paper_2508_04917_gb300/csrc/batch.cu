@@ -132,7 +132,8 @@ int ilu0dd_batch_create(ilu0dd_ctx* const* ctxs, int32_t nsys, const ilu0dd_opts
   if (!ctxs || nsys <= 0 || !out) return ILU0DD_ERR_INVALID;
   *out = nullptr;
   for (int32_t i = 0; i < nsys; ++i)
-    if (!ctxs[i] || ctxs[i]->dev.factor_prec != ctxs[0]->dev.factor_prec || ctxs[i]->device != ctxs[0]->device)
+    if (!ctxs[i] || ctxs[i]->dev.factor_prec != ctxs[0]->dev.factor_prec || ctxs[i]->device != ctxs[0]->device ||
+        ctxs[i]->dev.bs != 3)  // the batched kernels take 3x3 blocks
       return ILU0DD_ERR_INVALID;  // one device, one factor precision per batch
   int64_t na = 0, nt = 0;
   const BatchLayout L = batch_layout(ctxs, nsys, &na, &nt);

@@ -140,7 +140,7 @@ int setup_numeric(ilu0dd_ctx* c, const ilu0dd_bsr* A, const ilu0dd_opts& o, void
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.scal, 0, sizeof(SolverScalars), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.err, 0, sizeof(int32_t) * 4, s);
     for (int v = 0; v < kNumVec && e == cudaSuccess; ++v)
-      e = cudaMemsetAsync(c->ws + L.vec[v], 0, sizeof(double) * 3 * (size_t)p.N, s);
+      e = cudaMemsetAsync(c->ws + L.vec[v], 0, sizeof(double) * p.bs * (size_t)p.N, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host staging buffers die below
     if (e != cudaSuccess) {
       int r = cuda_fail(c, e, "setup upload");
@@ -173,6 +173,7 @@ int setup_numeric(ilu0dd_ctx* c, const ilu0dd_bsr* A, const ilu0dd_opts& o, void
     d.threads = p.threads;
     d.factor_prec = o.factor_prec;
     d.smem_bytes = p.smem_bytes;
+    d.bs = p.bs;
     e = apply_configure(d);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -185,8 +186,8 @@ int setup_numeric(ilu0dd_ctx* c, const ilu0dd_bsr* A, const ilu0dd_opts& o, void
   if (o.keep_host) {
     if (on_device) {  // the host copies the ILDU0 post-processing exactly as factor_ildu0 does
       const int64_t kept = p.dd_rp[p.N];
-      std::vector<double> W(9 * (size_t)kept);
-      invD.resize(9 * (size_t)p.N);
+      std::vector<double> W((size_t)p.bs * p.bs * (size_t)kept);
+      invD.resize((size_t)p.bs * p.bs * (size_t)p.N);
       cudaError_t e = cudaMemcpy(W.data(), dres.w, sizeof(double) * W.size(), cudaMemcpyDeviceToHost);
       if (e == cudaSuccess)
         e = cudaMemcpy(invD.data(), dres.invd, sizeof(double) * invD.size(), cudaMemcpyDeviceToHost);
@@ -350,7 +351,7 @@ int ilu0dd_plan_destroy(ilu0dd_plan* plan) {
 
 int ilu0_dd_apply(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream) {
   if (!ctx || (ctx->plan.N > 0 && (!d_r || !d_z))) return ILU0DD_ERR_INVALID;
-  const size_t n = 3 * (size_t)ctx->plan.N * sizeof(double);
+  const size_t n = (size_t)ctx->plan.bs * (size_t)ctx->plan.N * sizeof(double);
   const char* r = reinterpret_cast<const char*>(d_r);
   const char* z = reinterpret_cast<const char*>(d_z);
   if (r < z + n && z < r + n) return ILU0DD_ERR_INVALID;  // overlapping vectors
@@ -380,7 +381,7 @@ int ilu0_dd_apply_host(ilu0dd_ctx* ctx, const double* h_r, double* h_z, void* st
   CK(ctx, cudaEventRecord(ctx->hevents[0], s));  // after the caller's earlier work
   for (int i = 0; i < nch; ++i) {
     const int s0 = (int)((int64_t)p.nsub * i / nch), s1 = (int)((int64_t)p.nsub * (i + 1) / nch);
-    const size_t r0 = 3 * (size_t)p.part_ptr[s0], r1 = 3 * (size_t)p.part_ptr[s1];
+    const size_t r0 = (size_t)p.bs * p.part_ptr[s0], r1 = (size_t)p.bs * p.part_ptr[s1];
     cudaStream_t cs = ctx->hstreams[i];
     CK(ctx, cudaStreamWaitEvent(cs, ctx->hevents[0], 0));
     CK(ctx, cudaMemcpyAsync(dr + r0, h_r + r0, sizeof(double) * (r1 - r0), cudaMemcpyHostToDevice, cs));
@@ -394,7 +395,7 @@ int ilu0_dd_apply_host(ilu0dd_ctx* ctx, const double* h_r, double* h_z, void* st
 
 int ilu0_dd_apply_unfused(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream) {
   if (!ctx || (ctx->plan.N > 0 && (!d_r || !d_z))) return ILU0DD_ERR_INVALID;
-  const size_t n = 3 * (size_t)ctx->plan.N * sizeof(double);
+  const size_t n = (size_t)ctx->plan.bs * (size_t)ctx->plan.N * sizeof(double);
   const char* r = reinterpret_cast<const char*>(d_r);
   const char* z = reinterpret_cast<const char*>(d_z);
   if (r < z + n && z < r + n) return ILU0DD_ERR_INVALID;  // overlapping vectors
@@ -633,7 +634,8 @@ int ilu0_dd_export(const ilu0dd_ctx* c, int what, void* dst, size_t bytes) {
     case ILU0DD_X_SELL_VAL: {  // device copies, read back
       size_t off = p.lay.stream, n = (size_t)p.stream_bytes;
       if (what == ILU0DD_X_SELL_COL) off = p.lay.sell_col, n = sizeof(int32_t) * (size_t)p.sell_slots * kSlice;
-      if (what == ILU0DD_X_SELL_VAL) off = p.lay.sell_val, n = sizeof(double) * 9 * (size_t)p.sell_slots * kSlice;
+      if (what == ILU0DD_X_SELL_VAL)
+        off = p.lay.sell_val, n = sizeof(double) * p.bs * p.bs * (size_t)p.sell_slots * kSlice;
       if (n != bytes) return ILU0DD_ERR_INVALID;
       if (!n) return ILU0DD_OK;
       cudaError_t e = cudaMemcpy(dst, c->ws + off, n, cudaMemcpyDeviceToHost);
@@ -644,12 +646,13 @@ int ilu0_dd_export(const ilu0dd_ctx* c, int what, void* dst, size_t bytes) {
       return put(c->invD.data(), 8 * c->invD.size());
     case ILU0DD_X_L:
     case ILU0DD_X_UT: {
-      if (!c->have_factors || bytes != 72 * kept) return ILU0DD_ERR_INVALID;
+      const size_t bb = (size_t)p.bs * p.bs;
+      if (!c->have_factors || bytes != 8 * bb * kept) return ILU0DD_ERR_INVALID;
       double* o = static_cast<double*>(dst);
       for (int32_t i = 0; i < p.N; ++i)
         for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1]; ++q) {
           const bool take = what == ILU0DD_X_L ? p.dd_col[q] < i : p.dd_col[q] > i;
-          for (int e = 0; e < 9; ++e) o[9 * q + e] = take ? c->F[9 * (size_t)q + e] : 0.0;
+          for (size_t e = 0; e < bb; ++e) o[bb * q + e] = take ? c->F[bb * (size_t)q + e] : 0.0;
         }
       return ILU0DD_OK;
     }
@@ -679,6 +682,7 @@ int ilu0_dd_query(const ilu0dd_ctx* c, int what, int64_t* v) {
     case ILU0DD_Q_APPLY_KERNELS: *v = 1; break;
     case ILU0DD_Q_ITER_KERNELS: *v = 5; break;
     case ILU0DD_Q_SELL_SLOTS: *v = p.sell_slots; break;
+    case ILU0DD_Q_BLOCK_DIM: *v = p.bs; break;
     default: return ILU0DD_ERR_INVALID;
   }
   return ILU0DD_OK;

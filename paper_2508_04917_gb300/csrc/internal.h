@@ -132,6 +132,8 @@ using RawVec = std::vector<T, NoInitAlloc<T>>;
 struct Plan {
   int32_t N = 0;
   int64_t nnzb = 0;
+  int bs = 3;                                     // block dimension: 3 (3x3 blocks) or 1 (scalar CSR)
+  int rows_per_warp = kRowsPerWarp;               // apply rows per warp: 10 (three threads a row) or 32
   ilu0dd_geom geom{};
   ilu0dd_opts opts{};
   int32_t nsub = 0;

@@ -34,8 +34,21 @@ __device__ __forceinline__ int gu16(const unsigned char* p) {
   return (int)__ldg(reinterpret_cast<const unsigned short*>(p));
 }
 
+// Row i's contribution to a dot product in the fixed order: x0*y0, then
+// fma(x_c, y_c, .) for c = 1..BS-1 (BS = 3: fma(x2,y2,fma(x1,y1,x0*y0))).
+template <int BS>
 __device__ __forceinline__ double row_dot(const double* x, const double* y, int64_t i) {
-  return fma(x[3 * i + 2], y[3 * i + 2], fma(x[3 * i + 1], y[3 * i + 1], x[3 * i] * y[3 * i]));
+  double q = x[BS * i] * y[BS * i];
+#pragma unroll
+  for (int c = 1; c < BS; ++c) q = fma(x[BS * i + c], y[BS * i + c], q);
+  return q;
+}
+template <int BS>
+__device__ __forceinline__ double reg_dot(const double (&a)[BS], const double (&b)[BS]) {
+  double q = a[0] * b[0];
+#pragma unroll
+  for (int c = 1; c < BS; ++c) q = fma(a[c], b[c], q);
+  return q;
 }
 
 __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
@@ -58,9 +71,13 @@ __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 // Modes: plain z = M^-1 r; P: p <- r + beta (p - omega v), z = M^-1 p;
 // S: s <- r - alpha v, z = M^-1 s. Modes P and S skip a finished solve.
 // PART 0 runs every piece (the fused apply); 1 only the L sweep, 2 only the
-// D^-1 and U~ sweep (the two launches of the unfused apply).
-template <typename TF, int MODE, int PART = 0>
+// D^-1 and U~ sweep (the two launches of the unfused apply). BS = block
+// dimension: 3 (three threads per block row, ten rows per warp) or 1 (scalar
+// CSR: one thread per row, 32 rows per warp).
+template <typename TF, int MODE, int PART = 0, int BS = 3>
 __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const double* r, double* z) {
+  static_assert(BS == 1 || BS == 3, "block dimension 1 or 3");
+  constexpr int RPW = BS == 3 ? kRowsPerWarp : 32;  // rows per warp
   using TV = typename FactorLoad<TF>::compute;
   constexpr uint32_t FE = sizeof(TF);
   extern __shared__ __align__(128) unsigned char smem[];
@@ -90,8 +107,8 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
   if (pf_thread) prefetch_upto(pf_end + dist);
 
   // subdomain vector -> shared memory (with the fused BiCGSTAB update)
-  const int64_t base = 3ll * cd.row0;
-  const int nv = 3 * cd.nrows;
+  const int64_t base = (int64_t)BS * cd.row0;
+  const int nv = BS * cd.nrows;
   double alpha = 0.0, beta = 0.0, omega = 0.0;
   if (MODE == kModeP) { beta = S.scal->beta; omega = S.scal->omega; }
   if (MODE == kModeS) alpha = S.scal->alpha;
@@ -136,11 +153,11 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
   __syncthreads();
 
   const int warp = tid >> 5, lane = tid & 31;
-  const int comp = lane % 3;
-  const int trow = warp * kRowsPerWarp + lane / 3;
-  const bool lane_ok = lane < 3 * kRowsPerWarp;
+  const int comp = BS == 3 ? lane % 3 : 0;
+  const int trow = warp * RPW + (BS == 3 ? lane / 3 : lane);
+  const bool lane_ok = BS == 3 ? lane < 3 * kRowsPerWarp : true;
   const int base_lane = lane - comp;
-  const uint32_t lane_voff = (uint32_t)(3 * trow + comp) * FE;  // this thread's value offset in a slot
+  const uint32_t lane_voff = (uint32_t)(BS * trow + comp) * FE;  // this thread's value offset in a slot
   const uint32_t trow2 = 2u * (uint32_t)trow;
 
   // piece descriptors are staged in shared memory, kDescCache at a time
@@ -159,15 +176,15 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
     const int n = (int)(pd.meta & 0xFFFFu);
     const int w = (int)((pd.meta >> 16) & 0xFFu);
     const int kind = (int)(pd.meta >> 24);
-    if (warp * kRowsPerWarp < n) {  // warp-uniform: this warp has rows in the piece
+    if (warp * RPW < n) {  // warp-uniform: this warp has rows in the piece
       const bool active = lane_ok && trow < n;
       const unsigned char* rec = gs + pd.off;
       // 32-bit byte offsets from the block's (uniform) stream base: the
       // warp-uniform part per slot plus this thread's fixed part
-      const uint32_t vbase = pd.off + pd.voff + (kind ? 9u * (uint32_t)n * FE : 0u);
+      const uint32_t vbase = pd.off + pd.voff + (kind ? (uint32_t)(BS * BS) * (uint32_t)n * FE : 0u);
       const uint32_t cbase = pd.off + 2u * (uint32_t)(w + n);
       int col[kDescSlots];
-      TV bv[kDescSlots][3];
+      TV bv[kDescSlots][BS];
       uint32_t c0 = 0;
       int nsl = 0;
 #pragma unroll
@@ -176,40 +193,45 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
         const bool has = active && sl < w && (uint32_t)trow < cs;
         nsl += has;
         col[sl] = has ? gu16(gs + (cbase + 2u * c0 + trow2)) : 0;
-        const uint32_t vo = vbase + 9u * FE * c0 + lane_voff;
-        const uint32_t cstride = 3u * FE * cs;
+        const uint32_t vo = vbase + (uint32_t)(BS * BS) * FE * c0 + lane_voff;
+        const uint32_t cstride = (uint32_t)BS * FE * cs;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) bv[sl][c] = has ? gfactor<TF>(gs + (vo + (uint32_t)c * cstride)) : TV(0);
+        for (int c = 0; c < BS; ++c) bv[sl][c] = has ? gfactor<TF>(gs + (vo + (uint32_t)c * cstride)) : TV(0);
         c0 += cs;
       }
-      TV d[3] = {TV(0), TV(0), TV(0)};
+      TV d[BS];
+#pragma unroll
+      for (int c = 0; c < BS; ++c) d[c] = TV(0);
       if (kind && active) {
         const uint32_t io = pd.off + pd.voff + lane_voff;
-        const uint32_t cstride = 3u * FE * (uint32_t)n;
+        const uint32_t cstride = (uint32_t)BS * FE * (uint32_t)n;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) d[c] = gfactor<TF>(gs + (io + (uint32_t)c * cstride));
+        for (int c = 0; c < BS; ++c) d[c] = gfactor<TF>(gs + (io + (uint32_t)c * cstride));
       }
       const int row = active ? gu16(gs + (pd.off + 2u * (uint32_t)w + trow2)) : 0;
-      TV acc = active ? y[3 * row + comp] : TV(0);
+      TV acc = active ? y[BS * row + comp] : TV(0);
       if (kind) {
-        // D^-1 (Section 4.3): w_i = D_i^-1 y_i; the row's three components
-        // come from the neighbouring lanes
-        const TV y0 = shfl(acc, base_lane);
-        const TV y1 = shfl(acc, base_lane + 1);
-        const TV y2 = shfl(acc, base_lane + 2);
-        TV t = d[0] * y0;
-        t = mac(d[1], y1, t);
-        t = mac(d[2], y2, t);
-        if (active) acc = t;
+        // D^-1 (Section 4.3): w_i = D_i^-1 y_i; with 3x3 blocks the row's
+        // three components come from the neighbouring lanes
+        if constexpr (BS == 3) {
+          const TV y0 = shfl(acc, base_lane);
+          const TV y1 = shfl(acc, base_lane + 1);
+          const TV y2 = shfl(acc, base_lane + 2);
+          TV t = d[0] * y0;
+          t = mac(d[1], y1, t);
+          t = mac(d[2], y2, t);
+          if (active) acc = t;
+        } else {
+          if (active) acc = d[0] * acc;
+        }
       }
       if (active) {
 #pragma unroll
         for (int sl = 0; sl < kDescSlots; ++sl) {
           if (sl < nsl) {
             const int cl = col[sl];
-            acc = mac(-bv[sl][0], y[3 * cl], acc);
-            acc = mac(-bv[sl][1], y[3 * cl + 1], acc);
-            acc = mac(-bv[sl][2], y[3 * cl + 2], acc);
+#pragma unroll
+            for (int c = 0; c < BS; ++c) acc = mac(-bv[sl][c], y[BS * cl + c], acc);
           }
         }
         // rows with more than kDescSlots blocks (general patterns): remaining slots
@@ -218,15 +240,14 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
             const uint32_t cs = (uint32_t)gu16(rec + 2 * sl);
             if ((uint32_t)trow >= cs) break;
             const int cl = gu16(gs + (cbase + 2u * c0 + trow2));
-            const uint32_t vo = vbase + 9u * FE * c0 + lane_voff;
-            const uint32_t cstride = 3u * FE * cs;
-            acc = mac(-gfactor<TF>(gs + vo), y[3 * cl], acc);
-            acc = mac(-gfactor<TF>(gs + (vo + cstride)), y[3 * cl + 1], acc);
-            acc = mac(-gfactor<TF>(gs + (vo + 2u * cstride)), y[3 * cl + 2], acc);
+            const uint32_t vo = vbase + (uint32_t)(BS * BS) * FE * c0 + lane_voff;
+            const uint32_t cstride = (uint32_t)BS * FE * cs;
+#pragma unroll
+            for (int c = 0; c < BS; ++c) acc = mac(-gfactor<TF>(gs + (vo + (uint32_t)c * cstride)), y[BS * cl + c], acc);
             c0 += cs;
           }
         }
-        y[3 * row + comp] = acc;
+        y[BS * row + comp] = acc;
       }
     }
     __syncthreads();
@@ -251,18 +272,18 @@ struct ApplyMinBlocks<df64s> {  // pairs need FP64-sized registers
   static constexpr int value = kApplyMinBlocks;
 };
 
-template <typename TF, int MODE>
+template <typename TF, int MODE, int BS>
 __global__ void __launch_bounds__(kMaxApplyThreads, ApplyMinBlocks<TF>::value)
     ildu0_apply_kernel(SysDesc S, const double* r, double* z, int sub0) {
-  apply_block<TF, MODE>(S, sub0 + blockIdx.x, r, z);
+  apply_block<TF, MODE, 0, BS>(S, sub0 + blockIdx.x, r, z);
 }
 
 // The unfused apply's two launches (plain mode): PART 1 = L sweep, r -> z;
 // PART 2 = D^-1 and U~ sweep, z -> z in place.
-template <typename TF, int PART>
+template <typename TF, int PART, int BS>
 __global__ void __launch_bounds__(kMaxApplyThreads, ApplyMinBlocks<TF>::value)
     ildu0_apply_part_kernel(SysDesc S, const double* r, double* z) {
-  apply_block<TF, kModePlain, PART>(S, blockIdx.x, r, z);
+  apply_block<TF, kModePlain, PART, BS>(S, blockIdx.x, r, z);
 }
 
 // Batched apply (modes P and S): persistent blocks walk (system, subdomain) items.
@@ -279,14 +300,22 @@ __global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
 
 template <typename TF, int MODE>
 static cudaError_t configure_one(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(ildu0_apply_kernel<TF, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  const int sm = (int)smem;
+  cudaError_t e = cudaFuncSetAttribute(ildu0_apply_kernel<TF, MODE, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(ildu0_apply_kernel<TF, MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e == cudaSuccess && MODE != kModePlain)
-    e = cudaFuncSetAttribute(ildu0_apply_batched<TF, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess && MODE == kModePlain)
-    e = cudaFuncSetAttribute(ildu0_apply_part_kernel<TF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess && MODE == kModePlain)
-    e = cudaFuncSetAttribute(ildu0_apply_part_kernel<TF, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(ildu0_apply_batched<TF, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (MODE == kModePlain) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ildu0_apply_part_kernel<TF, 1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ildu0_apply_part_kernel<TF, 2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ildu0_apply_part_kernel<TF, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ildu0_apply_part_kernel<TF, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  }
   return e;
 }
 
@@ -316,17 +345,24 @@ cudaError_t apply_configure(const DevCtx& d) {
   return e;
 }
 
+template <typename TF, int BS>
+static cudaError_t launch_apply_tb(const DevCtx& d, int mode, const double* r, double* z, int sub0, int nsub,
+                                   cudaStream_t s) {
+  dim3 grid(nsub), block(d.threads);
+  if (mode == kModePlain)
+    ildu0_apply_kernel<TF, kModePlain, BS><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
+  else if (mode == kModeP)
+    ildu0_apply_kernel<TF, kModeP, BS><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
+  else
+    ildu0_apply_kernel<TF, kModeS, BS><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
+  return cudaGetLastError();
+}
+
 template <typename TF>
 static cudaError_t launch_apply_t(const DevCtx& d, int mode, const double* r, double* z, int sub0, int nsub,
                                   cudaStream_t s) {
-  dim3 grid(nsub), block(d.threads);
-  if (mode == kModePlain)
-    ildu0_apply_kernel<TF, kModePlain><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
-  else if (mode == kModeP)
-    ildu0_apply_kernel<TF, kModeP><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
-  else
-    ildu0_apply_kernel<TF, kModeS><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
-  return cudaGetLastError();
+  return d.bs == 1 ? launch_apply_tb<TF, 1>(d, mode, r, z, sub0, nsub, s)
+                   : launch_apply_tb<TF, 3>(d, mode, r, z, sub0, nsub, s);
 }
 
 cudaError_t launch_apply_range(const DevCtx& d, int mode, const double* r, double* z, int sub0, int nsub,
@@ -342,14 +378,19 @@ cudaError_t launch_apply(const DevCtx& d, int mode, const double* r, double* z, 
   return launch_apply_range(d, mode, r, z, 0, d.sd.nsub, s);
 }
 
-template <typename TF>
-static cudaError_t launch_unfused_t(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
+template <typename TF, int BS>
+static cudaError_t launch_unfused_tb(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
   dim3 grid(d.sd.nsub), block(d.threads);
-  ildu0_apply_part_kernel<TF, 1><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z);
+  ildu0_apply_part_kernel<TF, 1, BS><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  ildu0_apply_part_kernel<TF, 2><<<grid, block, d.smem_bytes, s>>>(d.sd, z, z);
+  ildu0_apply_part_kernel<TF, 2, BS><<<grid, block, d.smem_bytes, s>>>(d.sd, z, z);
   return cudaGetLastError();
+}
+
+template <typename TF>
+static cudaError_t launch_unfused_t(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
+  return d.bs == 1 ? launch_unfused_tb<TF, 1>(d, r, z, s) : launch_unfused_tb<TF, 3>(d, r, z, s);
 }
 
 cudaError_t launch_apply_unfused(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
@@ -435,38 +476,37 @@ __device__ __forceinline__ void finish_sum(double* partials, int64_t stride, int
 // ===========================================================================
 // SpMV (sliced ELL), kinds: 0 plain, 1 (rh . v) -> alpha, 2 (t . s), (t . t) -> omega
 // ===========================================================================
-template <int KIND>
+template <int KIND, int BS = 3>
 __device__ __forceinline__ void spmv_block(const SysDesc& S, int64_t tile, const double* x, double* y) {
   if (KIND != 0 && S.scal->done) return;
+  constexpr int BB = BS * BS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t slice = tile * (kDotTile / kSlice) + warp;
   const int64_t row = slice * kSlice + lane;
-  double y0 = 0.0, y1 = 0.0, y2 = 0.0;
+  double yv[BS];
+#pragma unroll
+  for (int a = 0; a < BS; ++a) yv[a] = 0.0;
   if (slice < S.nslices) {
     const int64_t so = S.slice_off[slice];
     const int w = S.slice_off[slice + 1] - (int32_t)so;
     const int32_t* cp = S.sell_col + so * kSlice + lane;
-    const double* vp = S.sell_val + so * 9 * kSlice + lane;
+    const double* vp = S.sell_val + so * BB * kSlice + lane;
     for (int sl = 0; sl < w; ++sl) {
       const int c = __ldg(cp + sl * kSlice);
-      double b[9];
+      double b[BB];
 #pragma unroll
-      for (int e = 0; e < 9; ++e) b[e] = __ldg(vp + (sl * 9 + e) * kSlice);
-      const double x0 = x[3ll * c], x1 = x[3ll * c + 1], x2 = x[3ll * c + 2];
-      y0 = fma(b[0], x0, y0);
-      y1 = fma(b[3], x0, y1);
-      y2 = fma(b[6], x0, y2);
-      y0 = fma(b[1], x1, y0);
-      y1 = fma(b[4], x1, y1);
-      y2 = fma(b[7], x1, y2);
-      y0 = fma(b[2], x2, y0);
-      y1 = fma(b[5], x2, y1);
-      y2 = fma(b[8], x2, y2);
+      for (int e = 0; e < BB; ++e) b[e] = __ldg(vp + (sl * BB + e) * kSlice);
+      // per output entry a: blocks in slot order, within a block c = 0..BS-1
+#pragma unroll
+      for (int cc = 0; cc < BS; ++cc) {
+        const double xc = x[(int64_t)BS * c + cc];
+#pragma unroll
+        for (int a = 0; a < BS; ++a) yv[a] = fma(b[BS * a + cc], xc, yv[a]);
+      }
     }
     if (row < S.N) {
-      y[3 * row] = y0;
-      y[3 * row + 1] = y1;
-      y[3 * row + 2] = y2;
+#pragma unroll
+      for (int a = 0; a < BS; ++a) y[BS * row + a] = yv[a];
     }
   }
   if (KIND == 0) return;
@@ -475,7 +515,10 @@ __device__ __forceinline__ void spmv_block(const SysDesc& S, int64_t tile, const
   const int64_t m = S.ntiles_pow2;
   if (KIND == 1) {
     const double* w = S.vec[kVecRh];
-    double q[1] = {in ? fma(w[3 * row + 2], y2, fma(w[3 * row + 1], y1, w[3 * row] * y0)) : 0.0};
+    double wv[BS];
+#pragma unroll
+    for (int a = 0; a < BS; ++a) wv[a] = in ? w[BS * row + a] : 0.0;
+    double q[1] = {in ? reg_dot<BS>(wv, yv) : 0.0};
     tile_halving_sum<1>(q, buf);
     uint32_t* counter = S.counters + kCntSpmvV;
     if (!publish_partials<1>(q, S.partials, m, tile, S.ntiles, counter)) return;
@@ -496,8 +539,10 @@ __device__ __forceinline__ void spmv_block(const SysDesc& S, int64_t tile, const
   } else {
     // (t . s) and (t . t), t = y
     const double* w = S.vec[kVecS];
-    double q[2] = {in ? fma(y2, w[3 * row + 2], fma(y1, w[3 * row + 1], y0 * w[3 * row])) : 0.0,
-                   in ? fma(y2, y2, fma(y1, y1, y0 * y0)) : 0.0};
+    double wv[BS];
+#pragma unroll
+    for (int a = 0; a < BS; ++a) wv[a] = in ? w[BS * row + a] : 0.0;
+    double q[2] = {in ? reg_dot<BS>(yv, wv) : 0.0, in ? reg_dot<BS>(yv, yv) : 0.0};
     tile_halving_sum<2>(q, buf);
     uint32_t* counter = S.counters + kCntSpmvT;
     if (!publish_partials<2>(q, S.partials, m, tile, S.ntiles, counter)) return;
@@ -513,9 +558,9 @@ __device__ __forceinline__ void spmv_block(const SysDesc& S, int64_t tile, const
   }
 }
 
-template <int KIND>
+template <int KIND, int BS>
 __global__ void __launch_bounds__(kDotTile) sell_spmv_kernel(SysDesc S, const double* x, double* y) {
-  spmv_block<KIND>(S, blockIdx.x, x, y);
+  spmv_block<KIND, BS>(S, blockIdx.x, x, y);
 }
 
 template <int KIND>
@@ -534,16 +579,21 @@ __global__ void __launch_bounds__(kDotTile)
   }
 }
 
-cudaError_t launch_spmv(const DevCtx& d, int kind, const double* x, double* y, cudaStream_t s) {
-  if (d.sd.N == 0) return cudaSuccess;
+template <int BS>
+static cudaError_t launch_spmv_b(const DevCtx& d, int kind, const double* x, double* y, cudaStream_t s) {
   dim3 grid((unsigned)d.sd.ntiles), block(kDotTile);
   if (kind == 0)
-    sell_spmv_kernel<0><<<grid, block, 0, s>>>(d.sd, x, y);
+    sell_spmv_kernel<0, BS><<<grid, block, 0, s>>>(d.sd, x, y);
   else if (kind == 1)
-    sell_spmv_kernel<1><<<grid, block, 0, s>>>(d.sd, x, y);
+    sell_spmv_kernel<1, BS><<<grid, block, 0, s>>>(d.sd, x, y);
   else
-    sell_spmv_kernel<2><<<grid, block, 0, s>>>(d.sd, x, y);
+    sell_spmv_kernel<2, BS><<<grid, block, 0, s>>>(d.sd, x, y);
   return cudaGetLastError();
+}
+
+cudaError_t launch_spmv(const DevCtx& d, int kind, const double* x, double* y, cudaStream_t s) {
+  if (d.sd.N == 0) return cudaSuccess;
+  return d.bs == 1 ? launch_spmv_b<1>(d, kind, x, y, s) : launch_spmv_b<3>(d, kind, x, y, s);
 }
 
 cudaError_t launch_spmv_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int kind, int grid,
@@ -563,6 +613,7 @@ cudaError_t launch_spmv_batched(const SysDesc* sys, const BatchItem* items, int6
 // ===========================================================================
 
 // x += alpha ph + omega sh; r = s - omega t; then ||r||/||b|| and rho.
+template <int BS = 3>
 __device__ __forceinline__ void update_block(const SysDesc& S, int64_t tile) {
   SolverScalars* sc = S.scal;
   if (sc->done) return;
@@ -577,16 +628,17 @@ __device__ __forceinline__ void update_block(const SysDesc& S, int64_t tile) {
     const double* sv = S.vec[kVecS];
     const double* t = S.vec[kVecT];
     const double* rh = S.vec[kVecRh];
-    double rr[3];
+    double rr[BS], rhv[BS];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int64_t e = 3 * i + c;
+    for (int c = 0; c < BS; ++c) {
+      const int64_t e = BS * i + c;
       x[e] = fma(omega, sh[e], fma(alpha, ph[e], x[e]));
       rr[c] = fma(-omega, t[e], sv[e]);
       r[e] = rr[c];
+      rhv[c] = rh[e];
     }
-    q[0] = fma(rr[2], rr[2], fma(rr[1], rr[1], rr[0] * rr[0]));
-    q[1] = fma(rh[3 * i + 2], rr[2], fma(rh[3 * i + 1], rr[1], rh[3 * i] * rr[0]));
+    q[0] = reg_dot<BS>(rr, rr);
+    q[1] = reg_dot<BS>(rhv, rr);
   }
   __shared__ double buf[2][kDotTile];
   tile_halving_sum<2>(q, buf);
@@ -623,14 +675,15 @@ __device__ __forceinline__ void update_block(const SysDesc& S, int64_t tile) {
 }
 
 // x = 0, r = rh = p = b, v = 0; bb = rho = (b . b).
+template <int BS = 3>
 __device__ __forceinline__ void init_block(const SysDesc& S, int64_t tile, double rtol, int32_t maxit) {
   const int64_t i = tile * kDotTile + threadIdx.x;
   double q[1] = {0.0};
   if (i < S.N) {
     const double* b = S.vec[kVecB];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int64_t e = 3 * i + c;
+    for (int c = 0; c < BS; ++c) {
+      const int64_t e = BS * i + c;
       const double be = b[e];
       S.vec[kVecX][e] = 0.0;
       S.vec[kVecR][e] = be;
@@ -638,7 +691,7 @@ __device__ __forceinline__ void init_block(const SysDesc& S, int64_t tile, doubl
       S.vec[kVecP][e] = be;
       S.vec[kVecV][e] = 0.0;
     }
-    q[0] = row_dot(b, b, i);
+    q[0] = row_dot<BS>(b, b, i);
   }
   __shared__ double buf[1][kDotTile];
   tile_halving_sum<1>(q, buf);
@@ -679,18 +732,19 @@ __device__ __forceinline__ void init_block(const SysDesc& S, int64_t tile, doubl
 }
 
 // r = b - t (t = A x computed before), rel_true = ||r||/||b||.
+template <int BS = 3>
 __device__ __forceinline__ void residual_block(const SysDesc& S, int64_t tile) {
   const int64_t i = tile * kDotTile + threadIdx.x;
   double q[1] = {0.0};
   if (i < S.N) {
-    double rr[3];
+    double rr[BS];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int64_t e = 3 * i + c;
+    for (int c = 0; c < BS; ++c) {
+      const int64_t e = BS * i + c;
       rr[c] = S.vec[kVecB][e] - S.vec[kVecT][e];
       S.vec[kVecR][e] = rr[c];
     }
-    q[0] = fma(rr[2], rr[2], fma(rr[1], rr[1], rr[0] * rr[0]));
+    q[0] = reg_dot<BS>(rr, rr);
   }
   __shared__ double buf[1][kDotTile];
   tile_halving_sum<1>(q, buf);
@@ -708,12 +762,13 @@ __device__ __forceinline__ void residual_block(const SysDesc& S, int64_t tile) {
 }
 
 // Continue from r: rh = p = r, v = 0, rho = (r . r) of the true residual, done = 0.
+template <int BS = 3>
 __device__ __forceinline__ void restart_block(const SysDesc& S, int64_t tile) {
   const int64_t i = tile * kDotTile + threadIdx.x;
   if (i < S.N) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int64_t e = 3 * i + c;
+    for (int c = 0; c < BS; ++c) {
+      const int64_t e = BS * i + c;
       const double re = S.vec[kVecR][e];
       S.vec[kVecRh][e] = re;
       S.vec[kVecP][e] = re;
@@ -729,17 +784,20 @@ __device__ __forceinline__ void restart_block(const SysDesc& S, int64_t tile) {
   }
 }
 
-__global__ void __launch_bounds__(kDotTile) update_kernel(SysDesc S) { update_block(S, blockIdx.x); }
+template <int BS>
+__global__ void __launch_bounds__(kDotTile) update_kernel(SysDesc S) { update_block<BS>(S, blockIdx.x); }
 
+template <int BS>
 __global__ void __launch_bounds__(kDotTile) init_kernel(SysDesc S, double rtol, int32_t maxit) {
-  init_block(S, blockIdx.x, rtol, maxit);
+  init_block<BS>(S, blockIdx.x, rtol, maxit);
 }
 
+template <int BS>
 __global__ void __launch_bounds__(kDotTile) residual_kernel(SysDesc S, int restart) {
   if (restart)
-    restart_block(S, blockIdx.x);
+    restart_block<BS>(S, blockIdx.x);
   else
-    residual_block(S, blockIdx.x);
+    residual_block<BS>(S, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kDotTile)
@@ -770,19 +828,28 @@ __global__ void __launch_bounds__(kDotTile)
 
 cudaError_t launch_update(const DevCtx& d, cudaStream_t s) {
   if (d.sd.N == 0) return cudaSuccess;
-  update_kernel<<<(unsigned)d.sd.ntiles, kDotTile, 0, s>>>(d.sd);
+  if (d.bs == 1)
+    update_kernel<1><<<(unsigned)d.sd.ntiles, kDotTile, 0, s>>>(d.sd);
+  else
+    update_kernel<3><<<(unsigned)d.sd.ntiles, kDotTile, 0, s>>>(d.sd);
   return cudaGetLastError();
 }
 
 cudaError_t launch_init(const DevCtx& d, double rtol, int32_t maxit, cudaStream_t s) {
   if (d.sd.N == 0) return cudaSuccess;
-  init_kernel<<<(unsigned)d.sd.ntiles, kDotTile, 0, s>>>(d.sd, rtol, maxit);
+  if (d.bs == 1)
+    init_kernel<1><<<(unsigned)d.sd.ntiles, kDotTile, 0, s>>>(d.sd, rtol, maxit);
+  else
+    init_kernel<3><<<(unsigned)d.sd.ntiles, kDotTile, 0, s>>>(d.sd, rtol, maxit);
   return cudaGetLastError();
 }
 
 cudaError_t launch_residual(const DevCtx& d, int restart, cudaStream_t s) {
   if (d.sd.N == 0) return cudaSuccess;
-  residual_kernel<<<(unsigned)d.sd.ntiles, kDotTile, 0, s>>>(d.sd, restart);
+  if (d.bs == 1)
+    residual_kernel<1><<<(unsigned)d.sd.ntiles, kDotTile, 0, s>>>(d.sd, restart);
+  else
+    residual_kernel<3><<<(unsigned)d.sd.ntiles, kDotTile, 0, s>>>(d.sd, restart);
   return cudaGetLastError();
 }
 
@@ -812,10 +879,11 @@ int tile_blocks_per_sm() {
 // ===========================================================================
 // Standalone dot product, permutation, status
 // ===========================================================================
+template <int BS>
 __global__ void __launch_bounds__(kDotTile) dot_kernel(const double* x, const double* y, int32_t N, double* partials,
                                                        int64_t m, uint32_t* counter, double* out_p) {
   const int64_t i = (int64_t)blockIdx.x * kDotTile + threadIdx.x;
-  double q[1] = {i < N ? row_dot(x, y, i) : 0.0};
+  double q[1] = {i < N ? row_dot<BS>(x, y, i) : 0.0};
   __shared__ double buf[1][kDotTile];
   tile_halving_sum<1>(q, buf);
   if (!publish_partials<1>(q, partials, m, blockIdx.x, gridDim.x, counter)) return;
@@ -829,36 +897,45 @@ __global__ void __launch_bounds__(kDotTile) dot_kernel(const double* x, const do
 
 cudaError_t launch_dot(const DevCtx& d, const double* x, const double* y, double* out, cudaStream_t s) {
   if (d.sd.N == 0) return cudaMemsetAsync(out, 0, sizeof(double), s);
-  dot_kernel<<<(unsigned)d.sd.ntiles, kDotTile, 0, s>>>(x, y, d.sd.N, d.sd.partials, d.sd.ntiles_pow2,
-                                                         d.sd.counters + kCntDot, out);
+  if (d.bs == 1)
+    dot_kernel<1><<<(unsigned)d.sd.ntiles, kDotTile, 0, s>>>(x, y, d.sd.N, d.sd.partials, d.sd.ntiles_pow2,
+                                                              d.sd.counters + kCntDot, out);
+  else
+    dot_kernel<3><<<(unsigned)d.sd.ntiles, kDotTile, 0, s>>>(x, y, d.sd.N, d.sd.partials, d.sd.ntiles_pow2,
+                                                              d.sd.counters + kCntDot, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dot_scratch(const double* x, const double* y, int32_t n_brows, double* partials, int64_t m,
                                uint32_t* counter, double* out, cudaStream_t s) {
   const int64_t ntiles = ((int64_t)n_brows + kDotTile - 1) / kDotTile;
-  dot_kernel<<<(unsigned)ntiles, kDotTile, 0, s>>>(x, y, n_brows, partials, m, counter, out);
+  dot_kernel<3><<<(unsigned)ntiles, kDotTile, 0, s>>>(x, y, n_brows, partials, m, counter, out);
   return cudaGetLastError();
 }
 
-// out[i] = in[map[i]] (3 doubles per row): map = perm gathers natural -> reordered,
+// out[i] = in[map[i]] (BS doubles per row): map = perm gathers natural -> reordered,
 // map = iperm gathers reordered -> natural.
+template <int BS = 3>
 __device__ __forceinline__ void gather_rows(const double* in, double* out, const int32_t* map, int64_t i) {
   const int64_t j = map[i];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) out[3 * i + c] = in[3 * j + c];
+  for (int c = 0; c < BS; ++c) out[BS * i + c] = in[BS * j + c];
 }
 
+template <int BS>
 __global__ void permute_kernel(const double* in, double* out, const int32_t* map, int32_t N) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) gather_rows(in, out, map, i);
+  if (i < N) gather_rows<BS>(in, out, map, i);
 }
 
 cudaError_t launch_permute(const DevCtx& d, const double* in, double* out, int dir, cudaStream_t s) {
   if (d.sd.N == 0) return cudaSuccess;
   const int threads = 256;
   const unsigned blocks = (unsigned)((d.sd.N + threads - 1) / threads);
-  permute_kernel<<<blocks, threads, 0, s>>>(in, out, dir == 0 ? d.sd.perm : d.sd.iperm, d.sd.N);
+  if (d.bs == 1)
+    permute_kernel<1><<<blocks, threads, 0, s>>>(in, out, dir == 0 ? d.sd.perm : d.sd.iperm, d.sd.N);
+  else
+    permute_kernel<3><<<blocks, threads, 0, s>>>(in, out, dir == 0 ? d.sd.perm : d.sd.iperm, d.sd.N);
   return cudaGetLastError();
 }
 

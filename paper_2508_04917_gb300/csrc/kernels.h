@@ -40,6 +40,7 @@ struct DevCtx {
   SysDesc sd;
   int threads, factor_prec;
   size_t smem_bytes;
+  int bs = 3;  // block dimension: 3 or 1 (scalar CSR); batched launches take 3 only
 };
 
 // Work item of a batched launch: system index and block index inside it.

@@ -43,51 +43,52 @@ void parallel_for(int64_t n, F&& f) {
 }
 
 // Bytes of one piece record (see internal.h).
-int64_t record_bytes(int n, int w, int64_t nb, int kind, int felem, int64_t* voff) {
+int64_t record_bytes(int n, int w, int64_t nb, int kind, int felem, int bs, int64_t* voff) {
   int64_t head = 2 * (int64_t)w + 2 * (int64_t)n + 2 * nb;
   int64_t v = align_up(head, 16);
   if (voff) *voff = v;
-  int64_t vals = (kind ? 9 * (int64_t)n : 0) + 9 * nb;
+  const int64_t bb = (int64_t)bs * bs;
+  int64_t vals = (kind ? bb * n : 0) + bb * nb;
   return align_up(v + vals * felem, 16);
 }
 
-// 3x3 inverse by Gauss-Jordan elimination with partial pivoting.
-bool inverse3(const double* M, double* X) {
+// bs x bs inverse (bs <= 3) by Gauss-Jordan elimination with partial pivoting.
+bool inverse_bs(int bs, const double* M, double* X) {
   double a[3][6];
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 6; ++c) a[r][c] = c < 3 ? M[3 * r + c] : (c - 3 == r ? 1.0 : 0.0);
-  for (int c = 0; c < 3; ++c) {
+  for (int r = 0; r < bs; ++r)
+    for (int c = 0; c < 2 * bs; ++c) a[r][c] = c < bs ? M[bs * r + c] : (c - bs == r ? 1.0 : 0.0);
+  for (int c = 0; c < bs; ++c) {
     int piv = c;
-    for (int r = c + 1; r < 3; ++r)
+    for (int r = c + 1; r < bs; ++r)
       if (std::fabs(a[r][c]) > std::fabs(a[piv][c])) piv = r;
     double pv = a[piv][c];
     if (!(std::fabs(pv) > 0.0) || !std::isfinite(pv)) return false;
     if (piv != c)
-      for (int q = 0; q < 6; ++q) std::swap(a[c][q], a[piv][q]);
+      for (int q = 0; q < 2 * bs; ++q) std::swap(a[c][q], a[piv][q]);
     double inv = 1.0 / a[c][c];
-    for (int q = 0; q < 6; ++q) a[c][q] *= inv;
-    for (int r = 0; r < 3; ++r) {
+    for (int q = 0; q < 2 * bs; ++q) a[c][q] *= inv;
+    for (int r = 0; r < bs; ++r) {
       if (r == c) continue;
       double m = a[r][c];
       if (m == 0.0) continue;
-      for (int q = 0; q < 6; ++q) a[r][q] -= m * a[c][q];
+      for (int q = 0; q < 2 * bs; ++q) a[r][q] -= m * a[c][q];
     }
   }
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) {
-      X[3 * r + c] = a[r][c + 3];
-      if (!std::isfinite(X[3 * r + c])) return false;
+  for (int r = 0; r < bs; ++r)
+    for (int c = 0; c < bs; ++c) {
+      X[bs * r + c] = a[r][c + bs];
+      if (!std::isfinite(X[bs * r + c])) return false;
     }
   return true;
 }
 
-// C = A * B (3x3).
-inline void mul3(const double* A, const double* B, double* C) {
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) {
+// C = A * B (bs x bs).
+inline void mul_bs(int bs, const double* A, const double* B, double* C) {
+  for (int r = 0; r < bs; ++r)
+    for (int c = 0; c < bs; ++c) {
       double s = 0.0;
-      for (int k = 0; k < 3; ++k) s += A[3 * r + k] * B[3 * k + c];
-      C[3 * r + c] = s;
+      for (int k = 0; k < bs; ++k) s += A[bs * r + k] * B[bs * k + c];
+      C[bs * r + c] = s;
     }
 }
 
@@ -133,6 +134,11 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   }
   if (labels && nlabels <= 0 && N64 > 0) {
     *why = "nparts must be positive";
+    return ILU0DD_ERR_INVALID;
+  }
+  const int bs = A->block_dim == 0 ? 3 : A->block_dim;
+  if (bs != 1 && bs != 3) {
+    *why = "block_dim must be 1 (scalar CSR) or 3 (3x3 blocks)";
     return ILU0DD_ERR_INVALID;
   }
   if (!A->row_ptr || !A->col_idx || (A->nnzb > 0 && !A->val)) {
@@ -185,6 +191,8 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   }
   Plan& p = *P;
   p = Plan();
+  p.bs = bs;
+  p.rows_per_warp = bs == 3 ? kRowsPerWarp : 32;
   // per-phase wall times (opts.trace)
   double tprev = wall_seconds();
   std::string tlog;
@@ -376,7 +384,7 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   }
   // warps of ten rows each
   p.threads = o->threads_per_cta > 0 ? o->threads_per_cta
-                                      : std::min(kMaxApplyThreads, 32 * ceil_div(widest, kRowsPerWarp));
+                                      : std::min(kMaxApplyThreads, 32 * ceil_div(widest, p.rows_per_warp));
   if (p.threads % 32 || p.threads > kMaxApplyThreads || p.threads < 32) {
     *why = "threads_per_cta must be a multiple of 32 in [32, 384]";
     return ILU0DD_ERR_INVALID;
@@ -386,7 +394,7 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
     *why = "prefetch_bytes must be a multiple of 16 up to 16 MiB";
     return ILU0DD_ERR_INVALID;
   }
-  const int rows_cap = (p.threads / 32) * kRowsPerWarp;
+  const int rows_cap = (p.threads / 32) * p.rows_per_warp;
   const int64_t cap = 1ll << 30;  // record bytes (offsets are 32-bit)
 
   // ---- pieces: per subdomain, L levels 1.. then U levels 0.., rows of a level
@@ -441,14 +449,14 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
           int64_t nb = 0;
           while (b < key.size() && (int)(b - a) < rows_cap) {
             int w = -key[a].first;
-            int64_t bytes = record_bytes((int)(b - a + 1), w, nb - key[b].first, kind, p.factor_elem, nullptr);
+            int64_t bytes = record_bytes((int)(b - a + 1), w, nb - key[b].first, kind, p.factor_elem, bs, nullptr);
             if (bytes > cap && b > a) break;
             nb += -key[b].first;
             ++b;
           }
           int n = (int)(b - a), w = -key[a].first;
           int64_t voff;
-          int64_t bytes = record_bytes(n, w, nb, kind, p.factor_elem, &voff);
+          int64_t bytes = record_bytes(n, w, nb, kind, p.factor_elem, bs, &voff);
           if (bytes > cap || w > 255) sub_fail[s] = 1;
           for (size_t t = a; t < b; ++t) out.push_back(key[t].second - r0);
           PieceDesc d{};
@@ -513,9 +521,9 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   });
   p.stream_bytes = soff;
   p.n_pieces = (int64_t)p.pieces.size();
-  p.smem_bytes = (size_t)align_up(3ll * p.rmax * p.vec_elem, 128) + sizeof(PieceDesc) * kDescCache;
+  p.smem_bytes = (size_t)align_up((int64_t)bs * p.rmax * p.vec_elem, 128) + sizeof(PieceDesc) * kDescCache;
   if ((int64_t)p.smem_bytes > (int64_t)max_smem - kApplyStaticSmem) {
-    *why = "subdomain vector (" + std::to_string(3ll * p.rmax * p.vec_elem) + " B) exceeds the " +
+    *why = "subdomain vector (" + std::to_string((int64_t)bs * p.rmax * p.vec_elem) + " B) exceeds the " +
            std::to_string(max_smem) +
            " B of shared memory per block";
     return ILU0DD_ERR_SMEM;
@@ -552,10 +560,10 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   L.pieces = take(sizeof(PieceDesc) * (size_t)std::max<int64_t>(1, p.n_pieces));
   L.sell_off = take(sizeof(int32_t) * (size_t)(p.nslices + 1));
   L.sell_col = take(sizeof(int32_t) * (size_t)p.sell_slots * kSlice);
-  L.sell_val = take(sizeof(double) * 9 * (size_t)p.sell_slots * kSlice);
+  L.sell_val = take(sizeof(double) * bs * bs * (size_t)p.sell_slots * kSlice);
   L.perm = take(sizeof(int32_t) * (size_t)N);
   L.iperm = take(sizeof(int32_t) * (size_t)N);
-  for (int v = 0; v < kNumVec; ++v) L.vec[v] = take(sizeof(double) * 3 * (size_t)N);
+  for (int v = 0; v < kNumVec; ++v) L.vec[v] = take(sizeof(double) * bs * (size_t)N);
   L.partials = take(sizeof(double) * 5 * (size_t)p.ntiles_pow2);
   L.counters = take(sizeof(uint32_t) * 16);
   L.scal = take(sizeof(SolverScalars));
@@ -566,8 +574,9 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
 
   // ---- algorithmic bytes (values + int32 column indices + row pointers of L
   // and U + FP64 r in and z out; SpMV: values + columns + row pointers + x, y)
-  p.apply_bytes = 9ll * p.factor_elem * (p.nL + p.nU + N) + 4 * (p.nL + p.nU) + 8ll * (N + 1) + 48ll * N;
-  p.spmv_bytes = 76ll * p.nnzb + 4ll * (N + 1) + 48ll * N;
+  const int64_t bb = (int64_t)bs * bs;
+  p.apply_bytes = bb * p.factor_elem * (p.nL + p.nU + N) + 4 * (p.nL + p.nU) + 8ll * (N + 1) + 16ll * bs * N;
+  p.spmv_bytes = (8 * bb + 4) * p.nnzb + 4ll * (N + 1) + 16ll * bs * N;
   tmark("sell+layout");
   if (o->trace) std::fprintf(stderr, "[ilu0dd] plan:%s\n", tlog.c_str());
   return ILU0DD_OK;
@@ -681,16 +690,17 @@ int factor_ildu0(const Plan& p, const double* aval, std::vector<double>* Fp, std
   std::vector<double>& F = *Fp;
   std::vector<double>& invD = *invDp;
   const int64_t kept = p.dd_rp[p.N];
-  F.assign(9 * (size_t)kept, 0.0);
-  invD.assign(9 * (size_t)p.N, 0.0);
+  const int bs = p.bs, bb = bs * bs;
+  F.assign(bb * (size_t)kept, 0.0);
+  invD.assign(bb * (size_t)p.N, 0.0);
   std::vector<int32_t> fail(p.nsub, -1);
   parallel_for(p.nsub, [&](int64_t s) {
     const int32_t r0 = p.part_ptr[s], r1 = p.part_ptr[s + 1];
     const int64_t q0 = p.dd_rp[r0], q1 = p.dd_rp[r1];
     // W: working rows of the subdomain (Algorithm 7, U <- A)
-    std::vector<double> W(9 * (size_t)(q1 - q0));
+    std::vector<double> W(bb * (size_t)(q1 - q0));
     for (int64_t q = q0; q < q1; ++q)
-      std::memcpy(&W[9 * (q - q0)], aval + 9 * p.ap_src[p.dd_ap[q]], 9 * sizeof(double));
+      std::memcpy(&W[bb * (q - q0)], aval + bb * p.ap_src[p.dd_ap[q]], bb * sizeof(double));
     std::vector<int64_t> pos(r1 - r0, -1);
     std::vector<int64_t> diag(r1 - r0, -1);
     double Lij[9], prod[9];
@@ -703,27 +713,27 @@ int factor_ildu0(const Plan& p, const double* aval, std::vector<double>* Fp, std
       for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1] && p.dd_col[q] < i; ++q) {
         int32_t j = p.dd_col[q];
         // L_ij = W_ij U_jj^-1 (U_jj^-1 is invD of row j, already final)
-        mul3(&W[9 * (q - q0)], &invD[9 * (size_t)j], Lij);
-        std::memcpy(&W[9 * (q - q0)], Lij, sizeof Lij);
+        mul_bs(bs, &W[bb * (q - q0)], &invD[bb * (size_t)j], Lij);
+        std::memcpy(&W[bb * (q - q0)], Lij, bb * sizeof(double));
         for (int64_t t = p.dd_rp[j + 1] - 1; t >= p.dd_rp[j] && p.dd_col[t] > j; --t) {
           int64_t at = pos[p.dd_col[t] - r0];
           if (at < 0) continue;
-          mul3(Lij, &W[9 * (t - q0)], prod);
-          for (int e = 0; e < 9; ++e) W[9 * at + e] -= prod[e];
+          mul_bs(bs, Lij, &W[bb * (t - q0)], prod);
+          for (int e = 0; e < bb; ++e) W[bb * at + e] -= prod[e];
         }
       }
-      if (!inverse3(&W[9 * diag[i - r0]], &invD[9 * (size_t)i])) { fail[s] = i; return; }
+      if (!inverse_bs(bs, &W[bb * diag[i - r0]], &invD[bb * (size_t)i])) { fail[s] = i; return; }
       for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1]; ++q) pos[p.dd_col[q] - r0] = -1;
     }
     // ILDU0 (Algorithm 7, lower half, read as scaling the strictly-upper blocks):
     // F <- L at lower positions, U~_ik = D_i^-1 U_ik at upper positions.
     for (int32_t i = r0; i < r1; ++i)
       for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1]; ++q) {
-        double* dst = &F[9 * (size_t)q];
+        double* dst = &F[bb * (size_t)q];
         if (p.dd_col[q] < i) {
-          std::memcpy(dst, &W[9 * (q - q0)], 9 * sizeof(double));
+          std::memcpy(dst, &W[bb * (q - q0)], bb * sizeof(double));
         } else if (p.dd_col[q] > i) {
-          mul3(&invD[9 * (size_t)i], &W[9 * (q - q0)], dst);
+          mul_bs(bs, &invD[bb * (size_t)i], &W[bb * (q - q0)], dst);
         }
       }
   });
@@ -739,13 +749,14 @@ void ildu0_from_w(const Plan& p, const std::vector<double>& W, const std::vector
                   std::vector<double>* Fp) {
   std::vector<double>& F = *Fp;
   F.assign(W.size(), 0.0);
+  const int bs = p.bs, bb = bs * bs;
   parallel_for(p.N, [&](int64_t i) {
     for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1]; ++q) {
-      double* dst = &F[9 * (size_t)q];
+      double* dst = &F[bb * (size_t)q];
       if (p.dd_col[q] < i) {
-        std::memcpy(dst, &W[9 * (size_t)q], 9 * sizeof(double));
+        std::memcpy(dst, &W[bb * (size_t)q], bb * sizeof(double));
       } else if (p.dd_col[q] > i) {
-        mul3(&invD[9 * (size_t)i], &W[9 * (size_t)q], dst);
+        mul_bs(bs, &invD[bb * (size_t)i], &W[bb * (size_t)q], dst);
       }
     }
   });
@@ -767,7 +778,7 @@ void pack_stream(const Plan& p, const std::vector<double>& F, const std::vector<
                  std::vector<uint8_t>* out) {
   std::vector<uint8_t>& S = *out;
   S.assign((size_t)p.stream_bytes, 0);
-  const int fe = p.factor_elem, fp = p.factor_prec;
+  const int fe = p.factor_elem, fp = p.factor_prec, bs = p.bs, bb = bs * bs;
   parallel_for(p.nsub, [&](int64_t s) {
     const CtaDesc& c = p.cta[s];
     for (int32_t k = 0; k < c.npieces; ++k) {
@@ -792,30 +803,32 @@ void pack_stream(const Plan& p, const std::vector<double>& F, const std::vector<
       for (int slot = 0; slot < w; ++slot)
         for (int t = 0; t < cnt[slot]; ++t) h[cpos++] = (uint16_t)(p.dd_col[blk[t][slot]] - c.row0);
       uint8_t* v = rec + d.voff;
-      // entry [a][c] of row t's block at (c * count + t) * 3 + a
+      // entry [a][c] of row t's block at (c * count + t) * bs + a
       if (kind) {
-        for (int cc = 0; cc < 3; ++cc)
+        for (int cc = 0; cc < bs; ++cc)
           for (int t = 0; t < n; ++t)
-            for (int a = 0; a < 3; ++a)
-              put_factor(v + (((int64_t)cc * n + t) * 3 + a) * fe, fp,
-                         invD[9 * (size_t)(c.row0 + rows[t]) + 3 * a + cc]);
-        v += 9ll * n * fe;
+            for (int a = 0; a < bs; ++a)
+              put_factor(v + (((int64_t)cc * n + t) * bs + a) * fe, fp,
+                         invD[bb * (size_t)(c.row0 + rows[t]) + bs * a + cc]);
+        v += (int64_t)bb * n * fe;
       }
       for (int slot = 0; slot < w; ++slot) {
         const int cs = cnt[slot];
-        for (int cc = 0; cc < 3; ++cc)
+        for (int cc = 0; cc < bs; ++cc)
           for (int t = 0; t < cs; ++t)
-            for (int a = 0; a < 3; ++a)
-              put_factor(v + (((int64_t)cc * cs + t) * 3 + a) * fe, fp, F[9 * (size_t)blk[t][slot] + 3 * a + cc]);
-        v += 9ll * cs * fe;
+            for (int a = 0; a < bs; ++a)
+              put_factor(v + (((int64_t)cc * cs + t) * bs + a) * fe, fp,
+                         F[bb * (size_t)blk[t][slot] + bs * a + cc]);
+        v += (int64_t)bb * cs * fe;
       }
     }
   });
 }
 
 void pack_sell(const Plan& p, const double* aval, std::vector<int32_t>* cols, std::vector<double>* vals) {
+  const int bb = p.bs * p.bs;
   cols->assign((size_t)p.sell_slots * kSlice, 0);
-  vals->assign((size_t)p.sell_slots * kSlice * 9, 0.0);
+  vals->assign((size_t)p.sell_slots * kSlice * bb, 0.0);
   parallel_for(p.nslices, [&](int64_t k) {
     int64_t so = p.slice_off[k];
     int32_t w = p.slice_off[k + 1] - p.slice_off[k];
@@ -828,10 +841,10 @@ void pack_sell(const Plan& p, const double* aval, std::vector<int32_t>* cols, st
         if (r < p.N && s < p.ap_rp[r + 1] - p.ap_rp[r]) {
           int64_t q = p.ap_rp[r] + s;
           col = p.ap_col[q];
-          std::memcpy(blk, aval + 9 * p.ap_src[q], sizeof blk);
+          std::memcpy(blk, aval + bb * p.ap_src[q], bb * sizeof(double));
         }
         (*cols)[(size_t)slot * kSlice + lane] = col;
-        for (int e = 0; e < 9; ++e) (*vals)[((size_t)slot * 9 + e) * kSlice + lane] = blk[e];
+        for (int e = 0; e < bb; ++e) (*vals)[((size_t)slot * bb + e) * kSlice + lane] = blk[e];
       }
     }
   });

@@ -55,9 +55,10 @@ ScratchLayout scratch_layout(const Plan& p, int64_t total_levels, int64_t total_
     return at;
   };
   const size_t kept = (size_t)p.dd_rp[p.N];
-  L.aval = take(sizeof(double) * 9 * (size_t)p.nnzb);
-  L.w = take(sizeof(double) * 9 * kept);
-  L.invd = take(sizeof(double) * 9 * (size_t)p.N);
+  const size_t bb = (size_t)p.bs * p.bs;
+  L.aval = take(sizeof(double) * bb * (size_t)p.nnzb);
+  L.w = take(sizeof(double) * bb * kept);
+  L.invd = take(sizeof(double) * bb * (size_t)p.N);
   L.dd_src = take(sizeof(int64_t) * kept);
   L.dd_rp = take(sizeof(int32_t) * (size_t)(p.N + 1));
   L.dd_col = take(sizeof(int32_t) * kept);
@@ -90,51 +91,51 @@ int64_t total_prows_of(const Plan& p) { return (int64_t)p.piece_rows.size(); }
 // ---------------------------------------------------------------- kernels
 
 __global__ void gather_w_kernel(const double* __restrict__ aval, const int64_t* __restrict__ dd_src, int64_t kept,
-                                double* __restrict__ W) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 9 * kept; e += (int64_t)gridDim.x * blockDim.x)
-    W[e] = aval[9 * dd_src[e / 9] + e % 9];
+                                int bb, double* __restrict__ W) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < bb * kept; e += (int64_t)gridDim.x * blockDim.x)
+    W[e] = aval[bb * dd_src[e / bb] + e % bb];
 }
 
-// C = A * B (3x3), the host's summation order: s = 0; s += A_rk B_kc, k = 0..2.
-__device__ __forceinline__ void dmul3(const double* A, const double* B, double* C) {
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) {
+// C = A * B (bs x bs), the host's summation order: s = 0; s += A_rk B_kc, k = 0..bs-1.
+__device__ __forceinline__ void dmul_bs(int bs, const double* A, const double* B, double* C) {
+  for (int r = 0; r < bs; ++r)
+    for (int c = 0; c < bs; ++c) {
       double s = 0.0;
-      for (int k = 0; k < 3; ++k) s += A[3 * r + k] * B[3 * k + c];
-      C[3 * r + c] = s;
+      for (int k = 0; k < bs; ++k) s += A[bs * r + k] * B[bs * k + c];
+      C[bs * r + c] = s;
     }
 }
 
-// 3x3 inverse by Gauss-Jordan elimination with partial pivoting (the host's steps).
-__device__ bool dinverse3(const double* M, double* X) {
+// bs x bs inverse (bs <= 3) by Gauss-Jordan elimination with partial pivoting (the host's steps).
+__device__ bool dinverse_bs(int bs, const double* M, double* X) {
   double a[3][6];
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 6; ++c) a[r][c] = c < 3 ? M[3 * r + c] : (c - 3 == r ? 1.0 : 0.0);
-  for (int c = 0; c < 3; ++c) {
+  for (int r = 0; r < bs; ++r)
+    for (int c = 0; c < 2 * bs; ++c) a[r][c] = c < bs ? M[bs * r + c] : (c - bs == r ? 1.0 : 0.0);
+  for (int c = 0; c < bs; ++c) {
     int piv = c;
-    for (int r = c + 1; r < 3; ++r)
+    for (int r = c + 1; r < bs; ++r)
       if (fabs(a[r][c]) > fabs(a[piv][c])) piv = r;
     double pv = a[piv][c];
     if (!(fabs(pv) > 0.0) || !isfinite(pv)) return false;
     if (piv != c)
-      for (int q = 0; q < 6; ++q) {
+      for (int q = 0; q < 2 * bs; ++q) {
         double tmp = a[c][q];
         a[c][q] = a[piv][q];
         a[piv][q] = tmp;
       }
     double inv = 1.0 / a[c][c];
-    for (int q = 0; q < 6; ++q) a[c][q] *= inv;
-    for (int r = 0; r < 3; ++r) {
+    for (int q = 0; q < 2 * bs; ++q) a[c][q] *= inv;
+    for (int r = 0; r < bs; ++r) {
       if (r == c) continue;
       double m = a[r][c];
       if (m == 0.0) continue;
-      for (int q = 0; q < 6; ++q) a[r][q] -= m * a[c][q];
+      for (int q = 0; q < 2 * bs; ++q) a[r][q] -= m * a[c][q];
     }
   }
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) {
-      X[3 * r + c] = a[r][c + 3];
-      if (!isfinite(X[3 * r + c])) return false;
+  for (int r = 0; r < bs; ++r)
+    for (int c = 0; c < bs; ++c) {
+      X[bs * r + c] = a[r][c + bs];
+      if (!isfinite(X[bs * r + c])) return false;
     }
   return true;
 }
@@ -145,7 +146,8 @@ __device__ bool dinverse3(const double* M, double* X) {
 // finally D_i^-1 = U_ii^-1. W holds L below and U on and above the diagonal.
 __global__ void factor_kernel(const int32_t* __restrict__ dd_rp, const int32_t* __restrict__ dd_col,
                               const int32_t* __restrict__ order, const int32_t* __restrict__ lev_off,
-                              const int32_t* __restrict__ lptr, double* W, double* invD, int32_t* bad_row) {
+                              const int32_t* __restrict__ lptr, int bs, double* W, double* invD, int32_t* bad_row) {
+  const int bb = bs * bs;
   const int s = blockIdx.x;
   const int32_t l0 = lev_off[s], l1 = lev_off[s + 1];
   for (int32_t l = l0; l + 1 < l1; ++l) {
@@ -158,19 +160,19 @@ __global__ void factor_kernel(const int32_t* __restrict__ dd_rp, const int32_t* 
       double Lij[9], prod[9];
       for (int32_t q = q0; q < q1 && dd_col[q] < i; ++q) {
         const int32_t j = dd_col[q];
-        dmul3(&W[9 * (int64_t)q], &invD[9 * (int64_t)j], Lij);
-        for (int e = 0; e < 9; ++e) W[9 * (int64_t)q + e] = Lij[e];
+        dmul_bs(bs, &W[bb * (int64_t)q], &invD[bb * (int64_t)j], Lij);
+        for (int e = 0; e < bb; ++e) W[bb * (int64_t)q + e] = Lij[e];
         for (int32_t t = dd_rp[j + 1] - 1; t >= dd_rp[j] && dd_col[t] > j; --t) {
           const int32_t ct = dd_col[t];
           int32_t at = -1;
           for (int32_t u = q0; u < q1; ++u)
             if (dd_col[u] == ct) at = u;
           if (at < 0) continue;
-          dmul3(Lij, &W[9 * (int64_t)t], prod);
-          for (int e = 0; e < 9; ++e) W[9 * (int64_t)at + e] -= prod[e];
+          dmul_bs(bs, Lij, &W[bb * (int64_t)t], prod);
+          for (int e = 0; e < bb; ++e) W[bb * (int64_t)at + e] -= prod[e];
         }
       }
-      if (diag < 0 || !dinverse3(&W[9 * (int64_t)diag], &invD[9 * (int64_t)i])) atomicMin(bad_row, i);
+      if (diag < 0 || !dinverse_bs(bs, &W[bb * (int64_t)diag], &invD[bb * (int64_t)i])) atomicMin(bad_row, i);
     }
     __syncthreads();
   }
@@ -202,15 +204,17 @@ __device__ __forceinline__ void dev_put(unsigned char* dst, int prec, double v, 
   }
 }
 
-// One thread block per piece, one thread per row of the piece: the record
+// One thread block per piece, its threads over the piece's rows: the record
 // head (slot counts, local rows, local columns slot-major) and the values
-// interleaved by component, entry [a][c] of row t's block at (c * count + t) * 3 + a.
+// interleaved by component, entry [a][c] of row t's block at
+// (c * count + t) * bs + a.
 __global__ void pack_stream_kernel(const CtaDesc* __restrict__ cta, const PieceDesc* __restrict__ pieces,
                                    const int32_t* __restrict__ piece_sub, const int32_t* __restrict__ prow_off,
                                    const int32_t* __restrict__ prows, const int32_t* __restrict__ dd_rp,
                                    const int32_t* __restrict__ dd_col, const double* __restrict__ W,
-                                   const double* __restrict__ invD, int fe, int prec, unsigned char* stream,
-                                   int32_t* range_bad) {
+                                   const double* __restrict__ invD, int fe, int prec, int bs,
+                                   unsigned char* stream, int32_t* range_bad) {
+  const int bb = bs * bs;
   __shared__ int32_t cnt[256];
   const int32_t p = blockIdx.x;
   const PieceDesc pd = pieces[p];
@@ -218,36 +222,42 @@ __global__ void pack_stream_kernel(const CtaDesc* __restrict__ cta, const PieceD
   const int n = (int)(pd.meta & 0xFFFFu), w = (int)((pd.meta >> 16) & 0xFFu), kind = (int)(pd.meta >> 24);
   for (int sl = threadIdx.x; sl < 256; sl += blockDim.x) cnt[sl] = 0;
   __syncthreads();
-  const int t = threadIdx.x;
-  int32_t i = 0, qa = 0, nblk = 0;
-  if (t < n) {
-    i = cd.row0 + prows[prow_off[p] + t];
-    const int32_t q0 = dd_rp[i], q1 = dd_rp[i + 1];
-    if (kind) {  // strictly-upper blocks: after the diagonal
-      int32_t q = q0;
-      while (q < q1 && dd_col[q] <= i) ++q;
-      qa = q;
-      nblk = q1 - q;
-    } else {  // strictly-lower blocks: the first ones of the row
-      int32_t q = q0;
-      while (q < q1 && dd_col[q] < i) ++q;
-      qa = q0;
-      nblk = q - q0;
+  // the blocks of row t of the piece: strictly lower ones (first in the row)
+  // or strictly upper ones (after the diagonal)
+  auto row_blocks = [&](int t, int32_t* i, int32_t* qa, int32_t* nblk) {
+    *i = cd.row0 + prows[prow_off[p] + t];
+    const int32_t q0 = dd_rp[*i], q1 = dd_rp[*i + 1];
+    int32_t q = q0;
+    if (kind) {
+      while (q < q1 && dd_col[q] <= *i) ++q;
+      *qa = q;
+      *nblk = q1 - q;
+    } else {
+      while (q < q1 && dd_col[q] < *i) ++q;
+      *qa = q0;
+      *nblk = q - q0;
     }
+  };
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    int32_t i, qa, nblk;
+    row_blocks(t, &i, &qa, &nblk);
     for (int sl = 0; sl < nblk; ++sl) atomicAdd(&cnt[sl], 1);
   }
   __syncthreads();
   unsigned char* rec = stream + cd.stream_off + pd.off;
   uint16_t* h = reinterpret_cast<uint16_t*>(rec);
   for (int sl = threadIdx.x; sl < w; sl += blockDim.x) h[sl] = (uint16_t)cnt[sl];
-  if (t < n) {
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    int32_t i, qa, nblk;
+    row_blocks(t, &i, &qa, &nblk);
     h[w + t] = (uint16_t)(i - cd.row0);
     unsigned char* v = rec + pd.voff;
     if (kind) {
-      const double* di = &invD[9 * (int64_t)i];
-      for (int cc = 0; cc < 3; ++cc)
-        for (int a = 0; a < 3; ++a) dev_put(v + (((int64_t)cc * n + t) * 3 + a) * fe, prec, di[3 * a + cc], range_bad);
-      v += 9ll * n * fe;
+      const double* di = &invD[bb * (int64_t)i];
+      for (int cc = 0; cc < bs; ++cc)
+        for (int a = 0; a < bs; ++a)
+          dev_put(v + (((int64_t)cc * n + t) * bs + a) * fe, prec, di[bs * a + cc], range_bad);
+      v += (int64_t)bb * n * fe;
     }
     int64_t c0 = 0;
     for (int sl = 0; sl < nblk; ++sl) {
@@ -256,13 +266,14 @@ __global__ void pack_stream_kernel(const CtaDesc* __restrict__ cta, const PieceD
       h[w + n + c0 + t] = (uint16_t)(dd_col[q] - cd.row0);
       double F[9];
       if (kind) {
-        dmul3(&invD[9 * (int64_t)i], &W[9 * (int64_t)q], F);  // U~_iq = D_i^-1 U_iq
+        dmul_bs(bs, &invD[bb * (int64_t)i], &W[bb * (int64_t)q], F);  // U~_iq = D_i^-1 U_iq
       } else {
-        for (int e = 0; e < 9; ++e) F[e] = W[9 * (int64_t)q + e];
+        for (int e = 0; e < bb; ++e) F[e] = W[bb * (int64_t)q + e];
       }
-      unsigned char* vs = v + 9 * c0 * fe;
-      for (int cc = 0; cc < 3; ++cc)
-        for (int a = 0; a < 3; ++a) dev_put(vs + (((int64_t)cc * cs + t) * 3 + a) * fe, prec, F[3 * a + cc], range_bad);
+      unsigned char* vs = v + bb * c0 * fe;
+      for (int cc = 0; cc < bs; ++cc)
+        for (int a = 0; a < bs; ++a)
+          dev_put(vs + (((int64_t)cc * cs + t) * bs + a) * fe, prec, F[bs * a + cc], range_bad);
       c0 += cs;
     }
   }
@@ -273,7 +284,7 @@ __global__ void pack_stream_kernel(const CtaDesc* __restrict__ cta, const PieceD
 // own column (column 0 past the last row).
 __global__ void pack_sell_kernel(const int32_t* __restrict__ slice_off, int64_t nslices, int32_t N,
                                  const int32_t* __restrict__ ap_rp, const int32_t* __restrict__ ap_col,
-                                 const int64_t* __restrict__ ap_src, const double* __restrict__ aval,
+                                 const int64_t* __restrict__ ap_src, const double* __restrict__ aval, int bb,
                                  int32_t* __restrict__ cols, double* __restrict__ vals) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t k = g / kSlice;
@@ -290,10 +301,10 @@ __global__ void pack_sell_kernel(const int32_t* __restrict__ slice_off, int64_t 
     if (s < len) {
       const int64_t q = ap_rp[r] + s;
       col = ap_col[q];
-      src = aval + 9 * ap_src[q];
+      src = aval + bb * ap_src[q];
     }
     cols[slot * kSlice + lane] = col;
-    for (int e = 0; e < 9; ++e) vals[(slot * 9 + e) * kSlice + lane] = src ? src[e] : 0.0;
+    for (int e = 0; e < bb; ++e) vals[(slot * bb + e) * kSlice + lane] = src ? src[e] : 0.0;
   }
 }
 
@@ -349,7 +360,8 @@ int setup_on_device(const Plan& p, const double* aval_host, unsigned char* scrat
   auto up = [&](size_t off, const void* src, size_t bytes) {
     if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(scratch + off, src, bytes, cudaMemcpyHostToDevice, s);
   };
-  up(L.aval, aval_host, sizeof(double) * 9 * (size_t)p.nnzb);
+  const int bs = p.bs, bb = bs * bs;
+  up(L.aval, aval_host, sizeof(double) * bb * (size_t)p.nnzb);
   up(L.dd_src, dd_src.data(), sizeof(int64_t) * dd_src.size());
   up(L.dd_rp, p.dd_rp.data(), sizeof(int32_t) * p.dd_rp.size());
   up(L.dd_col, p.dd_col.data(), sizeof(int32_t) * p.dd_col.size());
@@ -390,15 +402,15 @@ int setup_on_device(const Plan& p, const double* aval_host, unsigned char* scrat
   if (p.nslices > 0)
     pack_sell_kernel<<<(unsigned)((p.nslices * kSlice + 255) / 256), 256, 0, s>>>(
         reinterpret_cast<const int32_t*>(ws + p.lay.sell_off), p.nslices, p.N, I32(L.ap_rp), I32(L.ap_col),
-        reinterpret_cast<const int64_t*>(scratch + L.ap_src), aval, reinterpret_cast<int32_t*>(ws + p.lay.sell_col),
+        reinterpret_cast<const int64_t*>(scratch + L.ap_src), aval, bb, reinterpret_cast<int32_t*>(ws + p.lay.sell_col),
         reinterpret_cast<double*>(ws + p.lay.sell_val));
   // ---- factors
   if (kept > 0)
-    gather_w_kernel<<<(unsigned)std::min<int64_t>((9 * kept + 255) / 256, 152 * 64), 256, 0, s>>>(
-        aval, reinterpret_cast<const int64_t*>(scratch + L.dd_src), kept, W);
+    gather_w_kernel<<<(unsigned)std::min<int64_t>((bb * kept + 255) / 256, 152 * 64), 256, 0, s>>>(
+        aval, reinterpret_cast<const int64_t*>(scratch + L.dd_src), kept, bb, W);
   if (p.nsub > 0)
-    factor_kernel<<<p.nsub, 128, 0, s>>>(I32(L.dd_rp), I32(L.dd_col), I32(L.order), I32(L.lev_off), I32(L.lptr), W,
-                                         invD, flags);
+    factor_kernel<<<p.nsub, 128, 0, s>>>(I32(L.dd_rp), I32(L.dd_col), I32(L.order), I32(L.lev_off), I32(L.lptr), bs,
+                                         W, invD, flags);
   e = cudaGetLastError();
   int32_t hflags[4] = {0, 0, 0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(hflags, flags, sizeof hflags, cudaMemcpyDeviceToHost, s);
@@ -416,7 +428,7 @@ int setup_on_device(const Plan& p, const double* aval_host, unsigned char* scrat
     pack_stream_kernel<<<(unsigned)p.n_pieces, 128, 0, s>>>(
         reinterpret_cast<const CtaDesc*>(ws + p.lay.cta), reinterpret_cast<const PieceDesc*>(ws + p.lay.pieces),
         I32(L.piece_sub), I32(L.prow_off), I32(L.prows), I32(L.dd_rp), I32(L.dd_col), W, invD, p.factor_elem,
-        p.factor_prec, ws + p.lay.stream, flags + 1);
+        p.factor_prec, bs, ws + p.lay.stream, flags + 1);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(hflags, flags, sizeof hflags, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
