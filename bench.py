@@ -19,7 +19,7 @@ timed region. The JSON line also reports the whole-iteration throughput, the
 per-kernel breakdown, BiCGSTAB time to relative residual 1e-8 with FP64, FP32
 and BF16 factors, the FP64-pipe roof of the apply, the 64^3 subdomain-size and
 factor-precision sweeps, the cuSPARSE global-ILU0 context on the same system,
-an unstructured system on the graph-partition path,
+an unstructured system on the graph-partition path, a scalar CSR system,
 the batched solve of 64 ragged systems, the CPU oracle's throughput and the
 clocks seen.
 
@@ -281,11 +281,12 @@ def run_ours(args):
     del ctx
 
     # ---- context: the cuSPARSE global ILU0 on the same system; the 64^3 sweeps
-    vendor = sweep = unstructured = None
+    vendor = sweep = unstructured = scalar = None
     if not args.no_context and rank == 0:
         vendor = run_vendor(s, w, dev, plain_ms)
         sweep = run_sweep(dev)
         unstructured = run_unstructured(dev)
+        scalar = run_scalar(dev)
 
     # ---- BiCGSTAB time to relative residual 1e-8: FP64 vs FP32 / BF16 factors
     solves = {}
@@ -372,6 +373,7 @@ def run_ours(args):
         "sweep_64cubed": sweep,
         "vendor_context": vendor,
         "unstructured": unstructured,
+        "scalar_csr": scalar,
         "batched": batched,
         "setup_s": round(setup_s, 3),
         "cpu_baseline": cpu,
@@ -608,6 +610,38 @@ def run_unstructured(dev, cells=(128, 128, 128), part_rows=2048, reps=20):
                 "solve_s": round(sec, 5), "status": info["status"],
                 "max_rel_err_vs_xstar": float((x - xs).abs().max() / xs.abs().max())}
             ctx.close()
+    return out
+
+
+def run_scalar(dev, grid=(200, 200, 200), sub=(32, 16, 16), reps=20):
+    """Scalar CSR systems (the paper's CSR inputs): the layered model's scalar
+    form (one unknown per cell, 8M rows) cut into 32x16x16-cell subdomains of
+    8,192 rows (the paper's part size for its CSR matrices); FP64 and FP32
+    factors: setup, apply GB/s, BiCGSTAB iterations and time to 1e-8."""
+    import torch
+
+    import paper_2508_04917_gb300 as pkg
+    import synth
+    s = synth.system(*grid, 7, model=synth.MODEL_LAYERED, bs=1)
+    b = torch.from_numpy(s.b).to(dev)
+    r = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, s.n)).to(dev)
+    z = torch.empty_like(r)
+    out = {"rows": s.n, "nnz": s.nnzb, "grid": list(grid), "subdomain": list(sub)}
+    for prec in ("f64", "f32"):
+        t0 = time.perf_counter()
+        ctx = pkg.Ilu0DD(s.row_ptr, s.col, s.val, grid, sub, factor_prec=prec)
+        torch.cuda.synchronize()
+        su = time.perf_counter() - t0
+        ams = time_apply_warm(ctx, r, z, reps)
+        sec, x, info = timed_solve(ctx, b)
+        xs = torch.from_numpy(s.xstar).to(dev)
+        out[prec] = {"setup_s": round(su, 3), "threads": ctx.query("threads"),
+                     "dropped_pct": round(100.0 * (1 - ctx.query("kept") / ctx.query("nnzb")), 2),
+                     "apply_ms": round(ams, 5), "apply_bytes": ctx.query("apply_bytes"),
+                     "apply_gbs": round(ctx.query("apply_bytes") / ams / 1e6, 1), "iterations": info["iterations"],
+                     "solve_s": round(sec, 5), "status": info["status"],
+                     "max_rel_err_vs_xstar": float((x - xs).abs().max() / xs.abs().max())}
+        ctx.close()
     return out
 
 
