@@ -3,9 +3,10 @@
  *
  * C ABI of the library built from paper_2508_04917_gb300/csrc. It implements
  * the hot path of arXiv 2508.04917, "Mapping Sparse Triangular Solves to GPUs
- * via Fine-grained Domain Decomposition": a 3x3-block (BSR) system A x = b
- * from a 3D 7-point stencil is cut into box subdomains (Algorithm 2),
- * reordered so every subdomain is a contiguous row range (Algorithm 3),
+ * via Fine-grained Domain Decomposition": a 3x3-block (BSR) or scalar (CSR)
+ * system A x = b is cut into subdomains (box subdomains of a grid, Algorithm
+ * 2, or the parts of a graph partition, Section 3.1), reordered so every
+ * subdomain is a contiguous row range (Algorithm 3),
  * stripped of inter-subdomain blocks (Section 3.2) and factored with ILU0 /
  * ILDU0 (Algorithm 7). The preconditioner z = M^-1 r, M = LU, is then applied
  * by one fused L -> D^-1 -> U kernel with one thread block per subdomain and
@@ -21,10 +22,15 @@
  *    stream.
  *  - The library never allocates device memory. The caller allocates one
  *    device workspace of ilu0_dd_workspace_size() bytes (256-byte aligned)
- *    and keeps it alive for the lifetime of the context. Small host-side
- *    bookkeeping (the context object, host copies for ilu0_dd_export) is
- *    allocated with malloc and released by ilu0_dd_destroy.
- *  - Vectors hold 3 doubles per block row (cell), entry 3*i + a.
+ *    and keeps it alive for the lifetime of the context (and, for the device
+ *    setup, a scratch buffer that is free again once setup returns). Small
+ *    host-side bookkeeping (the context object, host copies for
+ *    ilu0_dd_export) is allocated with malloc and released by
+ *    ilu0_dd_destroy. The exceptions are the static array of
+ *    ilu0dd_dot_noalloc and the streams ilu0_dd_apply_host creates.
+ *  - Vectors hold bs doubles per block row (bs = the matrix's block_dim: 3
+ *    or 1), entry bs*i + a; "3*N doubles" below reads bs*N for scalar
+ *    matrices.
  */
 #ifndef ILU0DD_H_
 #define ILU0DD_H_
@@ -39,7 +45,7 @@ extern "C" {
 /* ---- return codes ---------------------------------------------------- */
 #define ILU0DD_OK 0
 #define ILU0DD_ERR_INVALID 1        /* bad pointer, size, pattern (unsorted columns, missing diagonal) */
-#define ILU0DD_ERR_ZERO_PIVOT 2     /* singular or non-finite 3x3 pivot block in ILU0 */
+#define ILU0DD_ERR_ZERO_PIVOT 2     /* singular or non-finite pivot block (3x3 or 1x1) in ILU0 */
 #define ILU0DD_ERR_SMEM 3           /* a subdomain vector does not fit in shared memory */
 #define ILU0DD_ERR_CUDA 4           /* a CUDA call failed (see ilu0_dd_query ILU0DD_Q_CUDA_ERROR) */
 #define ILU0DD_ERR_BREAKDOWN 5      /* BiCGSTAB breakdown: (r^,v)=0, rho=0, omega=0 or non-finite */

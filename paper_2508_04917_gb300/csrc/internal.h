@@ -24,22 +24,24 @@ namespace ilu0dd {
 //
 // Inside a record the rows are sorted by block count, longest first, and the
 // blocks are stored slot-major ("jagged diagonal" order): slot s holds the
-// s-th block (ascending column) of the first cnt[s] rows. Three threads work
-// on each row, one per output component a, so values are interleaved by
-// component: within slot s, entry B[a][c] of the block of row t sits at
-// (c * cnt[s] + t) * 3 + a, and consecutive threads read consecutive values.
+// s-th block (ascending column) of the first cnt[s] rows. With bs x bs
+// blocks, bs threads work on each row, one per output component a, so values
+// are interleaved by component: within slot s, entry B[a][c] of the block of
+// row t sits at (c * cnt[s] + t) * bs + a, and consecutive threads read
+// consecutive values.
 //
 //   u16 cnt[w]                 rows having more than s blocks, s = 0..w-1
 //   u16 rows[n]                local row index (0 .. nrows-1 of the subdomain)
 //   u16 cols[nb]               slot-major local column of each block
 //   pad to 16
-//   T   invD[3 * n * 3]        (kind 1 only) D^-1 = U_ii^-1, entry [a][c] at (c * n + t) * 3 + a
-//   T   vals[...]              per slot s: 9 * cnt[s] values as above
+//   T   invD[bs * n * bs]      (kind 1 only) D^-1 = U_ii^-1, entry [a][c] at (c * n + t) * bs + a
+//   T   vals[...]              per slot s: bs * bs * cnt[s] values as above
 //   pad to 16
-// T is the factor storage type (double, float or bf16). Each warp of a block
-// covers ten rows of a piece with lanes 0..29 (lane = 3 * row + a; lanes 30
-// and 31 idle), so the three threads of a row share a warp and exchange values
-// with shuffles.
+// T is the factor storage type (double, float, bf16 or a float pair). With
+// 3x3 blocks each warp of a block covers ten rows of a piece with lanes 0..29
+// (lane = 3 * row + a; lanes 30 and 31 idle), so the three threads of a row
+// share a warp and exchange values with shuffles; with scalar rows (bs = 1) a
+// warp covers 32 rows.
 // ---------------------------------------------------------------------------
 constexpr int kRowsPerWarp = 10;
 constexpr int kDescSlots = 3;   // slot counts carried in the descriptor

@@ -1,7 +1,8 @@
 // sm_103a kernels of the hot path:
 //  - apply_block: fused L -> D^-1 -> U~ sweep of one subdomain (Sections
 //    4.2-4.4) by one thread block, subdomain vector in shared memory,
-//    vertex-centric rows (Section 4.2.3) with three threads per row;
+//    vertex-centric rows (Section 4.2.3) with three threads per row (3x3
+//    blocks) or one (scalar CSR);
 //  - spmv_block: y = A_p x on a sliced-ELL copy (coalesced, entry-major),
 //    with the dot products of Algorithm 1 fused into the epilogue;
 //  - update / init / residual / dot / permute: the BiCGSTAB vector steps.
