@@ -312,8 +312,9 @@ int bicgstab_state(ilu0dd_ctx* ctx, ilu0dd_info* info, void* stream);
 /*
  * Batched BiCGSTAB over many independent systems (the batching pattern; the
  * paper has no batched solver). Each system is an ilu0dd_ctx from
- * ilu0_dd_setup (any grid and subdomain size, all with 3x3 blocks and the same factor_prec,
- * on the current device). ilu0dd_batch_create records them in a small device
+ * ilu0_dd_setup (any grid and subdomain size; all with the same block dimension,
+ * 3x3 or scalar, the same factor_prec and the current device; otherwise
+ * ilu0dd_batch_create returns ILU0DD_ERR_INVALID). It records them in a small device
  * workspace (ilu0dd_batch_workspace_size bytes, 256-byte aligned, caller-owned)
  * and keeps pointers to the contexts: they must outlive the batch, and a
  * context must not be solved alone while a batched solve that uses it runs.

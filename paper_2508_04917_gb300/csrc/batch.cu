@@ -26,7 +26,7 @@ struct ilu0dd_batch {
   SolverScalars* d_status = nullptr;
   int32_t* d_flags = nullptr;
   int64_t n_apply = 0, n_tile = 0;
-  int factor_prec = 0, threads = 0;
+  int factor_prec = 0, bs = 3, threads = 0;
   size_t smem = 0;
   int grid_apply = 1, grid_tile = 1;
   double rtol = 1e-8;
@@ -73,15 +73,17 @@ BatchLayout batch_layout(ilu0dd_ctx* const* ctxs, int32_t nsys, int64_t* n_apply
 
 cudaError_t batch_iteration(const ilu0dd_batch* b, cudaStream_t s) {
   cudaError_t e;
-  if ((e = launch_apply_batched(b->d_sys, b->d_apply_items, b->n_apply, kModeP, b->factor_prec, b->threads, b->smem,
-                                b->grid_apply, s)) != cudaSuccess)
+  if ((e = launch_apply_batched(b->d_sys, b->d_apply_items, b->n_apply, kModeP, b->factor_prec, b->bs, b->threads,
+                                b->smem, b->grid_apply, s)) != cudaSuccess)
     return e;
-  if ((e = launch_spmv_batched(b->d_sys, b->d_tile_items, b->n_tile, 1, b->grid_tile, s)) != cudaSuccess) return e;
-  if ((e = launch_apply_batched(b->d_sys, b->d_apply_items, b->n_apply, kModeS, b->factor_prec, b->threads, b->smem,
-                                b->grid_apply, s)) != cudaSuccess)
+  if ((e = launch_spmv_batched(b->d_sys, b->d_tile_items, b->n_tile, 1, b->bs, b->grid_tile, s)) != cudaSuccess)
     return e;
-  if ((e = launch_spmv_batched(b->d_sys, b->d_tile_items, b->n_tile, 2, b->grid_tile, s)) != cudaSuccess) return e;
-  return launch_update_batched(b->d_sys, b->d_tile_items, b->n_tile, b->grid_tile, s);
+  if ((e = launch_apply_batched(b->d_sys, b->d_apply_items, b->n_apply, kModeS, b->factor_prec, b->bs, b->threads,
+                                b->smem, b->grid_apply, s)) != cudaSuccess)
+    return e;
+  if ((e = launch_spmv_batched(b->d_sys, b->d_tile_items, b->n_tile, 2, b->bs, b->grid_tile, s)) != cudaSuccess)
+    return e;
+  return launch_update_batched(b->d_sys, b->d_tile_items, b->n_tile, b->bs, b->grid_tile, s);
 }
 
 cudaError_t batch_chunk(ilu0dd_batch* b) {
@@ -133,8 +135,8 @@ int ilu0dd_batch_create(ilu0dd_ctx* const* ctxs, int32_t nsys, const ilu0dd_opts
   *out = nullptr;
   for (int32_t i = 0; i < nsys; ++i)
     if (!ctxs[i] || ctxs[i]->dev.factor_prec != ctxs[0]->dev.factor_prec || ctxs[i]->device != ctxs[0]->device ||
-        ctxs[i]->dev.bs != 3)  // the batched kernels take 3x3 blocks
-      return ILU0DD_ERR_INVALID;  // one device, one factor precision per batch
+        ctxs[i]->dev.bs != ctxs[0]->dev.bs)
+      return ILU0DD_ERR_INVALID;  // one device, one factor precision, one block dimension per batch
   int64_t na = 0, nt = 0;
   const BatchLayout L = batch_layout(ctxs, nsys, &na, &nt);
   if (!d_workspace || ws_bytes < L.total || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
@@ -153,6 +155,7 @@ int ilu0dd_batch_create(ilu0dd_ctx* const* ctxs, int32_t nsys, const ilu0dd_opts
   b->n_apply = na;
   b->n_tile = nt;
   b->factor_prec = ctxs[0]->dev.factor_prec;
+  b->bs = ctxs[0]->dev.bs;
   ilu0dd_opts o;
   ilu0dd_default_opts(&o);
   if (opts) o = *opts;
@@ -201,8 +204,8 @@ int ilu0dd_batch_create(ilu0dd_ctx* const* ctxs, int32_t nsys, const ilu0dd_opts
     return ILU0DD_ERR_CUDA;
   }
   b->grid_apply = (int)std::min<int64_t>(std::max<int64_t>(1, na),
-                                         (int64_t)nsm * apply_blocks_per_sm(b->factor_prec, b->threads, b->smem));
-  b->grid_tile = (int)std::min<int64_t>(std::max<int64_t>(1, nt), (int64_t)nsm * tile_blocks_per_sm());
+                                         (int64_t)nsm * apply_blocks_per_sm(b->factor_prec, b->bs, b->threads, b->smem));
+  b->grid_tile = (int)std::min<int64_t>(std::max<int64_t>(1, nt), (int64_t)nsm * tile_blocks_per_sm(b->bs));
   b->h_status.resize(nsys);
   *out = b;
   return ILU0DD_OK;
@@ -225,9 +228,11 @@ int bicgstab_solve_batched(ilu0dd_batch* b, const double* const* d_b, double* co
   cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->d_ptrs, ptrs.data(), sizeof(double*) * ptrs.size(), cudaMemcpyHostToDevice, b->own);
-  if (e == cudaSuccess) e = launch_permute_batched(b->d_sys, b->d_tile_items, b->n_tile, b->d_ptrs, 0, b->grid_tile, b->own);
+  if (e == cudaSuccess) e = launch_permute_batched(b->d_sys, b->d_tile_items, b->n_tile, b->d_ptrs, 0, b->bs, b->grid_tile,
+                                                 b->own);
   if (e == cudaSuccess)
-    e = launch_vec_batched(b->d_sys, b->d_tile_items, b->n_tile, 0, b->rtol, b->maxit, nullptr, b->grid_tile, b->own);
+    e = launch_vec_batched(b->d_sys, b->d_tile_items, b->n_tile, 0, b->rtol, b->maxit, nullptr, b->bs, b->grid_tile,
+                           b->own);
   if (e == cudaSuccess) e = read_status(b);
   if (e != cudaSuccess) return fail(e);
   for (;;) {
@@ -240,9 +245,9 @@ int bicgstab_solve_batched(ilu0dd_batch* b, const double* const* d_b, double* co
       if ((e = batch_chunk(b)) != cudaSuccess || (e = read_status(b)) != cudaSuccess) return fail(e);
     }
     // true residual r = b - A x of every system
-    e = launch_spmv_batched(b->d_sys, b->d_tile_items, b->n_tile, 0, b->grid_tile, b->own);
+    e = launch_spmv_batched(b->d_sys, b->d_tile_items, b->n_tile, 0, b->bs, b->grid_tile, b->own);
     if (e == cudaSuccess)
-      e = launch_vec_batched(b->d_sys, b->d_tile_items, b->n_tile, 1, 0.0, 0, nullptr, b->grid_tile, b->own);
+      e = launch_vec_batched(b->d_sys, b->d_tile_items, b->n_tile, 1, 0.0, 0, nullptr, b->bs, b->grid_tile, b->own);
     if (e == cudaSuccess) e = read_status(b);
     if (e != cudaSuccess) return fail(e);
     // restart once the systems that converged on the recurrence only
@@ -258,11 +263,12 @@ int bicgstab_solve_batched(ilu0dd_batch* b, const double* const* d_b, double* co
     if (!any) break;
     e = cudaMemcpyAsync(b->d_flags, flags.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, b->own);
     if (e == cudaSuccess)
-      e = launch_vec_batched(b->d_sys, b->d_tile_items, b->n_tile, 2, 0.0, 0, b->d_flags, b->grid_tile, b->own);
+      e = launch_vec_batched(b->d_sys, b->d_tile_items, b->n_tile, 2, 0.0, 0, b->d_flags, b->bs, b->grid_tile,
+                             b->own);
     if (e == cudaSuccess) e = read_status(b);
     if (e != cudaSuccess) return fail(e);
   }
-  e = launch_permute_batched(b->d_sys, b->d_tile_items, b->n_tile, b->d_ptrs + n, 1, b->grid_tile, b->own);
+  e = launch_permute_batched(b->d_sys, b->d_tile_items, b->n_tile, b->d_ptrs + n, 1, b->bs, b->grid_tile, b->own);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->own);
   if (e != cudaSuccess) return fail(e);
   const double solve_s = wall_seconds() - t0;

@@ -288,13 +288,13 @@ __global__ void __launch_bounds__(kMaxApplyThreads, ApplyMinBlocks<TF>::value)
 }
 
 // Batched apply (modes P and S): persistent blocks walk (system, subdomain) items.
-template <typename TF, int MODE>
+template <typename TF, int MODE, int BS>
 __global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
     ildu0_apply_batched(const SysDesc* __restrict__ sys, const BatchItem* __restrict__ items, int64_t nitems) {
   for (int64_t i = blockIdx.x; i < nitems; i += gridDim.x) {
     const BatchItem it = items[i];
     const SysDesc& S = sys[it.sys];
-    apply_block<TF, MODE>(S, it.local, S.vec[kVecR], S.vec[MODE == kModeP ? kVecPh : kVecSh]);
+    apply_block<TF, MODE, 0, BS>(S, it.local, S.vec[kVecR], S.vec[MODE == kModeP ? kVecPh : kVecSh]);
     __syncthreads();  // the next item reuses shared memory
   }
 }
@@ -306,7 +306,9 @@ static cudaError_t configure_one(size_t smem) {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(ildu0_apply_kernel<TF, MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e == cudaSuccess && MODE != kModePlain)
-    e = cudaFuncSetAttribute(ildu0_apply_batched<TF, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    e = cudaFuncSetAttribute(ildu0_apply_batched<TF, MODE, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess && MODE != kModePlain)
+    e = cudaFuncSetAttribute(ildu0_apply_batched<TF, MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (MODE == kModePlain) {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(ildu0_apply_part_kernel<TF, 1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -402,39 +404,52 @@ cudaError_t launch_apply_unfused(const DevCtx& d, const double* r, double* z, cu
   return launch_unfused_t<bf16s>(d, r, z, s);
 }
 
-template <typename TF>
-static cudaError_t launch_apply_batched_t(const SysDesc* sys, const BatchItem* items, int64_t nitems, int mode,
-                                          int threads, size_t smem, int grid, cudaStream_t s) {
+template <typename TF, int BS>
+static cudaError_t launch_apply_batched_tb(const SysDesc* sys, const BatchItem* items, int64_t nitems, int mode,
+                                           int threads, size_t smem, int grid, cudaStream_t s) {
   if (mode == kModeP)
-    ildu0_apply_batched<TF, kModeP><<<grid, threads, smem, s>>>(sys, items, nitems);
+    ildu0_apply_batched<TF, kModeP, BS><<<grid, threads, smem, s>>>(sys, items, nitems);
   else
-    ildu0_apply_batched<TF, kModeS><<<grid, threads, smem, s>>>(sys, items, nitems);
+    ildu0_apply_batched<TF, kModeS, BS><<<grid, threads, smem, s>>>(sys, items, nitems);
   return cudaGetLastError();
 }
 
-cudaError_t launch_apply_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int mode,
-                                 int factor_prec, int threads, size_t smem, int grid, cudaStream_t s) {
-  if (nitems == 0) return cudaSuccess;
-  if (factor_prec == ILU0DD_F64)
-    return launch_apply_batched_t<double>(sys, items, nitems, mode, threads, smem, grid, s);
-  if (factor_prec == ILU0DD_F32)
-    return launch_apply_batched_t<float>(sys, items, nitems, mode, threads, smem, grid, s);
-  if (factor_prec == ILU0DD_DF64)
-    return launch_apply_batched_t<df64s>(sys, items, nitems, mode, threads, smem, grid, s);
-  return launch_apply_batched_t<bf16s>(sys, items, nitems, mode, threads, smem, grid, s);
+template <typename TF>
+static cudaError_t launch_apply_batched_t(const SysDesc* sys, const BatchItem* items, int64_t nitems, int mode,
+                                          int bs, int threads, size_t smem, int grid, cudaStream_t s) {
+  return bs == 1 ? launch_apply_batched_tb<TF, 1>(sys, items, nitems, mode, threads, smem, grid, s)
+                 : launch_apply_batched_tb<TF, 3>(sys, items, nitems, mode, threads, smem, grid, s);
 }
 
-int apply_blocks_per_sm(int factor_prec, int threads, size_t smem) {
+cudaError_t launch_apply_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int mode,
+                                 int factor_prec, int bs, int threads, size_t smem, int grid, cudaStream_t s) {
+  if (nitems == 0) return cudaSuccess;
+  if (factor_prec == ILU0DD_F64)
+    return launch_apply_batched_t<double>(sys, items, nitems, mode, bs, threads, smem, grid, s);
+  if (factor_prec == ILU0DD_F32)
+    return launch_apply_batched_t<float>(sys, items, nitems, mode, bs, threads, smem, grid, s);
+  if (factor_prec == ILU0DD_DF64)
+    return launch_apply_batched_t<df64s>(sys, items, nitems, mode, bs, threads, smem, grid, s);
+  return launch_apply_batched_t<bf16s>(sys, items, nitems, mode, bs, threads, smem, grid, s);
+}
+
+template <typename TF>
+static cudaError_t batched_occupancy(int* n, int bs, int threads, size_t smem) {
+  return bs == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, ildu0_apply_batched<TF, kModeP, 1>, threads, smem)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, ildu0_apply_batched<TF, kModeP, 3>, threads, smem);
+}
+
+int apply_blocks_per_sm(int factor_prec, int bs, int threads, size_t smem) {
   int n = 0;
   cudaError_t e;
   if (factor_prec == ILU0DD_F64)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ildu0_apply_batched<double, kModeP>, threads, smem);
+    e = batched_occupancy<double>(&n, bs, threads, smem);
   else if (factor_prec == ILU0DD_F32)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ildu0_apply_batched<float, kModeP>, threads, smem);
+    e = batched_occupancy<float>(&n, bs, threads, smem);
   else if (factor_prec == ILU0DD_DF64)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ildu0_apply_batched<df64s, kModeP>, threads, smem);
+    e = batched_occupancy<df64s>(&n, bs, threads, smem);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ildu0_apply_batched<bf16s, kModeP>, threads, smem);
+    e = batched_occupancy<bf16s>(&n, bs, threads, smem);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;
@@ -564,18 +579,18 @@ __global__ void __launch_bounds__(kDotTile) sell_spmv_kernel(SysDesc S, const do
   spmv_block<KIND, BS>(S, blockIdx.x, x, y);
 }
 
-template <int KIND>
+template <int KIND, int BS>
 __global__ void __launch_bounds__(kDotTile)
     sell_spmv_batched(const SysDesc* __restrict__ sys, const BatchItem* __restrict__ items, int64_t nitems) {
   for (int64_t i = blockIdx.x; i < nitems; i += gridDim.x) {
     const BatchItem it = items[i];
     const SysDesc& S = sys[it.sys];
     if (KIND == 0)
-      spmv_block<0>(S, it.local, S.vec[kVecX], S.vec[kVecT]);
+      spmv_block<0, BS>(S, it.local, S.vec[kVecX], S.vec[kVecT]);
     else if (KIND == 1)
-      spmv_block<1>(S, it.local, S.vec[kVecPh], S.vec[kVecV]);
+      spmv_block<1, BS>(S, it.local, S.vec[kVecPh], S.vec[kVecV]);
     else
-      spmv_block<2>(S, it.local, S.vec[kVecSh], S.vec[kVecT]);
+      spmv_block<2, BS>(S, it.local, S.vec[kVecSh], S.vec[kVecT]);
     __syncthreads();
   }
 }
@@ -597,16 +612,23 @@ cudaError_t launch_spmv(const DevCtx& d, int kind, const double* x, double* y, c
   return d.bs == 1 ? launch_spmv_b<1>(d, kind, x, y, s) : launch_spmv_b<3>(d, kind, x, y, s);
 }
 
-cudaError_t launch_spmv_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int kind, int grid,
-                                cudaStream_t s) {
-  if (nitems == 0) return cudaSuccess;
+template <int BS>
+static cudaError_t launch_spmv_batched_b(const SysDesc* sys, const BatchItem* items, int64_t nitems, int kind,
+                                         int grid, cudaStream_t s) {
   if (kind == 0)
-    sell_spmv_batched<0><<<grid, kDotTile, 0, s>>>(sys, items, nitems);
+    sell_spmv_batched<0, BS><<<grid, kDotTile, 0, s>>>(sys, items, nitems);
   else if (kind == 1)
-    sell_spmv_batched<1><<<grid, kDotTile, 0, s>>>(sys, items, nitems);
+    sell_spmv_batched<1, BS><<<grid, kDotTile, 0, s>>>(sys, items, nitems);
   else
-    sell_spmv_batched<2><<<grid, kDotTile, 0, s>>>(sys, items, nitems);
+    sell_spmv_batched<2, BS><<<grid, kDotTile, 0, s>>>(sys, items, nitems);
   return cudaGetLastError();
+}
+
+cudaError_t launch_spmv_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int kind, int bs,
+                                int grid, cudaStream_t s) {
+  if (nitems == 0) return cudaSuccess;
+  return bs == 1 ? launch_spmv_batched_b<1>(sys, items, nitems, kind, grid, s)
+                 : launch_spmv_batched_b<3>(sys, items, nitems, kind, grid, s);
 }
 
 // ===========================================================================
@@ -801,15 +823,17 @@ __global__ void __launch_bounds__(kDotTile) residual_kernel(SysDesc S, int resta
     residual_block<BS>(S, blockIdx.x);
 }
 
+template <int BS>
 __global__ void __launch_bounds__(kDotTile)
     update_batched(const SysDesc* __restrict__ sys, const BatchItem* __restrict__ items, int64_t nitems) {
   for (int64_t i = blockIdx.x; i < nitems; i += gridDim.x) {
     const BatchItem it = items[i];
-    update_block(sys[it.sys], it.local);
+    update_block<BS>(sys[it.sys], it.local);
     __syncthreads();
   }
 }
 
+template <int BS>
 __global__ void __launch_bounds__(kDotTile)
     vec_batched(const SysDesc* __restrict__ sys, const BatchItem* __restrict__ items, int64_t nitems, int mode,
                 double rtol, int32_t maxit, const int32_t* __restrict__ flags) {
@@ -818,11 +842,11 @@ __global__ void __launch_bounds__(kDotTile)
     if (flags && !flags[it.sys]) continue;  // uniform per item
     const SysDesc& S = sys[it.sys];
     if (mode == 0)
-      init_block(S, it.local, rtol, maxit);
+      init_block<BS>(S, it.local, rtol, maxit);
     else if (mode == 1)
-      residual_block(S, it.local);
+      residual_block<BS>(S, it.local);
     else
-      restart_block(S, it.local);
+      restart_block<BS>(S, it.local);
     __syncthreads();
   }
 }
@@ -854,23 +878,31 @@ cudaError_t launch_residual(const DevCtx& d, int restart, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_update_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int grid,
+cudaError_t launch_update_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int bs, int grid,
                                   cudaStream_t s) {
   if (nitems == 0) return cudaSuccess;
-  update_batched<<<grid, kDotTile, 0, s>>>(sys, items, nitems);
+  if (bs == 1)
+    update_batched<1><<<grid, kDotTile, 0, s>>>(sys, items, nitems);
+  else
+    update_batched<3><<<grid, kDotTile, 0, s>>>(sys, items, nitems);
   return cudaGetLastError();
 }
 
 cudaError_t launch_vec_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int mode, double rtol,
-                               int32_t maxit, const int32_t* flags, int grid, cudaStream_t s) {
+                               int32_t maxit, const int32_t* flags, int bs, int grid, cudaStream_t s) {
   if (nitems == 0) return cudaSuccess;
-  vec_batched<<<grid, kDotTile, 0, s>>>(sys, items, nitems, mode, rtol, maxit, flags);
+  if (bs == 1)
+    vec_batched<1><<<grid, kDotTile, 0, s>>>(sys, items, nitems, mode, rtol, maxit, flags);
+  else
+    vec_batched<3><<<grid, kDotTile, 0, s>>>(sys, items, nitems, mode, rtol, maxit, flags);
   return cudaGetLastError();
 }
 
-int tile_blocks_per_sm() {
+int tile_blocks_per_sm(int bs) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sell_spmv_batched<2>, kDotTile, 0) != cudaSuccess) {
+  cudaError_t e = bs == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sell_spmv_batched<2, 1>, kDotTile, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sell_spmv_batched<2, 3>, kDotTile, 0);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
@@ -941,6 +973,7 @@ cudaError_t launch_permute(const DevCtx& d, const double* in, double* out, int d
 }
 
 // Tile items of 256 rows; dir 0: vec B <- ptrs[sys] permuted; dir 1: ptrs[sys] <- vec X natural.
+template <int BS>
 __global__ void __launch_bounds__(kDotTile)
     permute_batched(const SysDesc* __restrict__ sys, const BatchItem* __restrict__ items, int64_t nitems,
                     const double* const* __restrict__ ptrs, int dir) {
@@ -950,16 +983,19 @@ __global__ void __launch_bounds__(kDotTile)
     const int64_t i = (int64_t)it.local * kDotTile + threadIdx.x;
     if (i >= S.N) continue;
     if (dir == 0)
-      gather_rows(ptrs[it.sys], S.vec[kVecB], S.perm, i);
+      gather_rows<BS>(ptrs[it.sys], S.vec[kVecB], S.perm, i);
     else
-      gather_rows(S.vec[kVecX], const_cast<double*>(ptrs[it.sys]), S.iperm, i);
+      gather_rows<BS>(S.vec[kVecX], const_cast<double*>(ptrs[it.sys]), S.iperm, i);
   }
 }
 
 cudaError_t launch_permute_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems,
-                                   const double* const* ptrs, int dir, int grid, cudaStream_t s) {
+                                   const double* const* ptrs, int dir, int bs, int grid, cudaStream_t s) {
   if (nitems == 0) return cudaSuccess;
-  permute_batched<<<grid, kDotTile, 0, s>>>(sys, items, nitems, ptrs, dir);
+  if (bs == 1)
+    permute_batched<1><<<grid, kDotTile, 0, s>>>(sys, items, nitems, ptrs, dir);
+  else
+    permute_batched<3><<<grid, kDotTile, 0, s>>>(sys, items, nitems, ptrs, dir);
   return cudaGetLastError();
 }
 

@@ -40,7 +40,7 @@ struct DevCtx {
   SysDesc sd;
   int threads, factor_prec;
   size_t smem_bytes;
-  int bs = 3;  // block dimension: 3 or 1 (scalar CSR); batched launches take 3 only
+  int bs = 3;  // block dimension: 3 or 1 (scalar CSR)
 };
 
 // Work item of a batched launch: system index and block index inside it.
@@ -90,25 +90,26 @@ cudaError_t launch_permute(const DevCtx& d, const double* in, double* out, int d
 // ---- batched launches: one launch covers the work items of many systems.
 // `sys` is a device array of SysDesc; items list (system, subdomain) for the
 // apply and (system, dot tile) for the others. Systems whose solve is done are
-// skipped. `grid` blocks loop over the items (persistent launch).
+// skipped. `grid` blocks loop over the items (persistent launch). Every
+// system of one launch has block dimension `bs` (3 or 1).
 cudaError_t launch_apply_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int mode,
-                                 int factor_prec, int threads, size_t smem, int grid, cudaStream_t s);
-cudaError_t launch_spmv_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int kind, int grid,
-                                cudaStream_t s);
-cudaError_t launch_update_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int grid,
+                                 int factor_prec, int bs, int threads, size_t smem, int grid, cudaStream_t s);
+cudaError_t launch_spmv_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int kind, int bs,
+                                int grid, cudaStream_t s);
+cudaError_t launch_update_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int bs, int grid,
                                   cudaStream_t s);
 // mode 0: init from b (vec B), 1: r = b - t with rel_true, 2: restart from r
 // (systems flagged in `flags`).
 cudaError_t launch_vec_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int mode, double rtol,
-                               int32_t maxit, const int32_t* flags, int grid, cudaStream_t s);
+                               int32_t maxit, const int32_t* flags, int bs, int grid, cudaStream_t s);
 // dir 0: vec B of system i <- in[i] permuted; dir 1: out[i] <- vec X of system i.
 cudaError_t launch_permute_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems,
-                                   const double* const* ptrs, int dir, int grid, cudaStream_t s);
+                                   const double* const* ptrs, int dir, int bs, int grid, cudaStream_t s);
 // out[i] = the solver scalars of system i (one small launch).
 cudaError_t launch_gather_status(const SysDesc* sys, int32_t nsys, SolverScalars* out, cudaStream_t s);
 
 // Blocks per SM of the batched kernels (for persistent grids).
-int apply_blocks_per_sm(int factor_prec, int threads, size_t smem);
-int tile_blocks_per_sm();
+int apply_blocks_per_sm(int factor_prec, int bs, int threads, size_t smem);
+int tile_blocks_per_sm(int bs);
 
 }  // namespace ilu0dd

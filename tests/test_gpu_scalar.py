@@ -6,7 +6,8 @@ reduction order); FP64 and DF64 applies within 1e-12 of the oracle's
 sequential ILU0 substitution, FP32/BF16 within their storage precision;
 BiCGSTAB with the oracle's iteration count on the laplace systems and within
 5 % on the ill-conditioned layered ones; the device setup, the unfused apply
-and the host-buffer apply giving the same bits as their counterparts.
+and the host-buffer apply giving the same bits as their counterparts; a
+batch of scalar systems giving each single solve's bits.
 """
 import numpy as np
 import pytest
@@ -115,11 +116,35 @@ def test_scalar_device_setup_unfused_and_host_apply(prec):
         host.close()
 
 
-def test_batch_refuses_scalar_contexts():
-    s = synth.system(8, 8, 8, 5, bs=1)
-    ctx = g.Ilu0DD(s.row_ptr, s.col, s.val, (8, 8, 8), (4, 4, 4))
+def test_scalar_batched_equals_single():
+    """A batch of scalar systems (different grids and subdomain boxes) gives
+    each system's single-solve bits and iteration count."""
+    specs = [GEOMS[0], GEOMS[1], GEOMS[2]]
+    ctxs, bvecs = [], []
+    for k, (grid, sub, model) in enumerate(specs):
+        s = synth.system(*grid, 21 + k, model=model, bs=1)
+        ctxs.append(g.Ilu0DD(s.row_ptr, s.col, s.val, grid, sub))
+        bvecs.append(cu(s.b))
+    try:
+        singles = [c.solve(b) for c, b in zip(ctxs, bvecs)]
+        batch = g.Batch(ctxs)
+        xs, infos = batch.solve(bvecs)
+        for (x1, i1), x2, i2 in zip(singles, xs, infos):
+            assert i2["status"] == 0 and i1["iterations"] == i2["iterations"] and torch.equal(x1, x2)
+        batch.close()
+    finally:
+        for c in ctxs:
+            c.close()
+
+
+def test_batch_refuses_mixed_block_dims():
+    s1 = synth.system(8, 8, 8, 5, bs=1)
+    s3 = synth.system(8, 8, 8, 5)
+    c1 = g.Ilu0DD(s1.row_ptr, s1.col, s1.val, (8, 8, 8), (4, 4, 4))
+    c3 = g.Ilu0DD(s3.row_ptr, s3.col, s3.val, (8, 8, 8), (4, 4, 4))
     try:
         with pytest.raises(g.Ilu0DDError):
-            g.Batch([ctx])
+            g.Batch([c1, c3])
     finally:
-        ctx.close()
+        c1.close()
+        c3.close()
