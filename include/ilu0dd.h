@@ -377,7 +377,7 @@ int ilu0_dd_export(const ilu0dd_ctx* ctx, int what, void* host_dst, size_t bytes
 #define ILU0DD_Q_STREAM_BYTES 8   /* bytes of the packed factor stream */
 #define ILU0DD_Q_THREADS 9        /* apply threads per block */
 #define ILU0DD_Q_SMEM 10          /* apply dynamic shared memory per block */
-#define ILU0DD_Q_PIECES 11        /* barrier-separated pieces, summed over subdomains */
+#define ILU0DD_Q_PIECES 11        /* pieces (level slices of a subdomain), summed over subdomains */
 #define ILU0DD_Q_CUDA_ERROR 12    /* last cudaError_t recorded by the context */
 #define ILU0DD_Q_MAX_LEVELS 13    /* max over subdomains of L levels + U levels */
 #define ILU0DD_Q_WORKSPACE 14     /* workspace bytes in use */
@@ -389,8 +389,24 @@ int ilu0_dd_export(const ilu0dd_ctx* ctx, int what, void* host_dst, size_t bytes
 int ilu0_dd_query(const ilu0dd_ctx* ctx, int what, int64_t* value);
 
 /* Read (and clear) the device error word: 0, or the code of a bounded wait
- * that expired inside a kernel. Synchronizes the device. */
+ * that expired inside a kernel (1: an apply warp's wait for the previous
+ * level, Section 4.4's level order). Synchronizes the device. */
 int ilu0_dd_device_error(const ilu0dd_ctx* ctx, int32_t* code);
+
+/* The apply's waits (Section 4.4: a warp starts a level's rows once the
+ * previous level is done) are bounded. A warp polls the previous level's
+ * completion counters at most `polls` times (0 restores the default, about
+ * 0.1 s); when they run out the block stops waiting, sets the device error
+ * word to 1 and finishes (its z values are then not valid), so the kernel
+ * always returns. bicgstab_solve then returns ILU0DD_ERR_DEVICE_WAIT, and a
+ * batched solve reports it for that system. stuck_piece >= 0 (a piece
+ * index in [0, ILU0DD_Q_PIECES)) makes that piece's completion count
+ * unreachable, so every wait on it expires: a failure-path test of the waits
+ * that needs no GPU fault; -1 (the default) disables it. Host-side only
+ * (takes effect at the context's next launch, and for batches created after
+ * the call). Returns ILU0DD_ERR_INVALID for a null ctx or a piece out of
+ * range. */
+int ilu0dd_set_wait_limits(ilu0dd_ctx* ctx, uint32_t polls, int32_t stuck_piece);
 
 /* Release the host-side context (the caller frees the workspace). */
 void ilu0_dd_destroy(ilu0dd_ctx* ctx);

@@ -121,6 +121,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "ilu0_dd_export": ([vp, ctypes.c_int, vp, sz], ctypes.c_int),
             "ilu0_dd_query": ([vp, ctypes.c_int, ctypes.POINTER(i64)], ctypes.c_int),
             "ilu0_dd_device_error": ([vp, ctypes.POINTER(i32)], ctypes.c_int),
+            "ilu0dd_set_wait_limits": ([vp, ctypes.c_uint32, i32], ctypes.c_int),
             "ilu0_dd_destroy": ([vp], None),
         }
         for name, (args, res) in sig.items():
@@ -421,6 +422,12 @@ class Ilu0DD:
         v = ctypes.c_int32(0)
         self._check(self._lib.ilu0_dd_device_error(self._ctx, ctypes.byref(v)), "ilu0_dd_device_error")
         return int(v.value)
+
+    def set_wait_limits(self, polls=0, stuck_piece=-1):
+        """Bound of the apply's level waits (0: default) and a piece whose
+        completion is never counted (-1: none), for failure-path tests."""
+        self._check(self._lib.ilu0dd_set_wait_limits(self._ctx, int(polls), int(stuck_piece)),
+                    "ilu0dd_set_wait_limits")
 
 
 class Batch:

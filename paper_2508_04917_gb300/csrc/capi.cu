@@ -154,7 +154,9 @@ int setup_numeric(ilu0dd_ctx* c, const ilu0dd_bsr* A, const ilu0dd_opts& o, void
     S.pieces = reinterpret_cast<const PieceDesc*>(c->ws + L.pieces);
     S.nsub = p.nsub;
     S.prefetch_bytes = p.prefetch_bytes;
-    S.vec_bytes = (int)(p.smem_bytes - sizeof(PieceDesc) * kDescCache);
+    S.vec_bytes = (int)(p.smem_bytes - kApplyTailSmem);
+    S.wait_polls = kApplyWaitPolls;
+    S.wait_stuck = -1;
     S.slice_off = reinterpret_cast<const int32_t*>(c->ws + L.sell_off);
     S.sell_col = reinterpret_cast<const int32_t*>(c->ws + L.sell_col);
     S.sell_val = reinterpret_cast<const double*>(c->ws + L.sell_val);
@@ -469,8 +471,10 @@ cudaError_t run_chunk(ilu0dd_ctx* c) {
   return cudaGraphLaunch(c->graph, c->own);
 }
 
-cudaError_t read_scalars(ilu0dd_ctx* c, SolverScalars* h) {
+// The solver scalars and the device error word (an apply wait that expired).
+cudaError_t read_scalars(ilu0dd_ctx* c, SolverScalars* h, int32_t* derr) {
   cudaError_t e = cudaMemcpyAsync(h, c->dev.sd.scal, sizeof *h, cudaMemcpyDeviceToHost, c->own);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(derr, c->dev.sd.err, sizeof *derr, cudaMemcpyDeviceToHost, c->own);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->own);
   return e;
 }
@@ -485,6 +489,7 @@ int bicgstab_solve(ilu0dd_ctx* c, const double* d_b, double* d_x, ilu0dd_info* i
   const DevCtx& d = c->dev;
   cudaStream_t us = reinterpret_cast<cudaStream_t>(stream);
   SolverScalars h{};
+  int32_t derr = 0;
   int status = ILU0DD_OK, restarts = 0;
   CK(c, cudaStreamSynchronize(us));
   if (c->plan.N == 0) {
@@ -496,13 +501,14 @@ int bicgstab_solve(ilu0dd_ctx* c, const double* d_b, double* d_x, ilu0dd_info* i
   }
   CK(c, launch_permute(d, d_b, d.sd.vec[kVecB], 0, c->own));
   CK(c, launch_init(d, c->rtol, c->maxit, c->own));
-  CK(c, read_scalars(c, &h));
+  CK(c, read_scalars(c, &h, &derr));
   if (h.status == ILU0DD_ERR_NONFINITE) status = ILU0DD_ERR_NONFINITE;
   while (status == ILU0DD_OK && !h.converged) {
-    while (!h.done) {
+    while (!h.done && !derr) {
       CK(c, run_chunk(c));
-      CK(c, read_scalars(c, &h));
+      CK(c, read_scalars(c, &h, &derr));
     }
+    if (derr) break;  // an apply wait expired: the iterates are not valid
     if (h.status != ILU0DD_OK) {
       status = h.status;
       break;
@@ -510,23 +516,22 @@ int bicgstab_solve(ilu0dd_ctx* c, const double* d_b, double* d_x, ilu0dd_info* i
     // true residual r = b - A x
     CK(c, launch_spmv(d, 0, d.sd.vec[kVecX], d.sd.vec[kVecT], c->own));
     CK(c, launch_residual(d, 0, c->own));
-    CK(c, read_scalars(c, &h));
+    CK(c, read_scalars(c, &h, &derr));
     if (h.rel_true < c->rtol) break;
     if (restarts == 0) {
       restarts = 1;
       CK(c, launch_residual(d, 1, c->own));
-      CK(c, read_scalars(c, &h));
+      CK(c, read_scalars(c, &h, &derr));
       continue;
     }
     status = ILU0DD_ERR_NOT_CONVERGED;
     break;
   }
-  // a device wait that expired poisons the result
-  int32_t derr = 0;
+  // a device wait that expired poisons the result, whatever else was seen
   CK(c, cudaMemcpyAsync(&derr, d.sd.err, sizeof derr, cudaMemcpyDeviceToHost, c->own));
   CK(c, launch_permute(d, d.sd.vec[kVecX], d_x, 1, c->own));
   CK(c, cudaStreamSynchronize(c->own));
-  if (derr && status == ILU0DD_OK) status = ILU0DD_ERR_DEVICE_WAIT;
+  if (derr) status = ILU0DD_ERR_DEVICE_WAIT;
   c->last_iterations = h.iter;
   if (info) {
     info->status = status;
@@ -684,6 +689,17 @@ int ilu0_dd_query(const ilu0dd_ctx* c, int what, int64_t* v) {
     case ILU0DD_Q_SELL_SLOTS: *v = p.sell_slots; break;
     case ILU0DD_Q_BLOCK_DIM: *v = p.bs; break;
     default: return ILU0DD_ERR_INVALID;
+  }
+  return ILU0DD_OK;
+}
+
+int ilu0dd_set_wait_limits(ilu0dd_ctx* c, uint32_t polls, int32_t stuck_piece) {
+  if (!c || stuck_piece < -1 || (stuck_piece >= 0 && stuck_piece >= c->plan.n_pieces)) return ILU0DD_ERR_INVALID;
+  c->dev.sd.wait_polls = polls ? polls : kApplyWaitPolls;
+  c->dev.sd.wait_stuck = stuck_piece;
+  if (c->graph) {  // captured launches hold the old kernel parameters
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
   }
   return ILU0DD_OK;
 }

@@ -52,8 +52,18 @@ struct PieceDesc {          // 32 bytes, one per piece, device array
   uint32_t nb;              // blocks in the record
   uint32_t voff;            // first value array (invD or vals), bytes from record start
   uint16_t cnt[4];          // cnt[s] for s < min(w, kDescSlots) (copy of the record's head), 0 beyond
-  uint32_t pad[2];
+  uint32_t lvl_first;       // first piece of this piece's level (index within the subdomain)
+  uint32_t prev_first;      // first piece of the previous level (= lvl_first for the first level)
 };
+
+// Shared memory of the apply after the subdomain vector: the staged piece
+// descriptors, one completion counter per staged piece, the abort flag.
+constexpr size_t kApplyTailSmem = sizeof(PieceDesc) * kDescCache + sizeof(uint32_t) * kDescCache + 16;
+// Polls a warp of the apply makes on a completion counter before it gives up
+// (about 0.1 s at 2 GHz; a level completes in microseconds).
+constexpr uint32_t kApplyWaitPolls = 1u << 22;
+// Device error word codes.
+constexpr int32_t kErrApplyWait = 1;  // an apply warp's wait for the previous level expired
 
 struct CtaDesc {            // 32 bytes, one per subdomain
   int64_t stream_off;       // bytes from the stream base, 128-aligned

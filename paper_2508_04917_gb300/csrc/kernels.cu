@@ -63,9 +63,13 @@ __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 // slot counts in the piece descriptor let every load of a level issue at
 // once) while one thread keeps bulk L2 prefetches (cp.async.bulk.prefetch.L2)
 // a fixed distance ahead in the subdomain's stream. Shared memory holds the
-// subdomain vector and the block's piece descriptors. Three threads per row
-// (lane = 3 * (row in warp) + a, ten rows per warp); rows of one piece are
-// independent and pieces are separated by block barriers.
+// subdomain vector, the block's piece descriptors and one completion counter
+// per piece. Three threads per row (lane = 3 * (row in warp) + a, ten rows per
+// warp); rows of one piece are independent. There are no block barriers
+// between pieces: a piece's row groups go to warps round-robin, a warp issues
+// the loads of its row group at once and then waits only until the previous
+// level's pieces have counted all their row groups done, so warps with no
+// rows in the current level run ahead to load for later ones.
 // In the DF64 mode the vector is held as float pairs, scaled by a power of two
 // per block (exact, and the apply is linear and local to the block) so that
 // the FP32 exponent range never limits it.
@@ -154,31 +158,50 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
   __syncthreads();
 
   const int warp = tid >> 5, lane = tid & 31;
+  const int nwarps = (int)(blockDim.x >> 5);
   const int comp = BS == 3 ? lane % 3 : 0;
-  const int trow = warp * RPW + (BS == 3 ? lane / 3 : lane);
   const bool lane_ok = BS == 3 ? lane < 3 * kRowsPerWarp : true;
   const int base_lane = lane - comp;
-  const uint32_t lane_voff = (uint32_t)(BS * trow + comp) * FE;  // this thread's value offset in a slot
-  const uint32_t trow2 = 2u * (uint32_t)trow;
 
-  // piece descriptors are staged in shared memory, kDescCache at a time
+  // Piece descriptors are staged in shared memory, kDescCache at a time, with
+  // one completion counter per staged piece (row groups done).
   PieceDesc* dsm = reinterpret_cast<PieceDesc*>(smem + S.vec_bytes);
+  uint32_t* done = reinterpret_cast<uint32_t*>(dsm + kDescCache);
+  volatile uint32_t* abort_flag = done + kDescCache;
+  int win0 = k0;  // first piece of the staged window
+  int rot = 0;    // warp that takes row group 0 of the next piece
   for (int k = k0; k < k1; ++k) {
     if ((k - k0) % kDescCache == 0) {
-      if (k > k0) __syncthreads();
+      if (k > k0) __syncthreads();  // every piece of the window is done
       const int cnt = min(kDescCache, k1 - k);
       const uint4* src = reinterpret_cast<const uint4*>(S.pieces + cd.piece0 + k);
       uint4* dst = reinterpret_cast<uint4*>(dsm);
       for (int q = tid; q < 2 * cnt; q += blockDim.x) dst[q] = __ldg(src + q);
+      for (int q = tid; q < kDescCache; q += blockDim.x) done[q] = 0;
+      if (k == k0 && tid == 0) *abort_flag = 0;
+      win0 = k;
       __syncthreads();
     }
-    const PieceDesc pd = dsm[(k - k0) % kDescCache];
+    const PieceDesc pd = dsm[k - win0];
     if (pf_thread) prefetch_upto(pd.off + dist);
     const int n = (int)(pd.meta & 0xFFFFu);
     const int w = (int)((pd.meta >> 16) & 0xFFu);
     const int kind = (int)(pd.meta >> 24);
-    if (warp * RPW < n) {  // warp-uniform: this warp has rows in the piece
+    // Row groups (RPW rows each) go to warps round-robin across pieces, so a
+    // warp issues the loads of its next group while the pieces before it run
+    // on other warps. Without block barriers, a warp waits only for the
+    // previous level's pieces (their completion counters), and only before it
+    // reads the subdomain vector.
+    const int ng = (n + RPW - 1) / RPW;  // <= nwarps (pieces fit the block)
+    int g = warp - rot;
+    if (g < 0) g += nwarps;
+    rot += ng;
+    if (rot >= nwarps) rot -= nwarps;
+    if (g < ng) {  // warp-uniform: this warp has a row group in the piece
+      const int trow = g * RPW + (BS == 3 ? lane / 3 : lane);
       const bool active = lane_ok && trow < n;
+      const uint32_t lane_voff = (uint32_t)(BS * trow + comp) * FE;  // this thread's value offset in a slot
+      const uint32_t trow2 = 2u * (uint32_t)trow;
       const unsigned char* rec = gs + pd.off;
       // 32-bit byte offsets from the block's (uniform) stream base: the
       // warp-uniform part per slot plus this thread's fixed part
@@ -210,6 +233,23 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
         for (int c = 0; c < BS; ++c) d[c] = gfactor<TF>(gs + (io + (uint32_t)c * cstride));
       }
       const int row = active ? gu16(gs + (pd.off + 2u * (uint32_t)w + trow2)) : 0;
+      // Wait (the whole warp, converged) for the previous level's pieces of
+      // this window; earlier windows are done. Bounded: after
+      // S.wait_polls polls the block gives up and flags the error word.
+      for (int j = max((int)pd.prev_first, win0); j < (int)pd.lvl_first; ++j) {
+        const uint32_t need = ((dsm[j - win0].meta & 0xFFFFu) + RPW - 1) / RPW +
+                              (cd.piece0 + j == S.wait_stuck ? 1u : 0u);
+        const volatile uint32_t* cj = done + (j - win0);
+        uint32_t polls = 0;
+        while (!__all_sync(0xffffffffu, *cj >= need)) {
+          if ((++polls & 255u) == 0 && (__any_sync(0xffffffffu, *abort_flag != 0) || polls >= S.wait_polls)) {
+            if (lane == 0 && atomicCAS(const_cast<uint32_t*>(abort_flag), 0u, 1u) == 0u)
+              atomicCAS(S.err, 0, kErrApplyWait);
+            break;
+          }
+        }
+      }
+      __threadfence_block();
       TV acc = active ? y[BS * row + comp] : TV(0);
       if (kind) {
         // D^-1 (Section 4.3): w_i = D_i^-1 y_i; with 3x3 blocks the row's
@@ -250,31 +290,20 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
         }
         y[BS * row + comp] = acc;
       }
+      __syncwarp();
+      __threadfence_block();
+      if (lane == 0) atomicAdd(done + (k - win0), 1u);
     }
-    __syncthreads();
   }
+  __syncthreads();
   for (int e = tid; e < nv; e += blockDim.x) z[base + e] = kDF ? to_double(y[e]) * unscale : to_double(y[e]);
 }
 
-// Resident blocks per SM the single-system apply's register budget targets:
-// FP32/BF16 blocks are latency-bound, so four per SM; FP64 and DF64 keep
-// three (their working sets would spill at four). The batched apply keeps
-// three (its work loop holds more state).
-template <typename TF>
-struct ApplyMinBlocks {
-  static constexpr int value = 4;
-};
-template <>
-struct ApplyMinBlocks<double> {
-  static constexpr int value = kApplyMinBlocks;
-};
-template <>
-struct ApplyMinBlocks<df64s> {  // pairs need FP64-sized registers
-  static constexpr int value = kApplyMinBlocks;
-};
-
+// Every apply instance is compiled for three resident blocks per SM (56
+// registers): at four (40 registers) the FP32/BF16 instances spill and run
+// slower; FP64 and DF64 spill at four either way.
 template <typename TF, int MODE, int BS>
-__global__ void __launch_bounds__(kMaxApplyThreads, ApplyMinBlocks<TF>::value)
+__global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
     ildu0_apply_kernel(SysDesc S, const double* r, double* z, int sub0) {
   apply_block<TF, MODE, 0, BS>(S, sub0 + blockIdx.x, r, z);
 }
@@ -282,7 +311,7 @@ __global__ void __launch_bounds__(kMaxApplyThreads, ApplyMinBlocks<TF>::value)
 // The unfused apply's two launches (plain mode): PART 1 = L sweep, r -> z;
 // PART 2 = D^-1 and U~ sweep, z -> z in place.
 template <typename TF, int PART, int BS>
-__global__ void __launch_bounds__(kMaxApplyThreads, ApplyMinBlocks<TF>::value)
+__global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
     ildu0_apply_part_kernel(SysDesc S, const double* r, double* z) {
   apply_block<TF, kModePlain, PART, BS>(S, blockIdx.x, r, z);
 }
@@ -999,9 +1028,15 @@ cudaError_t launch_permute_batched(const SysDesc* sys, const BatchItem* items, i
   return cudaGetLastError();
 }
 
+// A system whose device error word is set (an apply wait expired) reports
+// ILU0DD_ERR_DEVICE_WAIT in its gathered status.
 __global__ void gather_status(const SysDesc* __restrict__ sys, int32_t nsys, SolverScalars* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nsys) out[i] = *sys[i].scal;
+  if (i < nsys) {
+    SolverScalars h = *sys[i].scal;
+    if (*sys[i].err != 0) h.status = ILU0DD_ERR_DEVICE_WAIT;
+    out[i] = h;
+  }
 }
 
 cudaError_t launch_gather_status(const SysDesc* sys, int32_t nsys, SolverScalars* out, cudaStream_t s) {

@@ -33,6 +33,10 @@ struct SysDesc {
   int64_t ntiles, ntiles_pow2;
   int32_t N, nsub;
   int32_t vec_bytes, prefetch_bytes;
+  // apply waits: polls before giving up; a piece (global index) whose
+  // completion count is never reached (-1: none; failure-path tests only)
+  uint32_t wait_polls;
+  int32_t wait_stuck;
 };
 
 // Host view of one context: the system and its launch configuration.

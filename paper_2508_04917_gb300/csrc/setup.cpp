@@ -422,6 +422,7 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
     std::vector<int32_t> start, byl;
     std::vector<std::pair<int32_t, int32_t>> key;  // (-blocks, row)
     uint32_t off = 0;
+    int64_t prev_lvl = -1;  // first piece of the previous non-empty level
     for (int kind = 0; kind < 2; ++kind) {
       const int32_t nl = kind ? nlev_u[s] : nlev_l[s];
       const std::vector<int32_t>& lev = kind ? p.lev_u : p.lev_l;
@@ -436,6 +437,9 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
       }
       for (int32_t l = kind ? 0 : 1; l < nl; ++l) {
         if (start[l + 1] == start[l]) continue;
+        const uint32_t first = (uint32_t)sub_desc[s].size();
+        const uint32_t prev = prev_lvl < 0 ? first : (uint32_t)prev_lvl;
+        prev_lvl = first;
         key.clear();
         for (int32_t x = start[l]; x < start[l + 1]; ++x) {
           const int32_t i = byl[x];
@@ -464,6 +468,8 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
           d.meta = (uint32_t)n | ((uint32_t)w << 16) | ((uint32_t)kind << 24);
           d.nb = (uint32_t)nb;
           d.voff = (uint32_t)voff;
+          d.lvl_first = first;
+          d.prev_first = prev;
           for (int sl = 0; sl < std::min(w, kDescSlots); ++sl) {
             int c = 0;
             for (size_t t = a; t < b; ++t) c += -key[t].first > sl;
@@ -521,7 +527,7 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   });
   p.stream_bytes = soff;
   p.n_pieces = (int64_t)p.pieces.size();
-  p.smem_bytes = (size_t)align_up((int64_t)bs * p.rmax * p.vec_elem, 128) + sizeof(PieceDesc) * kDescCache;
+  p.smem_bytes = (size_t)align_up((int64_t)bs * p.rmax * p.vec_elem, 128) + kApplyTailSmem;
   if ((int64_t)p.smem_bytes > (int64_t)max_smem - kApplyStaticSmem) {
     *why = "subdomain vector (" + std::to_string((int64_t)bs * p.rmax * p.vec_elem) + " B) exceeds the " +
            std::to_string(max_smem) +
