@@ -92,7 +92,7 @@ typedef struct {
 typedef struct {
   int32_t factor_prec;      /* ILU0DD_F64 / ILU0DD_F32 / ILU0DD_BF16 / ILU0DD_DF64 */
   int32_t threads_per_cta;  /* apply block size; 0 = 32 per ten rows of the widest level (<= 384) */
-  int32_t prefetch_bytes;   /* apply: L2 prefetch distance per block, bytes (multiple of 16); 0 = 65536 */
+  int32_t prefetch_bytes;   /* apply: L2 prefetch distance per block, bytes (multiple of 16); 0 = 32768 */
   int32_t maxit;            /* BiCGSTAB iteration limit; 0 = 10000 */
   double rtol;              /* stop when ||r||_2/||b||_2 < rtol; 0 = 1e-8 */
   int32_t check_every;      /* iterations per CUDA-graph launch between convergence polls; 0 = 8 */
@@ -394,11 +394,11 @@ int ilu0_dd_query(const ilu0dd_ctx* ctx, int what, int64_t* value);
 int ilu0_dd_device_error(const ilu0dd_ctx* ctx, int32_t* code);
 
 /* The apply's waits (Section 4.4: a warp starts a level's rows once the
- * previous level is done) are bounded. A warp polls the previous level's
- * completion counters at most `polls` times (0 restores the default, about
- * 0.1 s); when they run out the block stops waiting, sets the device error
- * word to 1 and finishes (its z values are then not valid), so the kernel
- * always returns. bicgstab_solve then returns ILU0DD_ERR_DEVICE_WAIT, and a
+ * previous level is done) are bounded. A warp waits for the previous level's
+ * pieces at most `wait_us` microseconds (at the peak SM clock; 0 restores the
+ * default, 100000 = 0.1 s); then the block stops waiting, sets the device
+ * error word to 1 and finishes (its z values are then not valid), so the
+ * kernel always returns. bicgstab_solve then returns ILU0DD_ERR_DEVICE_WAIT, and a
  * batched solve reports it for that system. stuck_piece >= 0 (a piece
  * index in [0, ILU0DD_Q_PIECES)) makes that piece's completion count
  * unreachable, so every wait on it expires: a failure-path test of the waits
@@ -406,7 +406,7 @@ int ilu0_dd_device_error(const ilu0dd_ctx* ctx, int32_t* code);
  * (takes effect at the context's next launch, and for batches created after
  * the call). Returns ILU0DD_ERR_INVALID for a null ctx or a piece out of
  * range. */
-int ilu0dd_set_wait_limits(ilu0dd_ctx* ctx, uint32_t polls, int32_t stuck_piece);
+int ilu0dd_set_wait_limits(ilu0dd_ctx* ctx, uint32_t wait_us, int32_t stuck_piece);
 
 /* Release the host-side context (the caller frees the workspace). */
 void ilu0_dd_destroy(ilu0dd_ctx* ctx);

@@ -423,10 +423,11 @@ class Ilu0DD:
         self._check(self._lib.ilu0_dd_device_error(self._ctx, ctypes.byref(v)), "ilu0_dd_device_error")
         return int(v.value)
 
-    def set_wait_limits(self, polls=0, stuck_piece=-1):
-        """Bound of the apply's level waits (0: default) and a piece whose
-        completion is never counted (-1: none), for failure-path tests."""
-        self._check(self._lib.ilu0dd_set_wait_limits(self._ctx, int(polls), int(stuck_piece)),
+    def set_wait_limits(self, wait_us=0, stuck_piece=-1):
+        """Bound of the apply's level waits in microseconds (0: default) and a
+        piece whose completion is never reached (-1: none), for failure-path
+        tests."""
+        self._check(self._lib.ilu0dd_set_wait_limits(self._ctx, int(wait_us), int(stuck_piece)),
                     "ilu0dd_set_wait_limits")
 
 

@@ -25,6 +25,17 @@ int cuda_fail(ilu0dd_ctx* c, cudaError_t e, const char* what) {
   return ILU0DD_ERR_CUDA;
 }
 
+// The apply's wait bound in SM cycles, from microseconds at the device's
+// peak SM clock (a lower running clock only lengthens the bound).
+cudaError_t set_wait_us(ilu0dd_ctx* c, uint32_t us) {
+  int dev = 0, khz = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+  if (e != cudaSuccess) return e;
+  c->dev.sd.wait_cycles = (uint64_t)us * (uint64_t)(khz > 0 ? khz : 2000000) / 1000u;
+  return cudaSuccess;
+}
+
 #define CK(ctx, call)                                    \
   do {                                                   \
     cudaError_t e_ = (call);                             \
@@ -155,7 +166,6 @@ int setup_numeric(ilu0dd_ctx* c, const ilu0dd_bsr* A, const ilu0dd_opts& o, void
     S.nsub = p.nsub;
     S.prefetch_bytes = p.prefetch_bytes;
     S.vec_bytes = (int)(p.smem_bytes - kApplyTailSmem);
-    S.wait_polls = kApplyWaitPolls;
     S.wait_stuck = -1;
     S.slice_off = reinterpret_cast<const int32_t*>(c->ws + L.sell_off);
     S.sell_col = reinterpret_cast<const int32_t*>(c->ws + L.sell_col);
@@ -177,6 +187,7 @@ int setup_numeric(ilu0dd_ctx* c, const ilu0dd_bsr* A, const ilu0dd_opts& o, void
     d.smem_bytes = p.smem_bytes;
     d.bs = p.bs;
     e = apply_configure(d);
+    if (e == cudaSuccess) e = set_wait_us(c, kApplyWaitUs);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
       int r = cuda_fail(c, e, "setup configure");
@@ -693,9 +704,10 @@ int ilu0_dd_query(const ilu0dd_ctx* c, int what, int64_t* v) {
   return ILU0DD_OK;
 }
 
-int ilu0dd_set_wait_limits(ilu0dd_ctx* c, uint32_t polls, int32_t stuck_piece) {
+int ilu0dd_set_wait_limits(ilu0dd_ctx* c, uint32_t wait_us, int32_t stuck_piece) {
   if (!c || stuck_piece < -1 || (stuck_piece >= 0 && stuck_piece >= c->plan.n_pieces)) return ILU0DD_ERR_INVALID;
-  c->dev.sd.wait_polls = polls ? polls : kApplyWaitPolls;
+  if (cudaError_t e = set_wait_us(c, wait_us ? wait_us : kApplyWaitUs); e != cudaSuccess)
+    return cuda_fail(c, e, "wait limits");
   c->dev.sd.wait_stuck = stuck_piece;
   if (c->graph) {  // captured launches hold the old kernel parameters
     cudaGraphExecDestroy(c->graph);

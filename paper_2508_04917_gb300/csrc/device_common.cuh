@@ -1,5 +1,5 @@
-// Device helpers: mbarrier + bulk-copy (TMA) staging, bounded waits, the fixed
-// reduction order, precision conversions. sm_103a only.
+// Device helpers: shared-memory mbarriers, the fixed reduction order,
+// precision conversions. sm_103a only.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -9,15 +9,8 @@
 
 namespace ilu0dd {
 
-// Error word codes written by kernels (device error word).
-constexpr int32_t kDevErrWaitExpired = 1;
-
-// Iteration limit of an mbarrier wait loop. Each try_wait suspends the thread
-// for a hardware-chosen interval; the limit keeps every wait finite (well
-// above any legitimate copy latency) so a lost completion ends the kernel
-// with an error word instead of a hang.
-constexpr uint32_t kWaitSpins = 1u << 22;
-
+// Shared-memory mbarriers at CTA scope: arrive has release semantics,
+// try_wait acquire semantics.
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -26,16 +19,17 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// True once the phase with the given parity has completed. The thread may be
+// suspended for a hardware-chosen interval (woken when the phase completes)
+// before a false return.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -46,23 +40,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return ok != 0;
-}
-
-// Bounded wait for the completion of phase `parity`; false if the limit expired.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kWaitSpins; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-// One-dimensional bulk copy global -> shared, completing on `bar`.
-// dst, src 16-byte aligned; bytes a multiple of 16.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
 }
 
 __device__ __forceinline__ float bf16_to_f32(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }

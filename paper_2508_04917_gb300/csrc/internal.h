@@ -57,11 +57,11 @@ struct PieceDesc {          // 32 bytes, one per piece, device array
 };
 
 // Shared memory of the apply after the subdomain vector: the staged piece
-// descriptors, one completion counter per staged piece, the abort flag.
-constexpr size_t kApplyTailSmem = sizeof(PieceDesc) * kDescCache + sizeof(uint32_t) * kDescCache + 16;
-// Polls a warp of the apply makes on a completion counter before it gives up
-// (about 0.1 s at 2 GHz; a level completes in microseconds).
-constexpr uint32_t kApplyWaitPolls = 1u << 22;
+// descriptors, one mbarrier per staged piece, the abort flag.
+constexpr size_t kApplyTailSmem = sizeof(PieceDesc) * kDescCache + sizeof(uint64_t) * kDescCache + 16;
+// How long a warp of the apply waits for the previous level before it gives
+// up, in microseconds (a level completes in microseconds).
+constexpr uint32_t kApplyWaitUs = 100000;
 // Device error word codes.
 constexpr int32_t kErrApplyWait = 1;  // an apply warp's wait for the previous level expired
 

@@ -63,13 +63,13 @@ __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 // slot counts in the piece descriptor let every load of a level issue at
 // once) while one thread keeps bulk L2 prefetches (cp.async.bulk.prefetch.L2)
 // a fixed distance ahead in the subdomain's stream. Shared memory holds the
-// subdomain vector, the block's piece descriptors and one completion counter
-// per piece. Three threads per row (lane = 3 * (row in warp) + a, ten rows per
-// warp); rows of one piece are independent. There are no block barriers
-// between pieces: a piece's row groups go to warps round-robin, a warp issues
-// the loads of its row group at once and then waits only until the previous
-// level's pieces have counted all their row groups done, so warps with no
-// rows in the current level run ahead to load for later ones.
+// subdomain vector, the block's piece descriptors and one mbarrier per piece.
+// Three threads per row (lane = 3 * (row in warp) + a, ten rows per warp);
+// rows of one piece are independent. There are no block barriers between
+// pieces: a piece's row groups go to warps round-robin, a warp issues the
+// loads of its row group at once and then waits (suspended, not polling)
+// only until the previous level's pieces are complete, so warps with no rows
+// in the current level run ahead to load for later ones.
 // In the DF64 mode the vector is held as float pairs, scaled by a power of two
 // per block (exact, and the apply is linear and local to the block) so that
 // the FP32 exponent range never limits it.
@@ -164,22 +164,31 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
   const int base_lane = lane - comp;
 
   // Piece descriptors are staged in shared memory, kDescCache at a time, with
-  // one completion counter per staged piece (row groups done).
+  // one mbarrier per staged piece: every thread of the piece's row groups
+  // arrives once its rows are written (32 arrivals per group).
   PieceDesc* dsm = reinterpret_cast<PieceDesc*>(smem + S.vec_bytes);
-  uint32_t* done = reinterpret_cast<uint32_t*>(dsm + kDescCache);
-  volatile uint32_t* abort_flag = done + kDescCache;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(dsm + kDescCache);
+  volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(mbar + kDescCache);
   int win0 = k0;  // first piece of the staged window
   int rot = 0;    // warp that takes row group 0 of the next piece
   for (int k = k0; k < k1; ++k) {
     if ((k - k0) % kDescCache == 0) {
-      if (k > k0) __syncthreads();  // every piece of the window is done
       const int cnt = min(kDescCache, k1 - k);
+      if (k > k0) {
+        __syncthreads();  // every piece of the (full) window is done
+        for (int q = tid; q < kDescCache; q += blockDim.x) mbar_inval(mbar + q);
+      }
       const uint4* src = reinterpret_cast<const uint4*>(S.pieces + cd.piece0 + k);
       uint4* dst = reinterpret_cast<uint4*>(dsm);
       for (int q = tid; q < 2 * cnt; q += blockDim.x) dst[q] = __ldg(src + q);
-      for (int q = tid; q < kDescCache; q += blockDim.x) done[q] = 0;
       if (k == k0 && tid == 0) *abort_flag = 0;
       win0 = k;
+      __syncthreads();
+      for (int q = tid; q < cnt; q += blockDim.x) {
+        // the stuck piece (failure-path tests) expects one arrival too many
+        const uint32_t groups = ((dsm[q].meta & 0xFFFFu) + RPW - 1) / RPW;
+        mbar_init(mbar + q, 32u * groups + (cd.piece0 + k + q == S.wait_stuck ? 1u : 0u));
+      }
       __syncthreads();
     }
     const PieceDesc pd = dsm[k - win0];
@@ -190,8 +199,8 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
     // Row groups (RPW rows each) go to warps round-robin across pieces, so a
     // warp issues the loads of its next group while the pieces before it run
     // on other warps. Without block barriers, a warp waits only for the
-    // previous level's pieces (their completion counters), and only before it
-    // reads the subdomain vector.
+    // previous level's pieces (their mbarriers), and only before it reads the
+    // subdomain vector.
     const int ng = (n + RPW - 1) / RPW;  // <= nwarps (pieces fit the block)
     int g = warp - rot;
     if (g < 0) g += nwarps;
@@ -233,23 +242,22 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
         for (int c = 0; c < BS; ++c) d[c] = gfactor<TF>(gs + (io + (uint32_t)c * cstride));
       }
       const int row = active ? gu16(gs + (pd.off + 2u * (uint32_t)w + trow2)) : 0;
-      // Wait (the whole warp, converged) for the previous level's pieces of
-      // this window; earlier windows are done. Bounded: after
-      // S.wait_polls polls the block gives up and flags the error word.
+      // Wait for the previous level's pieces of this window (earlier windows
+      // are done). Bounded: after S.wait_cycles SM cycles the block gives up
+      // and flags the error word.
       for (int j = max((int)pd.prev_first, win0); j < (int)pd.lvl_first; ++j) {
-        const uint32_t need = ((dsm[j - win0].meta & 0xFFFFu) + RPW - 1) / RPW +
-                              (cd.piece0 + j == S.wait_stuck ? 1u : 0u);
-        const volatile uint32_t* cj = done + (j - win0);
-        uint32_t polls = 0;
-        while (!__all_sync(0xffffffffu, *cj >= need)) {
-          if ((++polls & 255u) == 0 && (__any_sync(0xffffffffu, *abort_flag != 0) || polls >= S.wait_polls)) {
-            if (lane == 0 && atomicCAS(const_cast<uint32_t*>(abort_flag), 0u, 1u) == 0u)
-              atomicCAS(S.err, 0, kErrApplyWait);
-            break;
+        uint64_t* b = mbar + (j - win0);
+        if (!mbar_try_wait(b, 0)) {
+          const long long t0 = clock64();
+          while (!mbar_try_wait(b, 0)) {
+            if (*abort_flag || clock64() - t0 > (long long)S.wait_cycles) {
+              if (atomicCAS(const_cast<uint32_t*>(abort_flag), 0u, 1u) == 0u) atomicCAS(S.err, 0, kErrApplyWait);
+              break;
+            }
           }
         }
       }
-      __threadfence_block();
+      __syncwarp();
       TV acc = active ? y[BS * row + comp] : TV(0);
       if (kind) {
         // D^-1 (Section 4.3): w_i = D_i^-1 y_i; with 3x3 blocks the row's
@@ -291,11 +299,11 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
         y[BS * row + comp] = acc;
       }
       __syncwarp();
-      __threadfence_block();
-      if (lane == 0) atomicAdd(done + (k - win0), 1u);
+      mbar_arrive(mbar + (k - win0));  // every lane: releases its own writes
     }
   }
   __syncthreads();
+  for (int q = tid; q < k1 - win0; q += blockDim.x) mbar_inval(mbar + q);
   for (int e = tid; e < nv; e += blockDim.x) z[base + e] = kDF ? to_double(y[e]) * unscale : to_double(y[e]);
 }
 

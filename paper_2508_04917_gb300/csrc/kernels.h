@@ -33,9 +33,9 @@ struct SysDesc {
   int64_t ntiles, ntiles_pow2;
   int32_t N, nsub;
   int32_t vec_bytes, prefetch_bytes;
-  // apply waits: polls before giving up; a piece (global index) whose
-  // completion count is never reached (-1: none; failure-path tests only)
-  uint32_t wait_polls;
+  // apply waits: SM cycles before giving up; a piece (global index) whose
+  // completion is never reached (-1: none; failure-path tests only)
+  uint64_t wait_cycles;
   int32_t wait_stuck;
 };
 

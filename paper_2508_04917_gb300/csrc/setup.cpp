@@ -389,7 +389,7 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
     *why = "threads_per_cta must be a multiple of 32 in [32, 384]";
     return ILU0DD_ERR_INVALID;
   }
-  p.prefetch_bytes = o->prefetch_bytes > 0 ? o->prefetch_bytes : 65536;
+  p.prefetch_bytes = o->prefetch_bytes > 0 ? o->prefetch_bytes : 32768;
   if (p.prefetch_bytes % 16 || p.prefetch_bytes > (1 << 24)) {
     *why = "prefetch_bytes must be a multiple of 16 up to 16 MiB";
     return ILU0DD_ERR_INVALID;

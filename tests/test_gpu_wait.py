@@ -1,10 +1,10 @@
 """Bounded waits of the apply: the failure path, tested without a GPU fault.
 
-The apply's warps start a level's rows once the previous level's pieces have
-counted all their row groups done (the level order of Section 4.4, with
-completion counters in shared memory instead of block barriers). Every wait
-is bounded. A piece whose completion is never counted (the stuck piece of
-ilu0dd_set_wait_limits) makes each wait on it expire after the poll limit:
+The apply's warps start a level's rows once the previous level's pieces are
+complete (the level order of Section 4.4, with one shared-memory mbarrier per
+piece instead of block barriers). Every wait is bounded. A piece whose
+completion is never reached (the stuck piece of ilu0dd_set_wait_limits, whose
+mbarrier expects one arrival too many) makes each wait on it expire:
 the block stops waiting and finishes, the device error word reads 1, the
 other subdomains' outputs are untouched, bicgstab_solve and the batched solve
 report ILU0DD_ERR_DEVICE_WAIT, and the context stays usable: with the stuck
@@ -44,7 +44,7 @@ def test_stuck_piece_expires_and_context_recovers(bs):
         z_ref = ctx.apply(cu(r))
         assert ctx.device_error() == 0
         # piece 0 = subdomain 0's first L level: the next level waits on it
-        ctx.set_wait_limits(polls=4096, stuck_piece=0)
+        ctx.set_wait_limits(wait_us=200, stuck_piece=0)
         z = ctx.apply(cu(r))
         torch.cuda.synchronize()
         assert ctx.device_error() == 1
@@ -63,7 +63,7 @@ def test_stuck_piece_expires_and_context_recovers(bs):
 def test_stuck_piece_fails_the_solve_then_solves():
     s, ctx = make()
     try:
-        ctx.set_wait_limits(polls=4096, stuck_piece=0)
+        ctx.set_wait_limits(wait_us=200, stuck_piece=0)
         x, info = ctx.solve(cu(s.b), check=False)
         assert info["status"] == B.ERR_DEVICE_WAIT
         assert ctx.device_error() == 1
@@ -82,7 +82,7 @@ def test_stuck_piece_in_a_batch_fails_that_system_only():
     bvec = [cu(s.b) for s, _ in systems]
     try:
         single = ctxs[1].solve(bvec[1])
-        ctxs[0].set_wait_limits(polls=4096, stuck_piece=0)
+        ctxs[0].set_wait_limits(wait_us=200, stuck_piece=0)
         batch = g.Batch(ctxs, maxit=60)  # the failed system iterates on to maxit
         xs, infos = batch.solve(bvec, check=False)
         batch.close()
