@@ -45,7 +45,10 @@ namespace ilu0dd {
 // ---------------------------------------------------------------------------
 constexpr int kRowsPerWarp = 10;
 constexpr int kDescSlots = 3;   // slot counts carried in the descriptor
-constexpr int kDescCache = 128; // piece descriptors staged in shared memory at a time
+// Piece descriptors staged in shared memory at a time: 124 keeps the largest
+// FP64 box that fits (16x16x37 cells, 222 KiB of vector) within 227 KiB with
+// the mbarriers, and a 32x16x16 scalar box (123 pieces) in one window.
+constexpr int kDescCache = 124;
 struct PieceDesc {          // 32 bytes, one per piece, device array
   uint32_t off;             // record start, bytes from the subdomain stream start
   uint32_t meta;            // n | (w << 16) | (kind << 24)
