@@ -91,3 +91,45 @@ def test_batch_rejects_mixed_precision():
                   factor_prec="f32")
     with pytest.raises(g.Ilu0DDError):
         g.Batch([c0, c1])
+
+
+def test_benchmark_batch_workload():
+    """The benchmark's batched workload in full: 64 laplace systems with sides
+    drawn from 24..96 (synth.ragged_batch), FP32 factors, 8x8x8 boxes at 160
+    threads per block (the configuration the autotuner picks on GB300). Every
+    system's batched solution has its single solve's bits and iteration count
+    and a true residual below 1e-8; with FP64 factors the two smallest systems
+    reach the oracle's iteration counts and solutions (1e-12)."""
+    sides = synth.ragged_batch(64)
+    systems = [synth.system(*sd, 5000 + i) for i, sd in enumerate(sides)]
+    ctxs = [g.Ilu0DD(s.row_ptr, s.col, s.val, (s.nx, s.ny, s.nz), (8, 8, 8), factor_prec="f32",
+                     threads_per_cta=160) for s in systems]
+    bs = [torch.from_numpy(s.b).cuda() for s in systems]
+    try:
+        batch = g.Batch(ctxs)
+        xs, infos = batch.solve(bs)
+        batch.close()
+        for c, b, x2, i2 in zip(ctxs, bs, xs, infos):
+            x1, i1 = c.solve(b)
+            assert i2["status"] == 0 and i2["rel_res_true"] < 1e-8
+            assert i2["iterations"] == i1["iterations"] and torch.equal(x1, x2)
+    finally:
+        for c in ctxs:
+            c.close()
+    small = sorted(range(len(systems)), key=lambda i: systems[i].n)[:2]
+    sel = [systems[i] for i in small]
+    ctxs = [g.Ilu0DD(s.row_ptr, s.col, s.val, (s.nx, s.ny, s.nz), (8, 8, 8)) for s in sel]
+    try:
+        batch = g.Batch(ctxs)
+        xs, infos = batch.solve([torch.from_numpy(s.b).cuda() for s in sel])
+        batch.close()
+        for s, x, info in zip(sel, xs, infos):
+            grid = (s.nx, s.ny, s.nz)
+            d = oracle.decompose(s.row_ptr, s.col, s.val, grid, (8, 8, 8))
+            ref = oracle.bicgstab(d.Ap, d.LU, s.b.reshape(-1, 3)[d.perm].reshape(-1))
+            assert info["iterations"] == ref.iterations
+            xo = ref.x.reshape(-1, 3)[d.iperm].reshape(-1)
+            assert np.abs(x.cpu().numpy() - xo).max() <= 1e-12 * np.abs(xo).max()
+    finally:
+        for c in ctxs:
+            c.close()

@@ -9,7 +9,9 @@ whole and bit-exact, the SpMV and the fixed-order dot bit-exact, the FP64 and
 DF64 applies within 1e-12 of the oracle's sequential substitution (FP32 and
 BF16 factors within their storage precision), the iterate after three
 BiCGSTAB iterations within 1e-12 of the oracle's, and the full solve must
-reach a true relative residual below 1e-8.
+reach a true relative residual below 1e-8. The benchmark's other full-size
+legs get the same comparison: the scalar CSR system (8M rows) and the
+unstructured system cut by the breadth-first partitioner.
 """
 import numpy as np
 import pytest
@@ -99,5 +101,46 @@ def test_fullsize_solve_converges(full):
         assert ctx.device_error() == 0
         # the generator's x* solves the system to the conditioning of A
         assert nrel(x.cpu().numpy(), s.xstar) < 1e-3
+    finally:
+        ctx.close()
+
+
+def test_fullsize_scalar_csr():
+    """The benchmark's scalar CSR workload: the 200^3 layered system with 1x1
+    blocks (8M rows, 55.8M nonzeros), 32x16x16 boxes of 8,192 rows."""
+    grid, sub = (200, 200, 200), (32, 16, 16)
+    s = synth.system(*grid, 7, model=synth.MODEL_LAYERED, bs=1)
+    d = oracle.decompose(s.row_ptr, s.col, s.val, grid, sub)
+    ctx = g.Ilu0DD(s.row_ptr, s.col, s.val, grid, sub)
+    try:
+        assert ctx.bs == 1 and ctx.size == s.n
+        for what, ref in [(B.X_PERM, d.perm), (B.X_PART_PTR, d.part_ptr),
+                          (B.X_LEVEL_L, oracle.levels_lower(d.Add)[0]), (B.X_LEVEL_U, oracle.levels_upper(d.Add)[0])]:
+            assert np.array_equal(ctx.export(what), ref), what
+        r = np.random.default_rng(8).uniform(-1, 1, s.n)
+        assert nrel(ctx.apply(cu(r)).cpu().numpy(), oracle.apply(d.LU, r)) <= 1e-12
+        assert np.array_equal(ctx.spmv(cu(r)).cpu().numpy(), oracle.spmv(d.Ap, r))
+        assert ctx.dot(cu(r), cu(r)).item() == oracle.dot(r, r, bs=1)
+    finally:
+        ctx.close()
+
+
+def test_fullsize_unstructured_partition():
+    """The benchmark's unstructured workload: 2.1M cells of a renumbered 128^3
+    grid with an irregular 27-point pattern, cut into 2,048-row parts by the
+    breadth-first partitioner (library and oracle give the same labels)."""
+    s = synth.unstructured(128, 128, 128, 6)
+    part, nparts = g.partition_bfs(s.row_ptr, s.col, 2048)
+    opart, onparts = oracle.partition_bfs(s.row_ptr, s.col, 2048)
+    assert nparts == onparts and np.array_equal(part, opart)
+    d = oracle.decompose_labeled(s.row_ptr, s.col, s.val, opart, onparts)
+    ctx = g.Ilu0DD(s.row_ptr, s.col, s.val, part_id=part, nparts=nparts)
+    try:
+        for what, ref in [(B.X_PERM, d.perm), (B.X_PART_PTR, d.part_ptr),
+                          (B.X_LEVEL_L, oracle.levels_lower(d.Add)[0]), (B.X_LEVEL_U, oracle.levels_upper(d.Add)[0])]:
+            assert np.array_equal(ctx.export(what), ref), what
+        r = np.random.default_rng(9).uniform(-1, 1, 3 * s.n)
+        assert nrel(ctx.apply(cu(r)).cpu().numpy(), oracle.apply(d.LU, r)) <= 1e-12
+        assert np.array_equal(ctx.spmv(cu(r)).cpu().numpy(), oracle.spmv(d.Ap, r))
     finally:
         ctx.close()
