@@ -276,7 +276,7 @@ def run_ours(args):
     e2e = {"value": round(world * apply_b / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
            "h2d_bytes_per_step": 24 * n, "d2h_bytes_per_step": 24 * n, "ms_per_step": round(e2e_ms, 5),
            "what": "ilu0_dd_apply_host: r from pinned host memory, z back to it, every step "
-                   "(copies and applies pipelined over 8 chunks of subdomains)"}
+                   "(copies and applies pipelined over 16 chunks of subdomains)"}
     ctx.close()
     del ctx
 

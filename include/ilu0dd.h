@@ -215,7 +215,7 @@ int ilu0_dd_apply(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* s
  * z = M^-1 r as ilu0_dd_apply, from and to HOST buffers: h_r, h_z hold 3*N
  * doubles in the reordered numbering (page-locked memory lets the copies
  * overlap; pageable memory works but serialises them). The subdomains are
- * split into up to eight contiguous chunks (subdomains are independent:
+ * split into up to sixteen contiguous chunks (subdomains are independent:
  * Section 3.2), each copied in, applied and copied out on its own stream of
  * the context, so one chunk's copies overlap other chunks' applies. Work is
  * ordered after earlier work on `stream`, and `stream` waits for all of it;

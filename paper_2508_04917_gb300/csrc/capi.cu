@@ -377,7 +377,7 @@ int ilu0_dd_apply_host(ilu0dd_ctx* ctx, const double* h_r, double* h_z, void* st
   if (!ctx || (ctx->plan.N > 0 && (!h_r || !h_z))) return ILU0DD_ERR_INVALID;
   const Plan& p = ctx->plan;
   if (p.N == 0) return ILU0DD_OK;
-  constexpr int kChunks = 8;
+  constexpr int kChunks = 16;
   const int nch = std::min(kChunks, p.nsub);
   if ((int)ctx->hstreams.size() != nch) {
     for (cudaStream_t x : ctx->hstreams) cudaStreamDestroy(x);
