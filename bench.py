@@ -314,11 +314,21 @@ def run_ours(args):
             u1.record()
             torch.cuda.synchronize()
             ums = u0.elapsed_time(u1) / 20
+            # synchronization ablation: per-row flags (Algorithm 4) instead of the level order
+            for _ in range(3):
+                c.apply_rowsync(r, zp)
+            u0.record()
+            for _ in range(20):
+                c.apply_rowsync(r, zp)
+            u1.record()
+            torch.cuda.synchronize()
+            rms = u0.elapsed_time(u1) / 20
             solves[prec] = {"s": round(wall, 5), "iterations": info["iterations"], "restarts": info["restarts"],
                             "rel_res_true": info["rel_res_true"], "setup_s": round(su, 3),
                             "max_rel_err_vs_xstar": err, "status": info["status"],
                             "apply_ms": round(ams, 5), "apply_unfused_ms": round(ums, 5),
-                            "fusion_speedup": round(ums / ams, 3), "apply_bytes": c.query("apply_bytes"),
+                            "fusion_speedup": round(ums / ams, 3), "apply_rowsync_ms": round(rms, 5),
+                            "apply_bytes": c.query("apply_bytes"),
                             "apply_gbs": round(c.query("apply_bytes") / ams / 1e6, 1)}
             c.close()
         if "f64" in solves:
@@ -442,16 +452,17 @@ def _events():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def time_apply_warm(ctx, r, z, reps):
+def time_apply_warm(ctx, r, z, reps, fn=None):
     """Mean apply time (ms) over `reps` back-to-back applies (L2-warm when the
-    factors fit in L2)."""
+    factors fit in L2); `fn` picks another apply entry point of the context."""
     import torch
+    fn = fn or ctx.apply
     for _ in range(3):
-        ctx.apply(r, z)
+        fn(r, z)
     e0, e1 = _events()
     e0.record()
     for _ in range(reps):
-        ctx.apply(r, z)
+        fn(r, z)
     e1.record()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
@@ -600,12 +611,13 @@ def run_unstructured(dev, cells=(128, 128, 128), part_rows=2048, reps=20):
             torch.cuda.synchronize()
             su = time.perf_counter() - t0
             ams = time_apply_warm(ctx, r, z, reps)
+            rms = time_apply_warm(ctx, r, z, reps, ctx.apply_rowsync)
             sec, x, info = timed_solve(ctx, b)
             xs = torch.from_numpy(s.xstar).to(dev)
             out[f"{name}_{prec}"] = {
                 "setup_s": round(su, 3),
                 "dropped_blocks_pct": round(100.0 * (1 - ctx.query("kept") / ctx.query("nnzb")), 2),
-                "apply_ms": round(ams, 5), "apply_bytes": ctx.query("apply_bytes"),
+                "apply_ms": round(ams, 5), "apply_rowsync_ms": round(rms, 5), "apply_bytes": ctx.query("apply_bytes"),
                 "apply_gbs": round(ctx.query("apply_bytes") / ams / 1e6, 1), "iterations": info["iterations"],
                 "solve_s": round(sec, 5), "status": info["status"],
                 "max_rel_err_vs_xstar": float((x - xs).abs().max() / xs.abs().max())}
@@ -633,11 +645,12 @@ def run_scalar(dev, grid=(200, 200, 200), sub=(32, 16, 16), reps=20):
         torch.cuda.synchronize()
         su = time.perf_counter() - t0
         ams = time_apply_warm(ctx, r, z, reps)
+        rms = time_apply_warm(ctx, r, z, reps, ctx.apply_rowsync)
         sec, x, info = timed_solve(ctx, b)
         xs = torch.from_numpy(s.xstar).to(dev)
         out[prec] = {"setup_s": round(su, 3), "threads": ctx.query("threads"),
                      "dropped_pct": round(100.0 * (1 - ctx.query("kept") / ctx.query("nnzb")), 2),
-                     "apply_ms": round(ams, 5), "apply_bytes": ctx.query("apply_bytes"),
+                     "apply_ms": round(ams, 5), "apply_rowsync_ms": round(rms, 5), "apply_bytes": ctx.query("apply_bytes"),
                      "apply_gbs": round(ctx.query("apply_bytes") / ams / 1e6, 1), "iterations": info["iterations"],
                      "solve_s": round(sec, 5), "status": info["status"],
                      "max_rel_err_vs_xstar": float((x - xs).abs().max() / xs.abs().max())}

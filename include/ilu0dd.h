@@ -237,6 +237,20 @@ int ilu0_dd_apply_host(ilu0dd_ctx* ctx, const double* h_r, double* h_z, void* st
 int ilu0_dd_apply_unfused(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream);
 
 /*
+ * The same z = M^-1 r as ilu0_dd_apply with the synchronization of the
+ * paper's synchronization-free triangular solve (Algorithm 4) in place of the
+ * level order: one completion flag per row in shared memory, and each row
+ * waits (spinning, bounded like every wait of the apply) for exactly the rows
+ * it reads instead of for the whole previous level; the L and U sweeps are
+ * separated by one block barrier. Same arguments; results bit-identical to
+ * ilu0_dd_apply (each row's arithmetic and its order are unchanged). For the
+ * synchronization ablation. Returns ILU0DD_ERR_SMEM when the subdomain vector
+ * plus one flag byte per row does not fit in shared memory (the largest
+ * boxes), ILU0DD_ERR_INVALID for overlapping r and z.
+ */
+int ilu0_dd_apply_rowsync(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream);
+
+/*
  * y = A_p x with the full reordered matrix (all inter-subdomain blocks kept,
  * Section 3.2 last paragraph). Device vectors in the reordered numbering,
  * 3*N doubles each, not overlapping. Asynchronous on `stream`.

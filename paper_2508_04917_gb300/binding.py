@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "ilu0dd_partition_bfs": ([ctypes.POINTER(Bsr), i32, vp, ctypes.POINTER(i32)], ctypes.c_int),
             "ilu0_dd_apply": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_apply_unfused": ([vp, vp, vp, vp], ctypes.c_int),
+            "ilu0_dd_apply_rowsync": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_apply_host": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_spmv": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_dot": ([vp, vp, vp, vp, vp], ctypes.c_int),
@@ -330,6 +331,14 @@ class Ilu0DD:
                                                  ctypes.c_void_p(host_ptr(z, "z")), st), "ilu0_dd_apply_host")
         if sync:
             (torch.cuda.current_stream() if stream is None else stream).synchronize()
+        return z
+
+    def apply_rowsync(self, r, z=None, stream=None):
+        """z = M^-1 r with per-row completion flags (Algorithm 4's
+        synchronization) instead of the level order; same bits as apply()."""
+        z = self._new() if z is None else z
+        self._check(self._lib.ilu0_dd_apply_rowsync(self._ctx, _dptr(r, self.size, "r"), _dptr(z, self.size, "z"),
+                                                    _stream(stream)), "ilu0_dd_apply_rowsync")
         return z
 
     def apply_unfused(self, r, z=None, stream=None):

@@ -146,6 +146,7 @@ int setup_numeric(ilu0dd_ctx* c, const ilu0dd_bsr* A, const ilu0dd_opts& o, void
     }
     if (e == cudaSuccess) e = up(L.perm, p.perm.data(), sizeof(int32_t) * p.perm.size());
     if (e == cudaSuccess) e = up(L.iperm, p.iperm.data(), sizeof(int32_t) * p.iperm.size());
+    if (e == cudaSuccess) e = up(L.row_l0, p.row_l0.data(), p.row_l0.size());
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.partials, 0, sizeof(double) * 5 * (size_t)p.ntiles_pow2, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.counters, 0, sizeof(uint32_t) * 16, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.scal, 0, sizeof(SolverScalars), s);
@@ -172,6 +173,7 @@ int setup_numeric(ilu0dd_ctx* c, const ilu0dd_bsr* A, const ilu0dd_opts& o, void
     S.sell_val = reinterpret_cast<const double*>(c->ws + L.sell_val);
     S.nslices = p.nslices;
     S.perm = reinterpret_cast<const int32_t*>(c->ws + L.perm);
+    S.row_l0 = c->ws + L.row_l0;
     S.iperm = reinterpret_cast<const int32_t*>(c->ws + L.iperm);
     S.N = p.N;
     S.ntiles = p.ntiles;
@@ -185,6 +187,7 @@ int setup_numeric(ilu0dd_ctx* c, const ilu0dd_bsr* A, const ilu0dd_opts& o, void
     d.threads = p.threads;
     d.factor_prec = o.factor_prec;
     d.smem_bytes = p.smem_bytes;
+    d.smem_rowsync = p.smem_rowsync;
     d.bs = p.bs;
     e = apply_configure(d);
     if (e == cudaSuccess) e = set_wait_us(c, kApplyWaitUs);
@@ -403,6 +406,18 @@ int ilu0_dd_apply_host(ilu0dd_ctx* ctx, const double* h_r, double* h_z, void* st
     CK(ctx, cudaEventRecord(ctx->hevents[1 + i], cs));
   }
   for (int i = 0; i < nch; ++i) CK(ctx, cudaStreamWaitEvent(s, ctx->hevents[1 + i], 0));
+  return ILU0DD_OK;
+}
+
+int ilu0_dd_apply_rowsync(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream) {
+  if (!ctx || (ctx->plan.N > 0 && (!d_r || !d_z))) return ILU0DD_ERR_INVALID;
+  const size_t n = (size_t)ctx->plan.bs * (size_t)ctx->plan.N * sizeof(double);
+  const char* r = reinterpret_cast<const char*>(d_r);
+  const char* z = reinterpret_cast<const char*>(d_z);
+  if (r < z + n && z < r + n) return ILU0DD_ERR_INVALID;  // overlapping vectors
+  if (ctx->plan.N > 0 && ctx->dev.smem_rowsync == 0) return ILU0DD_ERR_SMEM;
+  cudaError_t e = launch_apply_rowsync(ctx->dev, d_r, d_z, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(const_cast<ilu0dd_ctx*>(ctx), e, "row-flag apply launch");
   return ILU0DD_OK;
 }
 

@@ -171,6 +171,8 @@ struct Plan {
   int factor_prec = ILU0DD_F64;
   int rmax = 0, max_pieces = 0;
   size_t smem_bytes = 0;
+  size_t smem_rowsync = 0;                        // row-flag apply: + one byte per row (0: does not fit)
+  std::vector<uint8_t> row_l0;                    // 1 for rows without a strictly-lower block (L level 0)
   int64_t n_pieces = 0;
   std::vector<CtaDesc> cta;
   std::vector<PieceDesc> pieces;
@@ -182,7 +184,7 @@ struct Plan {
   std::vector<int32_t> slice_off;                 // [nslices+1] prefix of widths
   // workspace layout (byte offsets)
   struct Layout {
-    size_t stream, cta, pieces, sell_off, sell_col, sell_val, perm, iperm;
+    size_t stream, cta, pieces, sell_off, sell_col, sell_val, perm, iperm, row_l0;
     size_t vec[kNumVec];
     size_t partials, counters, scal, hist, err, total;
   } lay{};

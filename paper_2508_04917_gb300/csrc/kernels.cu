@@ -79,7 +79,7 @@ __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 // D^-1 and U~ sweep (the two launches of the unfused apply). BS = block
 // dimension: 3 (three threads per block row, ten rows per warp) or 1 (scalar
 // CSR: one thread per row, 32 rows per warp).
-template <typename TF, int MODE, int PART = 0, int BS = 3>
+template <typename TF, int MODE, int PART = 0, int BS = 3, int SYNC = 0>
 __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const double* r, double* z) {
   static_assert(BS == 1 || BS == 3, "block dimension 1 or 3");
   constexpr int RPW = BS == 3 ? kRowsPerWarp : 32;  // rows per warp
@@ -155,6 +155,12 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
     unscale = ldexp(1.0, k);
     for (int e = tid; e < nv; e += blockDim.x) y[e] = df_from_double(reinterpret_cast<double*>(y)[e] * scale);
   }
+  // SYNC 1 (Algorithm 4's synchronization): one flag per row, 1 once the
+  // row's L result is in the vector (at once for rows of L level 0), 2 once
+  // its final value is.
+  volatile uint8_t* rflag = smem + S.vec_bytes + kApplyTailSmem;
+  if constexpr (SYNC == 1)
+    for (int e = tid; e < cd.nrows; e += blockDim.x) rflag[e] = S.row_l0[cd.row0 + e];
   __syncthreads();
 
   const int warp = tid >> 5, lane = tid & 31;
@@ -172,11 +178,17 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
   int win0 = k0;  // first piece of the staged window
   int rot = 0;    // warp that takes row group 0 of the next piece
   for (int k = k0; k < k1; ++k) {
+    // Row flags order only the reads of each row; the U sweep overwrites L
+    // results that rows of the L sweep may still read (for unsymmetric
+    // patterns), so with SYNC 1 the sweeps are separated by a barrier.
+    if constexpr (SYNC == 1)
+      if (k == cd.npieces_l && k > k0 && (k - k0) % kDescCache != 0) __syncthreads();
     if ((k - k0) % kDescCache == 0) {
       const int cnt = min(kDescCache, k1 - k);
       if (k > k0) {
         __syncthreads();  // every piece of the (full) window is done
-        for (int q = tid; q < kDescCache; q += blockDim.x) mbar_inval(mbar + q);
+        if constexpr (SYNC == 0)
+          for (int q = tid; q < kDescCache; q += blockDim.x) mbar_inval(mbar + q);
       }
       const uint4* src = reinterpret_cast<const uint4*>(S.pieces + cd.piece0 + k);
       uint4* dst = reinterpret_cast<uint4*>(dsm);
@@ -184,12 +196,14 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
       if (k == k0 && tid == 0) *abort_flag = 0;
       win0 = k;
       __syncthreads();
-      for (int q = tid; q < cnt; q += blockDim.x) {
-        // the stuck piece (failure-path tests) expects one arrival too many
-        const uint32_t groups = ((dsm[q].meta & 0xFFFFu) + RPW - 1) / RPW;
-        mbar_init(mbar + q, 32u * groups + (cd.piece0 + k + q == S.wait_stuck ? 1u : 0u));
+      if constexpr (SYNC == 0) {
+        for (int q = tid; q < cnt; q += blockDim.x) {
+          // the stuck piece (failure-path tests) expects one arrival too many
+          const uint32_t groups = ((dsm[q].meta & 0xFFFFu) + RPW - 1) / RPW;
+          mbar_init(mbar + q, 32u * groups + (cd.piece0 + k + q == S.wait_stuck ? 1u : 0u));
+        }
+        __syncthreads();
       }
-      __syncthreads();
     }
     const PieceDesc pd = dsm[k - win0];
     if (pf_thread) prefetch_upto(pd.off + dist);
@@ -242,20 +256,53 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
         for (int c = 0; c < BS; ++c) d[c] = gfactor<TF>(gs + (io + (uint32_t)c * cstride));
       }
       const int row = active ? gu16(gs + (pd.off + 2u * (uint32_t)w + trow2)) : 0;
-      // Wait for the previous level's pieces of this window (earlier windows
-      // are done). Bounded: after S.wait_cycles SM cycles the block gives up
-      // and flags the error word.
-      for (int j = max((int)pd.prev_first, win0); j < (int)pd.lvl_first; ++j) {
-        uint64_t* b = mbar + (j - win0);
-        if (!mbar_try_wait(b, 0)) {
-          const long long t0 = clock64();
-          while (!mbar_try_wait(b, 0)) {
-            if (*abort_flag || clock64() - t0 > (long long)S.wait_cycles) {
-              if (atomicCAS(const_cast<uint32_t*>(abort_flag), 0u, 1u) == 0u) atomicCAS(S.err, 0, kErrApplyWait);
-              break;
+      if constexpr (SYNC == 0) {
+        // Wait for the previous level's pieces of this window (earlier
+        // windows are done). Bounded: after S.wait_cycles SM cycles the block
+        // gives up and flags the error word.
+        for (int j = max((int)pd.prev_first, win0); j < (int)pd.lvl_first; ++j) {
+          uint64_t* b = mbar + (j - win0);
+          if (!mbar_try_wait(b, 0)) {
+            const long long t0 = clock64();
+            while (!mbar_try_wait(b, 0)) {
+              if (*abort_flag || clock64() - t0 > (long long)S.wait_cycles) {
+                if (atomicCAS(const_cast<uint32_t*>(abort_flag), 0u, 1u) == 0u) atomicCAS(S.err, 0, kErrApplyWait);
+                break;
+              }
             }
           }
         }
+      } else {
+        // Algorithm 4: wait (spin, bounded) for exactly the rows this row
+        // reads: its own L result in the U sweep, then each slot's column.
+        if (active) {
+          const uint8_t phase = kind ? 2 : 1;
+          auto wait_row = [&](int rr, uint8_t ph) {
+            if (rflag[rr] >= ph) return;
+            const long long t0 = clock64();
+            while (rflag[rr] < ph) {
+              if (*abort_flag || clock64() - t0 > (long long)S.wait_cycles) {
+                if (atomicCAS(const_cast<uint32_t*>(abort_flag), 0u, 1u) == 0u) atomicCAS(S.err, 0, kErrApplyWait);
+                return;
+              }
+            }
+          };
+          if (kind) wait_row(row, 1);
+#pragma unroll
+          for (int sl = 0; sl < kDescSlots; ++sl)
+            if (sl < nsl) wait_row(col[sl], phase);
+          // further slots of general patterns: their columns come from the record
+          if (w > kDescSlots && nsl == kDescSlots) {
+            uint32_t cc = (uint32_t)pd.cnt[0] + pd.cnt[1] + pd.cnt[2];
+            for (int sl = kDescSlots; sl < w; ++sl) {
+              const uint32_t cs = (uint32_t)gu16(rec + 2 * sl);
+              if ((uint32_t)trow >= cs) break;
+              wait_row(gu16(gs + (cbase + 2u * cc + trow2)), phase);
+              cc += cs;
+            }
+          }
+        }
+        __threadfence_block();
       }
       __syncwarp();
       TV acc = active ? y[BS * row + comp] : TV(0);
@@ -299,11 +346,18 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
         y[BS * row + comp] = acc;
       }
       __syncwarp();
-      mbar_arrive(mbar + (k - win0));  // every lane: releases its own writes
+      if constexpr (SYNC == 0) {
+        mbar_arrive(mbar + (k - win0));  // every lane: releases its own writes
+      } else {
+        __threadfence_block();
+        __syncwarp();
+        if (active && comp == 0) rflag[row] = kind ? 2 : 1;
+      }
     }
   }
   __syncthreads();
-  for (int q = tid; q < k1 - win0; q += blockDim.x) mbar_inval(mbar + q);
+  if constexpr (SYNC == 0)
+    for (int q = tid; q < k1 - win0; q += blockDim.x) mbar_inval(mbar + q);
   for (int e = tid; e < nv; e += blockDim.x) z[base + e] = kDF ? to_double(y[e]) * unscale : to_double(y[e]);
 }
 
@@ -314,6 +368,15 @@ template <typename TF, int MODE, int BS>
 __global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
     ildu0_apply_kernel(SysDesc S, const double* r, double* z, int sub0) {
   apply_block<TF, MODE, 0, BS>(S, sub0 + blockIdx.x, r, z);
+}
+
+// The plain apply with Algorithm 4's synchronization (row flags, bounded
+// spin loops) instead of the per-level mbarriers: the same arithmetic in the
+// same order, for the synchronization ablation.
+template <typename TF, int BS>
+__global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
+    ildu0_apply_rowsync_kernel(SysDesc S, const double* r, double* z) {
+  apply_block<TF, kModePlain, 0, BS, 1>(S, blockIdx.x, r, z);
 }
 
 // The unfused apply's two launches (plain mode): PART 1 = L sweep, r -> z;
@@ -355,6 +418,10 @@ static cudaError_t configure_one(size_t smem) {
       e = cudaFuncSetAttribute(ildu0_apply_part_kernel<TF, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(ildu0_apply_part_kernel<TF, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ildu0_apply_rowsync_kernel<TF, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ildu0_apply_rowsync_kernel<TF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   }
   return e;
 }
@@ -449,6 +516,25 @@ static cudaError_t launch_apply_batched_tb(const SysDesc* sys, const BatchItem* 
   else
     ildu0_apply_batched<TF, kModeS, BS><<<grid, threads, smem, s>>>(sys, items, nitems);
   return cudaGetLastError();
+}
+
+template <typename TF, int BS>
+static cudaError_t launch_rowsync_tb(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
+  ildu0_apply_rowsync_kernel<TF, BS><<<d.sd.nsub, d.threads, d.smem_rowsync, s>>>(d.sd, r, z);
+  return cudaGetLastError();
+}
+
+template <typename TF>
+static cudaError_t launch_rowsync_t(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
+  return d.bs == 1 ? launch_rowsync_tb<TF, 1>(d, r, z, s) : launch_rowsync_tb<TF, 3>(d, r, z, s);
+}
+
+cudaError_t launch_apply_rowsync(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
+  if (d.sd.nsub == 0) return cudaSuccess;
+  if (d.factor_prec == ILU0DD_F64) return launch_rowsync_t<double>(d, r, z, s);
+  if (d.factor_prec == ILU0DD_F32) return launch_rowsync_t<float>(d, r, z, s);
+  if (d.factor_prec == ILU0DD_DF64) return launch_rowsync_t<df64s>(d, r, z, s);
+  return launch_rowsync_t<bf16s>(d, r, z, s);
 }
 
 template <typename TF>

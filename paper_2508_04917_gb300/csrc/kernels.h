@@ -23,6 +23,7 @@ struct SysDesc {
   // permutation
   const int32_t* perm;
   const int32_t* iperm;
+  const uint8_t* row_l0;  // 1 for rows of L level 0 (the row-flag apply's initial flags)
   // solver state
   double* vec[kNumVec];
   double* partials;     // 5 arrays of ntiles_pow2
@@ -44,6 +45,7 @@ struct DevCtx {
   SysDesc sd;
   int threads, factor_prec;
   size_t smem_bytes;
+  size_t smem_rowsync;  // shared memory of the row-flag apply (0: does not fit)
   int bs = 3;  // block dimension: 3 or 1 (scalar CSR)
 };
 
@@ -66,6 +68,9 @@ cudaError_t launch_apply_range(const DevCtx& d, int mode, const double* r, doubl
 // The same z = M^-1 r in two launches (L sweep r -> z, then D^-1 and U~ sweep
 // z -> z in place), the unfused variant of the fusion ablation.
 cudaError_t launch_apply_unfused(const DevCtx& d, const double* r, double* z, cudaStream_t s);
+// The plain apply with per-row completion flags (Algorithm 4's
+// synchronization) instead of per-level mbarriers; d.smem_rowsync must be > 0.
+cudaError_t launch_apply_rowsync(const DevCtx& d, const double* r, double* z, cudaStream_t s);
 
 // y = A_p x; kind 0 plain, 1: v = A ph with (rh.v) -> alpha, 2: t = A sh with (t.s),(t.t) -> omega.
 cudaError_t launch_spmv(const DevCtx& d, int kind, const double* x, double* y, cudaStream_t s);

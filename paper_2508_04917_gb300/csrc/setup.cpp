@@ -540,6 +540,12 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
            " B of shared memory per block";
     return ILU0DD_ERR_SMEM;
   }
+  // the row-flag apply (Algorithm 4's synchronization) adds one byte per row;
+  // 0 when that does not fit
+  p.smem_rowsync = p.smem_bytes + (size_t)align_up(p.rmax, 16);
+  if ((int64_t)p.smem_rowsync > (int64_t)max_smem - kApplyStaticSmem) p.smem_rowsync = 0;
+  p.row_l0.resize((size_t)N);
+  parallel_for(N, [&](int64_t i) { p.row_l0[i] = p.lev_l[i] == 0 ? 1 : 0; });
 
   tmark("pieces");
   // ---- sliced ELL for the SpMV
@@ -575,6 +581,7 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   L.sell_val = take(sizeof(double) * bs * bs * (size_t)p.sell_slots * kSlice);
   L.perm = take(sizeof(int32_t) * (size_t)N);
   L.iperm = take(sizeof(int32_t) * (size_t)N);
+  L.row_l0 = take((size_t)N);
   for (int v = 0; v < kNumVec; ++v) L.vec[v] = take(sizeof(double) * bs * (size_t)N);
   L.partials = take(sizeof(double) * 5 * (size_t)p.ntiles_pow2);
   L.counters = take(sizeof(uint32_t) * 16);
