@@ -323,11 +323,14 @@ def run_ours(args):
             u1.record()
             torch.cuda.synchronize()
             rms = u0.elapsed_time(u1) / 20
+            # traversal ablation: edge-centric (one thread per block, atomics); no DF64 form
+            ems = time_apply_warm(c, r, zp, 20, c.apply_edge) if prec != "df64" else None
             solves[prec] = {"s": round(wall, 5), "iterations": info["iterations"], "restarts": info["restarts"],
                             "rel_res_true": info["rel_res_true"], "setup_s": round(su, 3),
                             "max_rel_err_vs_xstar": err, "status": info["status"],
                             "apply_ms": round(ams, 5), "apply_unfused_ms": round(ums, 5),
                             "fusion_speedup": round(ums / ams, 3), "apply_rowsync_ms": round(rms, 5),
+                            "apply_edge_ms": None if ems is None else round(ems, 5),
                             "apply_bytes": c.query("apply_bytes"),
                             "apply_gbs": round(c.query("apply_bytes") / ams / 1e6, 1)}
             c.close()

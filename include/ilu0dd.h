@@ -91,7 +91,7 @@ typedef struct {
 
 typedef struct {
   int32_t factor_prec;      /* ILU0DD_F64 / ILU0DD_F32 / ILU0DD_BF16 / ILU0DD_DF64 */
-  int32_t threads_per_cta;  /* apply block size; 0 = 32 per ten rows of the widest level (<= 384) */
+  int32_t threads_per_cta;  /* apply block size; 0 = one warp per row group of the widest level, 1.5x for FP64/DF64 (<= 384) */
   int32_t prefetch_bytes;   /* apply: L2 prefetch distance per block, bytes (multiple of 16); 0 = 32768 */
   int32_t maxit;            /* BiCGSTAB iteration limit; 0 = 10000 */
   double rtol;              /* stop when ||r||_2/||b||_2 < rtol; 0 = 1e-8 */
@@ -249,6 +249,18 @@ int ilu0_dd_apply_unfused(const ilu0dd_ctx* ctx, const double* d_r, double* d_z,
  * boxes), ILU0DD_ERR_INVALID for overlapping r and z.
  */
 int ilu0_dd_apply_rowsync(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream);
+
+/*
+ * The same z = M^-1 r as ilu0_dd_apply with the paper's edge-centric
+ * traversal (Section 4.2.3) in place of the row-wise one: within each level
+ * one thread per block forms that block's product and subtracts it from its
+ * row with shared-memory atomic adds (after the row's D^-1 step in the U
+ * sweep). The row sums are rounded in a different order, so results agree
+ * with ilu0_dd_apply to rounding, not bit for bit. For the traversal
+ * ablation; FP64, FP32 and BF16 factors (ILU0DD_ERR_INVALID for DF64, whose
+ * float pairs have no atomic add, and for overlapping r and z).
+ */
+int ilu0_dd_apply_edge(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream);
 
 /*
  * y = A_p x with the full reordered matrix (all inter-subdomain blocks kept,

@@ -103,6 +103,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "ilu0_dd_apply": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_apply_unfused": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_apply_rowsync": ([vp, vp, vp, vp], ctypes.c_int),
+            "ilu0_dd_apply_edge": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_apply_host": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_spmv": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_dot": ([vp, vp, vp, vp, vp], ctypes.c_int),
@@ -339,6 +340,14 @@ class Ilu0DD:
         z = self._new() if z is None else z
         self._check(self._lib.ilu0_dd_apply_rowsync(self._ctx, _dptr(r, self.size, "r"), _dptr(z, self.size, "z"),
                                                     _stream(stream)), "ilu0_dd_apply_rowsync")
+        return z
+
+    def apply_edge(self, r, z=None, stream=None):
+        """z = M^-1 r with the edge-centric traversal (one thread per block,
+        shared-memory atomics); equal to apply() to rounding."""
+        z = self._new() if z is None else z
+        self._check(self._lib.ilu0_dd_apply_edge(self._ctx, _dptr(r, self.size, "r"), _dptr(z, self.size, "z"),
+                                                 _stream(stream)), "ilu0_dd_apply_edge")
         return z
 
     def apply_unfused(self, r, z=None, stream=None):

@@ -79,7 +79,7 @@ __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 // D^-1 and U~ sweep (the two launches of the unfused apply). BS = block
 // dimension: 3 (three threads per block row, ten rows per warp) or 1 (scalar
 // CSR: one thread per row, 32 rows per warp).
-template <typename TF, int MODE, int PART = 0, int BS = 3, int SYNC = 0>
+template <typename TF, int MODE, int PART = 0, int BS = 3, int SYNC = 0, int TRAV = 0>
 __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const double* r, double* z) {
   static_assert(BS == 1 || BS == 3, "block dimension 1 or 3");
   constexpr int RPW = BS == 3 ? kRowsPerWarp : 32;  // rows per warp
@@ -234,18 +234,47 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
       TV bv[kDescSlots][BS];
       uint32_t c0 = 0;
       int nsl = 0;
+      if constexpr (TRAV == 0) {
 #pragma unroll
-      for (int sl = 0; sl < kDescSlots; ++sl) {
-        const uint32_t cs = pd.cnt[sl];  // 0 beyond w
-        const bool has = active && sl < w && (uint32_t)trow < cs;
-        nsl += has;
-        col[sl] = has ? gu16(gs + (cbase + 2u * c0 + trow2)) : 0;
-        const uint32_t vo = vbase + (uint32_t)(BS * BS) * FE * c0 + lane_voff;
-        const uint32_t cstride = (uint32_t)BS * FE * cs;
+        for (int sl = 0; sl < kDescSlots; ++sl) {
+          const uint32_t cs = pd.cnt[sl];  // 0 beyond w
+          const bool has = active && sl < w && (uint32_t)trow < cs;
+          nsl += has;
+          col[sl] = has ? gu16(gs + (cbase + 2u * c0 + trow2)) : 0;
+          const uint32_t vo = vbase + (uint32_t)(BS * BS) * FE * c0 + lane_voff;
+          const uint32_t cstride = (uint32_t)BS * FE * cs;
 #pragma unroll
-        for (int c = 0; c < BS; ++c) bv[sl][c] = has ? gfactor<TF>(gs + (vo + (uint32_t)c * cstride)) : TV(0);
-        c0 += cs;
+          for (int c = 0; c < BS; ++c) bv[sl][c] = has ? gfactor<TF>(gs + (vo + (uint32_t)c * cstride)) : TV(0);
+          c0 += cs;
+        }
       }
+      // Edge-centric traversal (TRAV 1): the group's blocks are tasks
+      // (slot, row in group), task = 32 * round + lane; round 0's block is
+      // loaded here, ahead of the wait.
+      int e_row = 0, e_col = 0;
+      TV ev[BS][BS];
+      bool e_has = false;
+      auto edge_task = [&](int task, int& rrow, int& rcol, TV (&v)[BS][BS]) -> bool {
+        const int sl = task / RPW, t = task % RPW;
+        const int tr = g * RPW + t;
+        if (sl >= w) return false;
+        uint32_t cc = 0, cs = 0;
+        for (int q = 0; q <= sl; ++q) {
+          cs = q < kDescSlots ? (uint32_t)pd.cnt[q] : (uint32_t)gu16(rec + 2 * q);
+          if (q < sl) cc += cs;
+        }
+        if ((uint32_t)tr >= cs) return false;
+        rrow = gu16(gs + (pd.off + 2u * (uint32_t)w + 2u * (uint32_t)tr));
+        rcol = gu16(gs + (cbase + 2u * (cc + (uint32_t)tr)));
+        const uint32_t vo = vbase + (uint32_t)(BS * BS) * FE * cc;
+#pragma unroll
+        for (int a = 0; a < BS; ++a)
+#pragma unroll
+          for (int c = 0; c < BS; ++c)
+            v[a][c] = gfactor<TF>(gs + (vo + (((uint32_t)c * cs + (uint32_t)tr) * BS + (uint32_t)a) * FE));
+        return true;
+      };
+      if constexpr (TRAV == 1) e_has = edge_task(lane, e_row, e_col, ev);
       TV d[BS];
 #pragma unroll
       for (int c = 0; c < BS; ++c) d[c] = TV(0);
@@ -321,7 +350,27 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
           if (active) acc = d[0] * acc;
         }
       }
-      if (active) {
+      if constexpr (TRAV == 1) {
+        // the D^-1 result first (it is what the U blocks subtract from), then
+        // each task subtracts its block's product with shared-memory atomics
+        if (kind && active) y[BS * row + comp] = acc;
+        __syncwarp();
+        auto edge_apply = [&](int rrow, int rcol, const TV (&v)[BS][BS]) {
+#pragma unroll
+          for (int a = 0; a < BS; ++a) {
+            TV p = v[a][0] * y[BS * rcol];
+#pragma unroll
+            for (int c = 1; c < BS; ++c) p = mac(v[a][c], y[BS * rcol + c], p);
+            atomicAdd(&y[BS * rrow + a], -p);
+          }
+        };
+        if (e_has) edge_apply(e_row, e_col, ev);
+        for (int base_t = 32; base_t < RPW * w; base_t += 32) {  // further rounds (warp-uniform)
+          int rr, rc;
+          TV v[BS][BS];
+          if (edge_task(base_t + lane, rr, rc, v)) edge_apply(rr, rc, v);
+        }
+      } else if (active) {
 #pragma unroll
         for (int sl = 0; sl < kDescSlots; ++sl) {
           if (sl < nsl) {
@@ -379,6 +428,15 @@ __global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
   apply_block<TF, kModePlain, 0, BS, 1>(S, blockIdx.x, r, z);
 }
 
+// The plain apply with the edge-centric traversal of the paper (one thread
+// per block of a level, shared-memory atomics into the rows) instead of the
+// row-wise one, for the traversal ablation (FP64, FP32 and BF16 factors).
+template <typename TF, int BS>
+__global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
+    ildu0_apply_edge_kernel(SysDesc S, const double* r, double* z) {
+  apply_block<TF, kModePlain, 0, BS, 0, 1>(S, blockIdx.x, r, z);
+}
+
 // The unfused apply's two launches (plain mode): PART 1 = L sweep, r -> z;
 // PART 2 = D^-1 and U~ sweep, z -> z in place.
 template <typename TF, int PART, int BS>
@@ -422,6 +480,12 @@ static cudaError_t configure_one(size_t smem) {
       e = cudaFuncSetAttribute(ildu0_apply_rowsync_kernel<TF, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(ildu0_apply_rowsync_kernel<TF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if constexpr (!std::is_same<TF, df64s>::value) {
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ildu0_apply_edge_kernel<TF, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ildu0_apply_edge_kernel<TF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    }
   }
   return e;
 }
@@ -535,6 +599,23 @@ cudaError_t launch_apply_rowsync(const DevCtx& d, const double* r, double* z, cu
   if (d.factor_prec == ILU0DD_F32) return launch_rowsync_t<float>(d, r, z, s);
   if (d.factor_prec == ILU0DD_DF64) return launch_rowsync_t<df64s>(d, r, z, s);
   return launch_rowsync_t<bf16s>(d, r, z, s);
+}
+
+template <typename TF>
+static cudaError_t launch_edge_t(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
+  if (d.bs == 1)
+    ildu0_apply_edge_kernel<TF, 1><<<d.sd.nsub, d.threads, d.smem_bytes, s>>>(d.sd, r, z);
+  else
+    ildu0_apply_edge_kernel<TF, 3><<<d.sd.nsub, d.threads, d.smem_bytes, s>>>(d.sd, r, z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_edge(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
+  if (d.sd.nsub == 0) return cudaSuccess;
+  if (d.factor_prec == ILU0DD_F64) return launch_edge_t<double>(d, r, z, s);
+  if (d.factor_prec == ILU0DD_F32) return launch_edge_t<float>(d, r, z, s);
+  if (d.factor_prec == ILU0DD_BF16) return launch_edge_t<bf16s>(d, r, z, s);
+  return cudaErrorInvalidValue;  // DF64 pairs have no atomic add
 }
 
 template <typename TF>
