@@ -277,6 +277,7 @@ def run_ours(args):
            "h2d_bytes_per_step": 24 * n, "d2h_bytes_per_step": 24 * n, "ms_per_step": round(e2e_ms, 5),
            "what": "ilu0_dd_apply_host: r from pinned host memory, z back to it, every step "
                    "(copies and applies pipelined over 16 chunks of subdomains)"}
+    levels = run_levels(ctx, dev) if (not args.no_context and rank == 0) else None
     ctx.close()
     del ctx
 
@@ -385,6 +386,7 @@ def run_ours(args):
         "bicgstab": solves,
         "sweep_64cubed": sweep,
         "vendor_context": vendor,
+        "levels_device": levels,
         "unstructured": unstructured,
         "scalar_csr": scalar,
         "batched": batched,
@@ -586,6 +588,28 @@ def run_vendor(s, w, dev, ours_apply_ms, reps=20):
             "apply_ms": round(ams, 4), "apply_bytes": apply_bytes, "apply_gbs": round(apply_bytes / ams / 1e6, 1),
             "spmv_ms": round(sms, 4), "ours_apply_ms": round(ours_apply_ms, 5),
             "apply_speedup_ours_vs_vendor": round(ams / ours_apply_ms, 2)}
+
+
+def run_levels(ctx, dev, reps=10):
+    """Algorithm 5 on the device (ilu0dd_levels_device) for the context's
+    dropped pattern: milliseconds for both triangles, and whether the result
+    equals the library's host level sets."""
+    import torch
+
+    import paper_2508_04917_gb300 as pkg
+    from paper_2508_04917_gb300 import binding as B
+    rp, col, pp = (torch.from_numpy(ctx.export(x)).to(dev) for x in (B.X_DD_ROW_PTR, B.X_DD_COL, B.X_PART_PTR))
+    lev_l, lev_u, _, _ = pkg.levels_device(rp, col, pp)
+    same = bool(np.array_equal(lev_l.cpu().numpy(), ctx.export(B.X_LEVEL_L)) and
+                np.array_equal(lev_u.cpu().numpy(), ctx.export(B.X_LEVEL_U)))
+    e0, e1 = _events()
+    e0.record()
+    for _ in range(reps):
+        pkg.levels_device(rp, col, pp)
+    e1.record()
+    torch.cuda.synchronize()
+    return {"ms": round(e0.elapsed_time(e1) / reps, 4), "rows": int(rp.numel() - 1), "subdomains": int(pp.numel() - 1),
+            "equals_host_levels": same}
 
 
 def run_unstructured(dev, cells=(128, 128, 128), part_rows=2048, reps=20):

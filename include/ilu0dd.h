@@ -263,6 +263,23 @@ int ilu0_dd_apply_rowsync(const ilu0dd_ctx* ctx, const double* d_r, double* d_z,
 int ilu0_dd_apply_edge(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream);
 
 /*
+ * Level sets on the device (Algorithm 5, the paper's GPU level assignment,
+ * Section 4.2.2), one thread block per subdomain: a row joins level l + 1 once
+ * every lower (for d_lev_u: upper) neighbour inside its subdomain sits on a
+ * level <= l; rows without such neighbours are level 0. Inputs are DEVICE
+ * arrays of the reordered dropped (block-diagonal) pattern: d_row_ptr[n + 1],
+ * d_col[nnz] (block rows or scalar rows alike), and the subdomain row ranges
+ * d_part_ptr[nsub + 1] (rows of subdomain s are d_part_ptr[s] ..
+ * d_part_ptr[s+1] - 1); entries outside a row's subdomain are ignored.
+ * Outputs (device, caller-owned): d_lev_l[n], d_lev_u[n], and, if not NULL,
+ * d_nlev_l[nsub], d_nlev_u[nsub] (level counts per subdomain). The result
+ * equals the library's host level sets (ILU0DD_X_LEVEL_L / _U). Asynchronous
+ * on `stream`. ILU0DD_ERR_INVALID for nsub < 0 or null arrays (nsub > 0).
+ */
+int ilu0dd_levels_device(const int32_t* d_row_ptr, const int32_t* d_col, const int32_t* d_part_ptr, int32_t nsub,
+                         int32_t* d_lev_l, int32_t* d_lev_u, int32_t* d_nlev_l, int32_t* d_nlev_u, void* stream);
+
+/*
  * y = A_p x with the full reordered matrix (all inter-subdomain blocks kept,
  * Section 3.2 last paragraph). Device vectors in the reordered numbering,
  * 3*N doubles each, not overlapping. Asynchronous on `stream`.

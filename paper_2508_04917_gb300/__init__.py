@@ -4,4 +4,5 @@ The compute path is the CUDA library ``libilu0dd.so`` (C ABI in
 ``include/ilu0dd.h``); :mod:`.binding` marshals arguments to it.
 """
 from .binding import (BF16, DF64, F32, F64, PRECISIONS, Batch, Ilu0DD, Ilu0DDError,  # noqa: F401
-                      declared_functions, default_opts, library_path, load, partition_bfs, strerror, workspace_size)
+                      declared_functions, default_opts, levels_device, library_path, load, partition_bfs, strerror,
+                      workspace_size)

@@ -104,6 +104,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "ilu0_dd_apply_unfused": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_apply_rowsync": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_apply_edge": ([vp, vp, vp, vp], ctypes.c_int),
+            "ilu0dd_levels_device": ([vp, vp, vp, i32, vp, vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_apply_host": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_spmv": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_dot": ([vp, vp, vp, vp, vp], ctypes.c_int),
@@ -188,6 +189,23 @@ def partition_bfs(row_ptr, col, part_rows: int):
     if rc:
         raise Ilu0DDError(rc, "ilu0dd_partition_bfs")
     return part[:b.n_brows], int(k.value)
+
+
+def levels_device(row_ptr, col, part_ptr, stream=None):
+    """ilu0dd_levels_device: Algorithm 5's level sets of a reordered dropped
+    pattern on the GPU. Arguments are arrays (host or device); returns device
+    int32 tensors (lev_l, lev_u, nlev_l, nlev_u)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rp, cl, pp = (torch.as_tensor(np.ascontiguousarray(a, np.int32) if isinstance(a, np.ndarray) else a,
+                                  dtype=torch.int32, device=dev).contiguous() for a in (row_ptr, col, part_ptr))
+    n, nsub = rp.numel() - 1, pp.numel() - 1
+    out = [torch.empty(max(m, 1), dtype=torch.int32, device=dev) for m in (n, n, nsub, nsub)]
+    rc = load().ilu0dd_levels_device(*(ctypes.c_void_p(t.data_ptr()) for t in (rp, cl, pp)), nsub,
+                                     *(ctypes.c_void_p(t.data_ptr()) for t in out), _stream(stream))
+    if rc:
+        raise Ilu0DDError(rc, "ilu0dd_levels_device")
+    return out[0][:n], out[1][:n], out[2][:nsub], out[3][:nsub]
 
 
 def workspace_size(row_ptr, col, val, grid, sub, **opts) -> int:

@@ -432,6 +432,16 @@ int ilu0_dd_apply_edge(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, vo
   return ILU0DD_OK;
 }
 
+int ilu0dd_levels_device(const int32_t* d_row_ptr, const int32_t* d_col, const int32_t* d_part_ptr, int32_t nsub,
+                         int32_t* d_lev_l, int32_t* d_lev_u, int32_t* d_nlev_l, int32_t* d_nlev_u, void* stream) {
+  if (nsub < 0 || (nsub > 0 && (!d_row_ptr || !d_col || !d_part_ptr || !d_lev_l || !d_lev_u)))
+    return ILU0DD_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = launch_levels(d_row_ptr, d_col, d_part_ptr, nsub, 0, d_lev_l, d_nlev_l, s);
+  if (e == cudaSuccess) e = launch_levels(d_row_ptr, d_col, d_part_ptr, nsub, 1, d_lev_u, d_nlev_u, s);
+  return e == cudaSuccess ? ILU0DD_OK : ILU0DD_ERR_CUDA;
+}
+
 int ilu0_dd_apply_unfused(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream) {
   if (!ctx || (ctx->plan.N > 0 && (!d_r || !d_z))) return ILU0DD_ERR_INVALID;
   const size_t n = (size_t)ctx->plan.bs * (size_t)ctx->plan.N * sizeof(double);

@@ -308,7 +308,60 @@ __global__ void pack_sell_kernel(const int32_t* __restrict__ slice_off, int64_t 
   }
 }
 
+// Algorithm 5 (level sets by repeated sweeps), one block per subdomain: a row
+// joins level l + 1 once all its lower (upper = 1: upper) neighbours inside
+// the subdomain sit on levels <= l. lev[] is in global memory: kUnset until
+// assigned, kJoining between the check and the promotion of a sweep.
+constexpr int32_t kUnset = INT32_MAX, kJoining = -1;
+__global__ void levels_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                              const int32_t* __restrict__ part_ptr, int upper, int32_t* lev, int32_t* nlev) {
+  const int32_t r0 = part_ptr[blockIdx.x], r1 = part_ptr[blockIdx.x + 1];
+  auto dep = [&](int32_t i, int32_t j) { return j >= r0 && j < r1 && (upper ? j > i : j < i); };
+  for (int32_t i = r0 + (int32_t)threadIdx.x; i < r1; i += (int32_t)blockDim.x) {
+    bool any = false;
+    for (int32_t q = rp[i]; q < rp[i + 1] && !any; ++q) any = dep(i, col[q]);
+    lev[i] = any ? kUnset : 0;
+  }
+  volatile int32_t* vlev = lev;  // read while other threads of the sweep mark rows
+  __shared__ int joined;
+  int32_t level = 0;
+  // at most one sweep per row: every sweep of an acyclic pattern adds a row
+  for (; level <= r1 - r0; ++level) {
+    if (threadIdx.x == 0) joined = 0;
+    __syncthreads();
+    for (int32_t i = r0 + (int32_t)threadIdx.x; i < r1; i += (int32_t)blockDim.x) {
+      if (vlev[i] != kUnset) continue;
+      bool ready = true;
+      for (int32_t q = rp[i]; q < rp[i + 1] && ready; ++q) {
+        const int32_t j = col[q];
+        if (dep(i, j)) {
+          const int32_t lj = vlev[j];
+          ready = lj >= 0 && lj <= level;
+        }
+      }
+      if (ready) {
+        vlev[i] = kJoining;
+        joined = 1;
+      }
+    }
+    __syncthreads();
+    const int any = joined;
+    for (int32_t i = r0 + (int32_t)threadIdx.x; i < r1; i += (int32_t)blockDim.x)
+      if (lev[i] == kJoining) lev[i] = level + 1;
+    __syncthreads();
+    if (!any) break;
+  }
+  if (threadIdx.x == 0 && nlev) nlev[blockIdx.x] = r1 > r0 ? level + 1 : 0;
+}
+
 }  // namespace
+
+cudaError_t launch_levels(const int32_t* rp, const int32_t* col, const int32_t* part_ptr, int32_t nsub, int upper,
+                          int32_t* lev, int32_t* nlev, cudaStream_t s) {
+  if (nsub <= 0) return cudaSuccess;
+  levels_kernel<<<nsub, 256, 0, s>>>(rp, col, part_ptr, upper, lev, nlev);
+  return cudaGetLastError();
+}
 
 size_t device_setup_scratch_bytes(const Plan& p) {
   return scratch_layout(p, total_levels_of(p), total_prows_of(p)).total;

@@ -30,4 +30,12 @@ size_t device_setup_scratch_bytes(const Plan& p);
 int setup_on_device(const Plan& p, const double* aval_host, unsigned char* scratch, size_t scratch_bytes,
                     unsigned char* ws, cudaStream_t s, DeviceSetupResult* res);
 
+// Level sets of the lower (upper = 0) or upper (upper = 1) triangle of a
+// block-diagonal pattern (device CSR rp/col of the reordered dropped matrix,
+// subdomain row ranges part_ptr[nsub + 1]) by Algorithm 5, one block per
+// subdomain; lev[N] receives each row's level and nlev[nsub] (optional) each
+// subdomain's level count. Entries outside a row's subdomain are ignored.
+cudaError_t launch_levels(const int32_t* rp, const int32_t* col, const int32_t* part_ptr, int32_t nsub, int upper,
+                          int32_t* lev, int32_t* nlev, cudaStream_t s);
+
 }  // namespace ilu0dd
