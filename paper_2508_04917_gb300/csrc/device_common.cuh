@@ -44,12 +44,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 __device__ __forceinline__ float bf16_to_f32(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
 
+// Factor loads from the packed stream (read-only path), converted to the
+// apply's compute type.
 template <typename TF>
 struct FactorLoad;
 template <>
 struct FactorLoad<double> {
   using compute = double;
-  __device__ __forceinline__ static double get(const unsigned char* p) { return *reinterpret_cast<const double*>(p); }
   __device__ __forceinline__ static double getg(const unsigned char* p) {
     return __ldg(reinterpret_cast<const double*>(p));
   }
@@ -57,7 +58,6 @@ struct FactorLoad<double> {
 template <>
 struct FactorLoad<float> {
   using compute = float;
-  __device__ __forceinline__ static float get(const unsigned char* p) { return *reinterpret_cast<const float*>(p); }
   __device__ __forceinline__ static float getg(const unsigned char* p) {
     return __ldg(reinterpret_cast<const float*>(p));
   }
@@ -68,9 +68,6 @@ struct bf16s {
 template <>
 struct FactorLoad<bf16s> {
   using compute = float;
-  __device__ __forceinline__ static float get(const unsigned char* p) {
-    return bf16_to_f32(*reinterpret_cast<const uint16_t*>(p));
-  }
   __device__ __forceinline__ static float getg(const unsigned char* p) {
     return bf16_to_f32(__ldg(reinterpret_cast<const unsigned short*>(p)));
   }
@@ -159,10 +156,6 @@ __device__ __forceinline__ double to_double(df64 v) { return df_to_double(v); }
 template <>
 struct FactorLoad<df64s> {
   using compute = df64;
-  __device__ __forceinline__ static df64 get(const unsigned char* p) {
-    const float2 v = *reinterpret_cast<const float2*>(p);
-    return df64(v.x, v.y);
-  }
   __device__ __forceinline__ static df64 getg(const unsigned char* p) {
     const float2 v = __ldg(reinterpret_cast<const float2*>(p));
     return df64(v.x, v.y);
