@@ -204,10 +204,15 @@ int ilu0_dd_setup_planned(ilu0dd_plan* plan, const ilu0dd_bsr* A, void* d_worksp
 int ilu0dd_plan_destroy(ilu0dd_plan* plan);
 
 /*
- * z = M^-1 r = U~^-1 D^-1 L^-1 r (Sections 4.3-4.4), one fused kernel launch.
- * d_r, d_z: device, 3*N doubles each, in the reordered (subdomain-
- * contiguous) numbering; they must not overlap. Asynchronous on `stream`.
- * The context is only read, so concurrent applies on one context are safe.
+ * z = M^-1 r = U~^-1 D^-1 L^-1 r (Sections 4.3-4.4), one fused kernel launch:
+ * one thread block per subdomain, the subdomain vector in shared memory, the
+ * rows in Algorithm 5's level order (a warp starts a level's rows once the
+ * previous level is complete; one mbarrier per level slice, no block
+ * barriers). d_r, d_z: device, bs*N doubles each, in the reordered
+ * (subdomain-contiguous) numbering; they must not overlap. Asynchronous on
+ * `stream`. The context is only read, so concurrent applies on one context
+ * are safe. A wait that exceeds its bound (ilu0dd_set_wait_limits) sets the
+ * device error word (ilu0_dd_device_error) instead of hanging.
  */
 int ilu0_dd_apply(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream);
 

@@ -18,9 +18,10 @@ namespace ilu0dd {
 // Every subdomain owns one contiguous byte range ("its stream"), read in order
 // by its thread block (with bulk L2 prefetches running ahead). The stream is a sequence
 // of piece records. A piece is a set of rows of one level of the subdomain's L
-// DAG (kind 0) or U DAG (kind 1); rows of one piece are independent, pieces
-// are separated by a block barrier. Rows with no strictly-lower block (L level
-// 0) need no work in the L sweep and appear in no L piece.
+// DAG (kind 0) or U DAG (kind 1); rows of one piece are independent, and a
+// piece's rows start once the previous level's pieces are complete (one
+// mbarrier per piece). Rows with no strictly-lower block (L level 0) need no
+// work in the L sweep and appear in no L piece.
 //
 // Inside a record the rows are sorted by block count, longest first, and the
 // blocks are stored slot-major ("jagged diagonal" order): slot s holds the
