@@ -114,7 +114,8 @@ typedef struct {
 
 typedef struct ilu0dd_ctx ilu0dd_ctx;
 
-/* Fill *opts with the defaults listed above. */
+/* Fill *opts with the defaults listed above; trace defaults to 1 when the
+ * environment variable ILU0DD_TRACE is a positive integer. */
 int ilu0dd_default_opts(ilu0dd_opts* opts);
 
 /* Human-readable name of a return code (static string, never NULL). */

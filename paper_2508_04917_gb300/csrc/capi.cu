@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -246,7 +247,8 @@ int ilu0dd_default_opts(ilu0dd_opts* o) {
   o->check_every = 8;
   o->use_graphs = 1;
   o->keep_host = 0;
-  o->trace = 0;
+  const char* tr = std::getenv("ILU0DD_TRACE");  // per-phase timings without recompiling the caller
+  o->trace = tr && std::atoi(tr) > 0 ? 1 : 0;
   return ILU0DD_OK;
 }
 

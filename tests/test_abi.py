@@ -5,7 +5,9 @@ No kernel is launched here; the structural query runs the host part of the
 setup only (Algorithm 2, Algorithm 3, the drop of Section 3.2, level sets).
 """
 import ctypes
+import os
 import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -98,3 +100,15 @@ def test_context_library_builds_and_exports():
                  "ctx_vendor_ilu0_destroy", "ctx_fp64_fma_rate"):
         assert hasattr(lib, name), name
     assert lib.ctx_vendor_ilu0_apply(None, None, None, None) == 4
+
+
+
+def test_trace_from_environment():
+    """ILU0DD_TRACE=1 turns on the per-phase timings of the defaults (checked in
+    a child process: the environment is read when the defaults are filled)."""
+    code = "import paper_2508_04917_gb300 as g; print(g.default_opts().trace)"
+    repo = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for value, want in (("1", "1"), ("0", "0")):
+        env = dict(os.environ, ILU0DD_TRACE=value)
+        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=repo)
+        assert out.returncode == 0 and out.stdout.strip() == want, out.stderr
