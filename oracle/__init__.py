@@ -113,7 +113,15 @@ class BSR:
 
     @property
     def bs(self) -> int:
-        return int(self.val.shape[1]) if self.val is not None and self.val.ndim == 3 else self.block
+        if self.val is not None:
+            if self.val.ndim == 3:
+                return int(self.val.shape[1])
+            nnzb = int(self.row_ptr[-1])  # flat values: bs*bs per block
+            if nnzb > 0:
+                b = int(round((self.val.size / nnzb) ** 0.5))
+                if b * b * nnzb == self.val.size:
+                    return b
+        return self.block
 
     @property
     def n(self) -> int:

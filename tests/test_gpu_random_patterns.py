@@ -1,8 +1,8 @@
 """Random block patterns with random partitions on the GPU against the
 oracle: irregular rows (many blocks a side, unsymmetric patterns), empty and
 one-row parts, parts of any shape. Every apply form of the library
-(fused, unfused, row flags, edge-centric) and the SpMV, for 3x3 and scalar
-blocks, FP64 factors."""
+(fused, unfused, row flags, edge-centric), the SpMV and BiCGSTAB, for 3x3
+and scalar blocks, FP64 factors."""
 import numpy as np
 import pytest
 
@@ -59,6 +59,14 @@ def test_random_pattern_applies_match_oracle(seed):
         assert nrel(ctx.apply_edge(rd).cpu().numpy(), zo) <= 1e-12
         x = rng.uniform(-1, 1, ctx.size)
         assert np.array_equal(ctx.spmv(torch.from_numpy(x).cuda()).cpu().numpy(), oracle.spmv(d.Ap, x))
+        # BiCGSTAB (natural numbering) against the oracle's (reordered numbering)
+        b = oracle.spmv(oracle.BSR(rp, col, val), rng.uniform(-1, 1, ctx.size))
+        xs, info = ctx.solve(torch.from_numpy(b).cuda())
+        perm = np.asarray(d.perm)
+        to_new = (lambda v: v.reshape(-1, bs)[perm].reshape(-1))
+        ref = oracle.bicgstab(d.Ap, d.LU, to_new(b))
+        assert info["status"] == 0 and info["iterations"] == ref.iterations
+        assert nrel(to_new(xs.cpu().numpy()), ref.x) <= 1e-12
         assert ctx.device_error() == 0
     finally:
         ctx.close()

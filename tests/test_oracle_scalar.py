@@ -109,3 +109,14 @@ def test_scalar_bicgstab_matches_scipy_iterates():
         assert np.linalg.norm(ours.x - ref) <= 1e-9 * np.linalg.norm(ref)
     full = oracle.bicgstab(d.Ap, d.LU, b)
     assert full.status == 0 and full.rel_res_true < 1e-8
+
+
+def test_block_size_from_flat_values():
+    """Flat value arrays carry bs*bs entries per block: the oracle reads the
+    block size from their length (a scalar matrix is never read as 3x3)."""
+    s1 = synth.system(4, 3, 2, 3, bs=1)
+    s3 = synth.system(4, 3, 2, 3)
+    assert oracle.BSR(s1.row_ptr, s1.col, np.ravel(s1.val)).bs == 1
+    assert oracle.BSR(s3.row_ptr, s3.col, np.ravel(s3.val)).bs == 3
+    assert oracle.BSR(s3.row_ptr, s3.col, np.asarray(s3.val).reshape(-1, 3, 3)).bs == 3
+    assert oracle.BSR(s1.row_ptr, s1.col, None, block=1).bs == 1
