@@ -374,6 +374,9 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": round(apply_gbs_rank, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(apply_gbs_rank / peak, 4), "traffic": traffic,
+                     # DRAM GB/s from the ncu bytes per launch over the mean mode P/S launch time
+                     "dram_gbs_from_traffic": None if traffic is None else round(
+                         traffic / (0.5 * (per_kernel["apply_p"]["ms"] + per_kernel["apply_s"]["ms"]) * 1e6), 1),
                      "kernel": "ildu0_apply_kernel<double, P|S>", "peak_source": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": {"apply_p": bytes_k[0], "apply_s": bytes_k[2]}},
         "e2e": e2e,
