@@ -78,7 +78,10 @@ __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 // PART 0 runs every piece (the fused apply); 1 only the L sweep, 2 only the
 // D^-1 and U~ sweep (the two launches of the unfused apply). BS = block
 // dimension: 3 (three threads per block row, ten rows per warp) or 1 (scalar
-// CSR: one thread per row, 32 rows per warp).
+// CSR: one thread per row, 32 rows per warp). The ablations: SYNC 1 orders
+// rows by per-row flags (Algorithm 4) instead of the per-piece mbarriers;
+// TRAV 1 traverses a level edge-centrically (one thread per block, shared-
+// memory atomics into the rows) instead of row-wise.
 template <typename TF, int MODE, int PART = 0, int BS = 3, int SYNC = 0, int TRAV = 0>
 __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const double* r, double* z) {
   static_assert(BS == 1 || BS == 3, "block dimension 1 or 3");
@@ -106,8 +109,8 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
       pf_end += bytes;
     }
   };
-  // L2 prefetches come from lane 0 of the last warp, which has rows only in the
-  // widest levels, so the issue cost stays off the other warps' paths
+  // L2 prefetches come from lane 0 of the last warp, as that warp passes the
+  // pieces
   const bool pf_thread = tid == (int)blockDim.x - 32;
   if (pf_thread) prefetch_upto(pf_end + dist);
 
