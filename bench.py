@@ -676,6 +676,7 @@ def run_unstructured(dev, cells=(128, 128, 128), part_rows=2048, reps=20):
             out[f"{name}_{prec}"] = {
                 "setup_s": round(su, 3),
                 "dropped_blocks_pct": round(100.0 * (1 - ctx.query("kept") / ctx.query("nnzb")), 2),
+                "max_levels": ctx.query("max_levels"), "pieces": ctx.query("pieces"),
                 "apply_ms": round(ams, 5), "apply_rowsync_ms": round(rms, 5), "apply_bytes": ctx.query("apply_bytes"),
                 "apply_gbs": round(ctx.query("apply_bytes") / ams / 1e6, 1), "iterations": info["iterations"],
                 "solve_s": round(sec, 5), "status": info["status"],
@@ -709,6 +710,7 @@ def run_scalar(dev, grid=(200, 200, 200), sub=(32, 16, 16), reps=20):
         xs = torch.from_numpy(s.xstar).to(dev)
         out[prec] = {"setup_s": round(su, 3), "threads": ctx.query("threads"),
                      "dropped_pct": round(100.0 * (1 - ctx.query("kept") / ctx.query("nnzb")), 2),
+                     "max_levels": ctx.query("max_levels"), "pieces": ctx.query("pieces"),
                      "apply_ms": round(ams, 5), "apply_rowsync_ms": round(rms, 5), "apply_bytes": ctx.query("apply_bytes"),
                      "apply_gbs": round(ctx.query("apply_bytes") / ams / 1e6, 1), "iterations": info["iterations"],
                      "solve_s": round(sec, 5), "status": info["status"],
