@@ -382,18 +382,46 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
             for (int c = 0; c < BS; ++c) acc = mac(-bv[sl][c], y[BS * cl + c], acc);
           }
         }
-        // rows with more than kDescSlots blocks (general patterns): remaining slots
+        // Rows with more than kDescSlots blocks (general patterns): the further
+        // slots, G at a time with all their loads issued first (the slot
+        // counts come from the record head), into two alternating
+        // accumulators added at the end.
         if (w > kDescSlots && nsl == kDescSlots) {
-          for (int sl = kDescSlots; sl < w; ++sl) {
-            const uint32_t cs = (uint32_t)gu16(rec + 2 * sl);
-            if ((uint32_t)trow >= cs) break;
-            const int cl = gu16(gs + (cbase + 2u * c0 + trow2));
-            const uint32_t vo = vbase + (uint32_t)(BS * BS) * FE * c0 + lane_voff;
-            const uint32_t cstride = (uint32_t)BS * FE * cs;
+          constexpr int G = sizeof(TV) >= 8 ? 4 : 3;
+          TV acc_b = TV(0);
+          for (int sl = kDescSlots; sl < w; sl += G) {
+            uint32_t cs[G], off[G];
+            bool has[G];
+            uint32_t cc = c0;
 #pragma unroll
-            for (int c = 0; c < BS; ++c) acc = mac(-gfactor<TF>(gs + (vo + (uint32_t)c * cstride)), y[BS * cl + c], acc);
-            c0 += cs;
+            for (int u = 0; u < G; ++u) {
+              cs[u] = sl + u < w ? (uint32_t)gu16(rec + 2 * (sl + u)) : 0u;
+              off[u] = cc;
+              cc += cs[u];
+              has[u] = (uint32_t)trow < cs[u];  // counts do not grow with the slot
+            }
+            int cl[G];
+            TV v[G][BS];
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+              cl[u] = has[u] ? gu16(gs + (cbase + 2u * off[u] + trow2)) : 0;
+              const uint32_t vo = vbase + (uint32_t)(BS * BS) * FE * off[u] + lane_voff;
+#pragma unroll
+              for (int c = 0; c < BS; ++c)
+                v[u][c] = has[u] ? gfactor<TF>(gs + (vo + (uint32_t)c * ((uint32_t)BS * FE * cs[u]))) : TV(0);
+            }
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+              if (has[u]) {
+                TV& a2 = (u & 1) ? acc_b : acc;
+#pragma unroll
+                for (int c = 0; c < BS; ++c) a2 = mac(-v[u][c], y[BS * cl[u] + c], a2);
+              }
+            }
+            c0 = cc;
+            if (!has[G - 1]) break;
           }
+          acc = mac(TV(1), acc_b, acc);
         }
         y[BS * row + comp] = acc;
       }
