@@ -327,12 +327,15 @@ def run_ours(args):
             rms = u0.elapsed_time(u1) / 20
             # traversal ablation: edge-centric (one thread per block, atomics); no DF64 form
             ems = time_apply_warm(c, r, zp, 20, c.apply_edge) if prec != "df64" else None
+            # shared-memory ablation: the subdomain vector in global memory (FP64 only)
+            gms = time_apply_warm(c, r, zp, 20, c.apply_global_vector) if prec == "f64" else None
             solves[prec] = {"s": round(wall, 5), "iterations": info["iterations"], "restarts": info["restarts"],
                             "rel_res_true": info["rel_res_true"], "setup_s": round(su, 3),
                             "max_rel_err_vs_xstar": err, "status": info["status"],
                             "apply_ms": round(ams, 5), "apply_unfused_ms": round(ums, 5),
                             "fusion_speedup": round(ums / ams, 3), "apply_rowsync_ms": round(rms, 5),
                             "apply_edge_ms": None if ems is None else round(ems, 5),
+                            "apply_vector_in_global_ms": None if gms is None else round(gms, 5),
                             "apply_bytes": c.query("apply_bytes"),
                             "apply_gbs": round(c.query("apply_bytes") / ams / 1e6, 1)}
             c.close()
@@ -526,7 +529,8 @@ def run_table4_shapes(dev, reps=20):
                      "dropped_blocks_pct": round(100.0 * (1 - ctx.query("kept") / ctx.query("nnzb")), 2),
                      "fused_ms": round(time_apply_warm(ctx, r, z, reps), 4),
                      "unfused_ms": round(time_apply_warm(ctx, r, z, reps, ctx.apply_unfused), 4),
-                     "edge_centric_ms": round(time_apply_warm(ctx, r, z, reps, ctx.apply_edge), 4)}
+                     "edge_centric_ms": round(time_apply_warm(ctx, r, z, reps, ctx.apply_edge), 4),
+                     "vector_in_global_memory_ms": round(time_apply_warm(ctx, r, z, reps, ctx.apply_global_vector), 4)}
         ctx.close()
     return out
 

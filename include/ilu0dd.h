@@ -269,6 +269,16 @@ int ilu0_dd_apply_rowsync(const ilu0dd_ctx* ctx, const double* d_r, double* d_z,
 int ilu0_dd_apply_edge(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream);
 
 /*
+ * The same z = M^-1 r as ilu0_dd_apply, FP64 factors only, with the
+ * subdomain vector kept in global memory (in d_z itself) instead of shared
+ * memory: the vector-in-global-memory variant of the paper's lower-solve
+ * comparison (Table 3), to measure what shared memory brings. Results
+ * bit-identical to ilu0_dd_apply. ILU0DD_ERR_INVALID for other factor
+ * precisions and for overlapping r and z.
+ */
+int ilu0_dd_apply_global_vector(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream);
+
+/*
  * Level sets on the device (Algorithm 5, the paper's GPU level assignment,
  * Section 4.2.2), one thread block per subdomain: a row joins level l + 1 once
  * every lower (for d_lev_u: upper) neighbour inside its subdomain sits on a

@@ -104,6 +104,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "ilu0_dd_apply_unfused": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_apply_rowsync": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_apply_edge": ([vp, vp, vp, vp], ctypes.c_int),
+            "ilu0_dd_apply_global_vector": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0dd_levels_device": ([vp, vp, vp, i32, vp, vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_apply_host": ([vp, vp, vp, vp], ctypes.c_int),
             "ilu0_dd_spmv": ([vp, vp, vp, vp], ctypes.c_int),
@@ -366,6 +367,15 @@ class Ilu0DD:
         z = self._new() if z is None else z
         self._check(self._lib.ilu0_dd_apply_edge(self._ctx, _dptr(r, self.size, "r"), _dptr(z, self.size, "z"),
                                                  _stream(stream)), "ilu0_dd_apply_edge")
+        return z
+
+    def apply_global_vector(self, r, z=None, stream=None):
+        """z = M^-1 r (FP64 factors) with the subdomain vector in global memory
+        instead of shared memory; same bits as apply()."""
+        z = self._new() if z is None else z
+        self._check(self._lib.ilu0_dd_apply_global_vector(self._ctx, _dptr(r, self.size, "r"),
+                                                          _dptr(z, self.size, "z"), _stream(stream)),
+                    "ilu0_dd_apply_global_vector")
         return z
 
     def apply_unfused(self, r, z=None, stream=None):

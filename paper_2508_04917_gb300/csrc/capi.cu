@@ -423,6 +423,17 @@ int ilu0_dd_apply_rowsync(const ilu0dd_ctx* ctx, const double* d_r, double* d_z,
   return ILU0DD_OK;
 }
 
+int ilu0_dd_apply_global_vector(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream) {
+  if (!ctx || (ctx->plan.N > 0 && (!d_r || !d_z)) || ctx->dev.factor_prec != ILU0DD_F64) return ILU0DD_ERR_INVALID;
+  const size_t n = (size_t)ctx->plan.bs * (size_t)ctx->plan.N * sizeof(double);
+  const char* r = reinterpret_cast<const char*>(d_r);
+  const char* z = reinterpret_cast<const char*>(d_z);
+  if (r < z + n && z < r + n) return ILU0DD_ERR_INVALID;  // overlapping vectors
+  cudaError_t e = launch_apply_vglobal(ctx->dev, d_r, d_z, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(const_cast<ilu0dd_ctx*>(ctx), e, "global-vector apply launch");
+  return ILU0DD_OK;
+}
+
 int ilu0_dd_apply_edge(const ilu0dd_ctx* ctx, const double* d_r, double* d_z, void* stream) {
   if (!ctx || (ctx->plan.N > 0 && (!d_r || !d_z)) || ctx->dev.factor_prec == ILU0DD_DF64) return ILU0DD_ERR_INVALID;
   const size_t n = (size_t)ctx->plan.bs * (size_t)ctx->plan.N * sizeof(double);

@@ -81,8 +81,10 @@ __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 // CSR: one thread per row, 32 rows per warp). The ablations: SYNC 1 orders
 // rows by per-row flags (Algorithm 4) instead of the per-piece mbarriers;
 // TRAV 1 traverses a level edge-centrically (one thread per block, shared-
-// memory atomics into the rows) instead of row-wise.
-template <typename TF, int MODE, int PART = 0, int BS = 3, int SYNC = 0, int TRAV = 0>
+// memory atomics into the rows) instead of row-wise; VGLOB 1 (FP64 only)
+// keeps the subdomain vector in global memory (in z) instead of shared
+// memory, to measure what shared memory brings.
+template <typename TF, int MODE, int PART = 0, int BS = 3, int SYNC = 0, int TRAV = 0, int VGLOB = 0>
 __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const double* r, double* z) {
   static_assert(BS == 1 || BS == 3, "block dimension 1 or 3");
   constexpr int RPW = BS == 3 ? kRowsPerWarp : 32;  // rows per warp
@@ -93,7 +95,8 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
   if (MODE != kModePlain && S.scal->done) return;
   const CtaDesc cd = S.cta[sub];
   const int tid = threadIdx.x;
-  TV* y = reinterpret_cast<TV*>(smem);
+  static_assert(!VGLOB || std::is_same<TF, double>::value, "global vector: FP64 only");
+  TV* y = VGLOB ? reinterpret_cast<TV*>(z + (int64_t)BS * cd.row0) : reinterpret_cast<TV*>(smem);
   const unsigned char* gs = S.stream + cd.stream_off;
   const uint32_t len = (uint32_t)cd.stream_len;
   const uint32_t dist = (uint32_t)S.prefetch_bytes;
@@ -438,7 +441,8 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
   __syncthreads();
   if constexpr (SYNC == 0)
     for (int q = tid; q < k1 - win0; q += blockDim.x) mbar_inval(mbar + q);
-  for (int e = tid; e < nv; e += blockDim.x) z[base + e] = kDF ? to_double(y[e]) * unscale : to_double(y[e]);
+  if constexpr (!VGLOB)
+    for (int e = tid; e < nv; e += blockDim.x) z[base + e] = kDF ? to_double(y[e]) * unscale : to_double(y[e]);
 }
 
 // Every apply instance is compiled for three resident blocks per SM (56
@@ -466,6 +470,15 @@ template <typename TF, int BS>
 __global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
     ildu0_apply_edge_kernel(SysDesc S, const double* r, double* z) {
   apply_block<TF, kModePlain, 0, BS, 0, 1>(S, blockIdx.x, r, z);
+}
+
+// The plain FP64 apply with the subdomain vector in global memory (z itself)
+// instead of shared memory: the same arithmetic in the same order, for the
+// shared-memory ablation.
+template <int BS>
+__global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
+    ildu0_apply_vglobal_kernel(SysDesc S, const double* r, double* z) {
+  apply_block<double, kModePlain, 0, BS, 0, 0, 1>(S, blockIdx.x, r, z);
 }
 
 // The unfused apply's two launches (plain mode): PART 1 = L sweep, r -> z;
@@ -511,6 +524,12 @@ static cudaError_t configure_one(size_t smem) {
       e = cudaFuncSetAttribute(ildu0_apply_rowsync_kernel<TF, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(ildu0_apply_rowsync_kernel<TF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if constexpr (std::is_same<TF, double>::value) {
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ildu0_apply_vglobal_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ildu0_apply_vglobal_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    }
     if constexpr (!std::is_same<TF, df64s>::value) {
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(ildu0_apply_edge_kernel<TF, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -638,6 +657,16 @@ static cudaError_t launch_edge_t(const DevCtx& d, const double* r, double* z, cu
     ildu0_apply_edge_kernel<TF, 1><<<d.sd.nsub, d.threads, d.smem_bytes, s>>>(d.sd, r, z);
   else
     ildu0_apply_edge_kernel<TF, 3><<<d.sd.nsub, d.threads, d.smem_bytes, s>>>(d.sd, r, z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_vglobal(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
+  if (d.sd.nsub == 0) return cudaSuccess;
+  if (d.factor_prec != ILU0DD_F64) return cudaErrorInvalidValue;
+  if (d.bs == 1)
+    ildu0_apply_vglobal_kernel<1><<<d.sd.nsub, d.threads, d.smem_bytes, s>>>(d.sd, r, z);
+  else
+    ildu0_apply_vglobal_kernel<3><<<d.sd.nsub, d.threads, d.smem_bytes, s>>>(d.sd, r, z);
   return cudaGetLastError();
 }
 

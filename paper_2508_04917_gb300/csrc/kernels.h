@@ -74,6 +74,8 @@ cudaError_t launch_apply_rowsync(const DevCtx& d, const double* r, double* z, cu
 // The plain apply with the edge-centric traversal (one thread per block,
 // shared-memory atomics); FP64, FP32 and BF16 factors only.
 cudaError_t launch_apply_edge(const DevCtx& d, const double* r, double* z, cudaStream_t s);
+// The plain FP64 apply with the subdomain vector in global memory (z).
+cudaError_t launch_apply_vglobal(const DevCtx& d, const double* r, double* z, cudaStream_t s);
 
 // y = A_p x; kind 0 plain, 1: v = A ph with (rh.v) -> alpha, 2: t = A sh with (t.s),(t.t) -> omega.
 cudaError_t launch_spmv(const DevCtx& d, int kind, const double* x, double* y, cudaStream_t s);

@@ -6,7 +6,9 @@ Both run the same per-row arithmetic in the same order on the same packed
 stream; only when a row may start differs. So the results are bit-identical
 in every factor precision and block dimension, on 7-point, 27-point and
 unsymmetric patterns (where the U sweep would overwrite L results that rows
-of the L sweep still read, without the barrier between the sweeps).
+of the L sweep still read, without the barrier between the sweeps). The FP64
+apply with its subdomain vector in global memory instead of shared memory
+(the shared-memory ablation) gives the same bits as well.
 """
 import numpy as np
 import pytest
@@ -107,5 +109,30 @@ def test_rowsync_refuses_boxes_without_room_for_the_flags():
         with pytest.raises(g.Ilu0DDError) as e:
             ctx.apply_rowsync(r)
         assert e.value.code == 3
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("bs", [3, 1])
+@pytest.mark.parametrize("grid,sub,model", GEOMS, ids=IDS)
+def test_global_vector_apply_equals_shared(grid, sub, model, bs):
+    """The FP64 apply with the subdomain vector in global memory (the shared-
+    memory ablation) gives the shared-memory apply's bits."""
+    s = synth.system(*grid, 22, model=model, bs=bs)
+    ctx = g.Ilu0DD(s.row_ptr, s.col, s.val, grid, sub)
+    try:
+        r = torch.from_numpy(np.random.default_rng(3).uniform(-1, 1, ctx.size)).cuda()
+        assert torch.equal(ctx.apply_global_vector(r), ctx.apply(r))
+    finally:
+        ctx.close()
+
+
+def test_global_vector_apply_needs_fp64():
+    s = synth.system(8, 8, 8, 3)
+    ctx = g.Ilu0DD(s.row_ptr, s.col, s.val, (8, 8, 8), (4, 4, 4), factor_prec="f32")
+    try:
+        with pytest.raises(g.Ilu0DDError) as e:
+            ctx.apply_global_vector(torch.zeros(ctx.size, dtype=torch.float64, device="cuda"))
+        assert e.value.code == 1
     finally:
         ctx.close()
