@@ -14,8 +14,10 @@ Paper map:
   permutation/reorder  Section 3.1, Algorithm 3
   drop                 Section 3.2
   ilu0                 Algorithm 7 (ILU0 part), block form
+  ildu0                Algorithm 7 with the ILDU0 post-processing (Section 4.3)
   levels_lower/upper   Algorithm 5 (level sets of the subdomain DAGs)
-  apply                Section 4.2.2 / 4.4 result: z = U^-1 L^-1 r
+  apply                Section 4.2.2 / 4.4 result: z = U^-1 L^-1 r (ILU0 form)
+  apply_ildu0          the same z in the ILDU0 form: z = U~^-1 D^-1 L^-1 r
   spmv, dot            the products inside Algorithm 1
   bicgstab             Algorithm 1 (right-preconditioned reading)
 """
@@ -32,21 +34,49 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
+_threads = 1
 
 OK, ZERO_PIVOT, BREAKDOWN, NOT_CONVERGED = 0, 2, 5, 6
 DOT_TILE = 256
 
 
-def build(force: bool = False) -> str:
-    """Compile ``liboracle.so`` (O2, no fast-math, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+def _compile(lib: str, extra: list, force: bool) -> str:
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", *extra,
                                "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, lib)
+    return lib
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` (one thread) and ``liboracle_omp.so`` (the same
+    source with OpenMP on its independent loops): O2, no fast-math, no FMA
+    contraction."""
+    _compile(_LIB_OMP, ["-fopenmp"], force)
+    return _compile(_LIB, [], force)
+
+
+def set_threads(k: int) -> None:
+    """Run the oracle on k host threads (k = 1: the plain single-thread build;
+    k > 1: the OpenMP build, which gives the same bits)."""
+    global _threads
+    _threads = max(1, int(k))
+    if _threads > 1:
+        _load().oracle_set_threads(_threads)
+
+
+def threads() -> int:
+    return _threads
+
+
+class _Precond(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int32), ("nparts", ctypes.c_int32), ("part_ptr", ctypes.c_void_p),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("lu", ctypes.c_void_p),
+                ("f", ctypes.c_void_p), ("inv_d", ctypes.c_void_p)]
 
 
 class _Info(ctypes.Structure):
@@ -56,10 +86,11 @@ class _Info(ctypes.Structure):
 
 
 def _load():
-    global _lib
+    omp = _threads > 1
     with _lock:
-        if _lib is None:
-            lib = ctypes.CDLL(build())
+        if omp not in _libs:
+            build()
+            lib = ctypes.CDLL(_LIB_OMP if omp else _LIB)
             i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
             f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
             vp = ctypes.c_void_p
@@ -89,8 +120,21 @@ def _load():
             lib.oracle_bicgstab.argtypes = [I, ctypes.c_int, i32p, i32p, f64p, i32p, i32p, f64p, f64p, f64p, I, D,
                                             ctypes.POINTER(_Info), vp]
             lib.oracle_bicgstab.restype = ctypes.c_int
-            _lib = lib
-    return _lib
+            lib.oracle_inverse_gj.argtypes = [ctypes.c_int, f64p, f64p]
+            lib.oracle_inverse_gj.restype = ctypes.c_int
+            lib.oracle_ildu0.argtypes = [I, ctypes.c_int, i32p, i32p, f64p, I, i32p, f64p, f64p]
+            lib.oracle_ildu0.restype = ctypes.c_int
+            lib.oracle_apply_ildu0.argtypes = [I, ctypes.c_int, i32p, i32p, f64p, f64p, I, i32p, f64p, f64p]
+            lib.oracle_apply_ildu0.restype = None
+            lib.oracle_bicgstab_general.argtypes = [I, ctypes.c_int, i32p, i32p, f64p, ctypes.POINTER(_Precond),
+                                                    f64p, vp, f64p, I, D, ctypes.POINTER(_Info), vp]
+            lib.oracle_bicgstab_general.restype = ctypes.c_int
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
+            lib.oracle_set_threads.restype = None
+            lib.oracle_threads.argtypes = []
+            lib.oracle_threads.restype = ctypes.c_int
+            _libs[omp] = lib
+    return _libs[omp]
 
 
 def _ptr(a):
@@ -198,6 +242,46 @@ def ilu0(Add: BSR):
     return lu, int(st)
 
 
+@dataclass
+class ILDU:
+    """ILDU0 factors (Algorithm 7 with Section 4.3's post-processing): ``F`` holds
+    L at strictly-lower and U~ = D^-1 U at strictly-upper positions of the dropped
+    pattern (zero on the diagonal), ``inv_d`` the (n, bs, bs) inverses of U's
+    diagonal blocks, ``part_ptr`` the subdomain row ranges."""
+
+    F: BSR
+    inv_d: np.ndarray
+    part_ptr: np.ndarray
+
+
+def inverse(M: np.ndarray) -> np.ndarray | None:
+    """bs x bs inverse by Gauss-Jordan with partial pivoting (None if singular)."""
+    M = np.ascontiguousarray(M, np.float64)
+    X = np.empty_like(M)
+    return None if _load().oracle_inverse_gj(M.shape[0], M.reshape(-1), X.reshape(-1)) else X
+
+
+def ildu0(Add: BSR, part_ptr: np.ndarray):
+    """Algorithm 7 followed by the ILDU0 post-processing.  Returns (ILDU, status)."""
+    bs = Add.bs
+    pp = np.ascontiguousarray(part_ptr, np.int32)
+    f = np.empty((Add.nnzb, bs, bs), np.float64)
+    inv_d = np.empty((Add.n, bs, bs), np.float64)
+    st = _load().oracle_ildu0(Add.n, bs, Add.row_ptr, Add.col, _f64(Add.val), len(pp) - 1, pp,
+                              f.reshape(-1), inv_d.reshape(-1))
+    return ILDU(BSR(Add.row_ptr, Add.col, f, bs), inv_d, pp), int(st)
+
+
+def apply_ildu0(M: ILDU, r: np.ndarray) -> np.ndarray:
+    """z = U~^-1 D^-1 L^-1 r (sequential substitution per subdomain, ILDU0 form)."""
+    F = M.F
+    bs = F.bs
+    z = np.empty(bs * F.n, np.float64)
+    _load().oracle_apply_ildu0(F.n, bs, F.row_ptr, F.col, _f64(F.val), _f64(M.inv_d), len(M.part_ptr) - 1,
+                               M.part_ptr, _f64(r), z)
+    return z
+
+
 def levels_lower(M: BSR):
     lev = np.empty(M.n, np.int32)
     nl = _load().oracle_levels_lower(M.n, M.row_ptr, M.col, lev)
@@ -247,14 +331,27 @@ class SolveResult:
     history: np.ndarray
 
 
-def bicgstab(A: BSR, LU: BSR, b: np.ndarray, maxit: int = 10000, rtol: float = 1e-8) -> SolveResult:
-    """Algorithm 1 with M = LU; vectors in the reordered numbering."""
+def bicgstab(A: BSR, M, b: np.ndarray, maxit: int = 10000, rtol: float = 1e-8, x0=None) -> SolveResult:
+    """Algorithm 1 with M = LU; vectors in the reordered numbering.  M is the
+    ILU0-form factor matrix (a BSR from ``ilu0``) or an ``ILDU`` (ILDU0 form);
+    x0 is the initial guess (None: zero)."""
     bs = A.bs
     x = np.empty(bs * A.n, np.float64)
     hist = np.zeros(maxit + 1, np.float64)
     info = _Info()
-    _load().oracle_bicgstab(A.n, bs, A.row_ptr, A.col, _f64(A.val), LU.row_ptr, LU.col, _f64(LU.val),
-                            _f64(b), x, maxit, rtol, ctypes.byref(info), _ptr(hist))
+    keep = []
+    if isinstance(M, ILDU):
+        F = M.F
+        fv, dv, pp = _f64(F.val), _f64(M.inv_d), np.ascontiguousarray(M.part_ptr, np.int32)
+        keep += [fv, dv, pp]
+        pc = _Precond(1, len(pp) - 1, _ptr(pp), _ptr(F.row_ptr), _ptr(F.col), None, _ptr(fv), _ptr(dv))
+    else:
+        lv = _f64(M.val)
+        keep.append(lv)
+        pc = _Precond(0, 0, None, _ptr(M.row_ptr), _ptr(M.col), _ptr(lv), None, None)
+    x0a = None if x0 is None else _f64(x0)
+    _load().oracle_bicgstab_general(A.n, bs, A.row_ptr, A.col, _f64(A.val), ctypes.byref(pc), _f64(b),
+                                    _ptr(x0a), x, maxit, rtol, ctypes.byref(info), _ptr(hist))
     it = info.iterations
     return SolveResult(x, info.status, it, info.restarts, info.rel_res_recurrence,
                        info.rel_res_true, hist[: it + 1].copy())
@@ -274,6 +371,15 @@ class Decomposition:
     Add: BSR         # reordered matrix without inter-subdomain blocks
     LU: BSR          # ILU0 factors of Add, same pattern
     status: int
+
+    def ildu(self) -> ILDU:
+        """The ILDU0 factors of Add (computed on first use); raises on a zero pivot."""
+        if getattr(self, "_ildu", None) is None:
+            m, st = ildu0(self.Add, self.part_ptr)
+            if st:
+                raise ArithmeticError(f"singular pivot block at row {-st - 1}")
+            self._ildu = m
+        return self._ildu
 
 
 def decompose(row_ptr, col, val, grid, sub, factor: bool = True) -> Decomposition:

@@ -19,6 +19,11 @@
  *  - Algorithm 7, block form: L unit block-lower with L_ij = W_ij * U_jj^-1,
  *    U keeps full 3x3 diagonal blocks; the update loop runs over k > j.
  *  - 3x3 solves: Gaussian elimination with partial pivoting.
+ *  - ILDU0 form (Section 4.3, Algorithm 7 post-processing), block reading:
+ *    inv_D_i = U_ii^-1 by Gauss-Jordan elimination with partial pivoting,
+ *    L_ij = W_ij * inv_D_j (the block form of U[i,j] / U[j,j], with the
+ *    stored inverse), U~_ik = inv_D_i * U_ik for k > i (the strictly-upper
+ *    blocks; the algorithm's "j < i" loop is read as the text describes).
  *  - Algorithm 1 with K1 = I, K2 = M = LU (right preconditioning), x0 = 0,
  *    stop when ||r||_2 / ||b||_2 < rtol (checked on r_{j+1} only), then one
  *    restart from the true residual if the true residual misses rtol.
@@ -28,6 +33,11 @@
  *
  * Parity pins for every function are in the CPU test suite. Nothing in this
  * file is "parity unpinned".
+ *
+ * Loops over independent subdomains, rows and dot tiles carry OpenMP
+ * pragmas. Built without -fopenmp they are ignored; built with it, every
+ * result is the same bits (no loop with a pragma combines values across its
+ * iterations).
  */
 #include <math.h>
 #include <stdint.h>
@@ -407,6 +417,137 @@ int32_t oracle_levels_upper(int32_t n, const int32_t* row_ptr, const int32_t* co
 }
 
 /* ------------------------------------------------------------------------ */
+/* Algorithm 7 with the ILDU0 post-processing (Section 4.3)                  */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * bs x bs inverse by Gauss-Jordan elimination with partial pivoting on the
+ * augmented matrix [M | I]. For each column c in turn: the row at or below
+ * c with the largest |entry| in column c (the first of equals) is swapped
+ * into row c; row c is multiplied by the reciprocal of its pivot; every
+ * other row r with a nonzero entry m in column c has m times row c
+ * subtracted from it. The right half is then M^-1. Returns 0, or -1 for a
+ * zero or non-finite pivot or a non-finite entry of the result.
+ */
+static int inverse_gj_bs(int bs, const double* M, double* X) {
+  double a[3][6];
+  for (int r = 0; r < bs; ++r)
+    for (int c = 0; c < 2 * bs; ++c) a[r][c] = c < bs ? M[bs * r + c] : (c - bs == r ? 1.0 : 0.0);
+  for (int c = 0; c < bs; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < bs; ++r)
+      if (fabs(a[r][c]) > fabs(a[piv][c])) piv = r;
+    if (!(fabs(a[piv][c]) > 0.0) || !isfinite(a[piv][c])) return -1;
+    if (piv != c)
+      for (int q = 0; q < 2 * bs; ++q) {
+        double t = a[c][q];
+        a[c][q] = a[piv][q];
+        a[piv][q] = t;
+      }
+    double recip = 1.0 / a[c][c];
+    for (int q = 0; q < 2 * bs; ++q) a[c][q] = a[c][q] * recip;
+    for (int r = 0; r < bs; ++r) {
+      if (r == c || a[r][c] == 0.0) continue;
+      double m = a[r][c];
+      for (int q = 0; q < 2 * bs; ++q) a[r][q] = a[r][q] - m * a[c][q];
+    }
+  }
+  for (int r = 0; r < bs; ++r)
+    for (int c = 0; c < bs; ++c) {
+      X[bs * r + c] = a[r][bs + c];
+      if (!isfinite(X[bs * r + c])) return -1;
+    }
+  return 0;
+}
+
+/* Exported for the pins of the inverse on its own. */
+int oracle_inverse_gj(int bs, const double* M, double* X) { return inverse_gj_bs(bs, M, X); }
+
+/* C = A B for bs x bs blocks: each entry sums k = 0..bs-1 in order, from 0, without FMA. */
+static void block_product(int bs, const double* A, const double* B, double* C) {
+  for (int a = 0; a < bs; ++a)
+    for (int c = 0; c < bs; ++c) {
+      double s = 0.0;
+      for (int k = 0; k < bs; ++k) s = s + A[bs * a + k] * B[bs * k + c];
+      C[bs * a + c] = s;
+    }
+}
+
+/*
+ * Block ILU0 followed by the ILDU0 post-processing (Algorithm 7; Section
+ * 4.3), the factors the fused apply uses, on the dropped matrix's pattern.
+ * Row by row (ascending) with a working row W_i* = A_i* (U <- A):
+ *   for each strictly-lower block j of row i, ascending:
+ *     L_ij = W_ij inv_D_j                  (U[i,j] / U[j,j] in block form)
+ *     W_ik = W_ik - L_ij U_jk              for every k > j present in rows i and j
+ *   inv_D_i = W_ii^-1                      (Gauss-Jordan, above)
+ * and afterwards, for every strictly-upper block of row i,
+ *   U~_ik = inv_D_i U_ik                   (U = D U~, unit block diagonal).
+ * Rows of different subdomains share no block (Section 3.2), so the
+ * subdomains part_ptr[p] .. part_ptr[p+1] are factored independently.
+ * f receives L at strictly-lower positions, U~ at strictly-upper positions
+ * and zero on the diagonal; inv_d (bs*bs per row) receives inv_D. Returns 0,
+ * or -(row+1) for the first subdomain's failing pivot block in row order.
+ */
+int oracle_ildu0(int32_t n, int bs, const int32_t* row_ptr, const int32_t* col, const double* val,
+                 int32_t nparts, const int32_t* part_ptr, double* f, double* inv_d) {
+  const int bb = bs * bs;
+  int32_t* fail = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nparts > 0 ? nparts : 1));
+  int32_t p;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (p = 0; p < nparts; ++p) {
+    const int32_t r0 = part_ptr[p], r1 = part_ptr[p + 1];
+    const int64_t q0 = row_ptr[r0], q1 = row_ptr[r1];
+    double* W = (double*)malloc(sizeof(double) * (size_t)bb * (size_t)(q1 > q0 ? q1 - q0 : 1));
+    int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)(r1 > r0 ? r1 - r0 : 1));
+    fail[p] = -1;
+    memcpy(W, val + bb * q0, sizeof(double) * (size_t)bb * (size_t)(q1 - q0));
+    for (int32_t c = r0; c < r1; ++c) pos[c - r0] = -1;
+    for (int32_t i = r0; i < r1 && fail[p] < 0; ++i) {
+      int64_t d = -1;
+      for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+        pos[col[q] - r0] = q;
+        if (col[q] == i) d = q;
+      }
+      if (d < 0) { fail[p] = i; break; }
+      for (int64_t q = row_ptr[i]; q < row_ptr[i + 1] && col[q] < i; ++q) {
+        const int32_t j = col[q];
+        double Lij[9], prod[9];
+        block_product(bs, W + bb * (q - q0), inv_d + bb * (int64_t)j, Lij);
+        memcpy(W + bb * (q - q0), Lij, sizeof(double) * bb);
+        for (int64_t t = row_ptr[j]; t < row_ptr[j + 1]; ++t) {
+          const int32_t k = col[t];
+          if (k <= j || pos[k - r0] < 0) continue;
+          block_product(bs, Lij, W + bb * (t - q0), prod);
+          double* Wik = W + bb * (pos[k - r0] - q0);
+          for (int e = 0; e < bb; ++e) Wik[e] = Wik[e] - prod[e];
+        }
+      }
+      if (inverse_gj_bs(bs, W + bb * (d - q0), inv_d + bb * (int64_t)i)) fail[p] = i;
+      for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) pos[col[q] - r0] = -1;
+    }
+    if (fail[p] < 0)
+      for (int32_t i = r0; i < r1; ++i)
+        for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+          double* dst = f + bb * q;
+          if (col[q] < i)
+            memcpy(dst, W + bb * (q - q0), sizeof(double) * bb);
+          else if (col[q] > i)
+            block_product(bs, inv_d + bb * (int64_t)i, W + bb * (q - q0), dst);
+          else
+            for (int e = 0; e < bb; ++e) dst[e] = 0.0;
+        }
+    free(W);
+    free(pos);
+  }
+  int status = 0;
+  for (int32_t q = 0; q < nparts && status == 0; ++q)
+    if (fail[q] >= 0) status = -(fail[q] + 1);
+  free(fail);
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Preconditioner apply, SpMV, dot                                           */
 /* ------------------------------------------------------------------------ */
 
@@ -447,11 +588,68 @@ int oracle_apply(int32_t n, int bs, const int32_t* row_ptr, const int32_t* col, 
   return status;
 }
 
+/*
+ * z = U~^-1 D^-1 L^-1 r with the ILDU0 factors of oracle_ildu0 (Section
+ * 4.3; the fused kernel of Section 4.4 computes the same rows level by
+ * level, Algorithm 6), by plain sequential substitution:
+ *   y_i = r_i - sum_j L_ij y_j        for i ascending (strictly-lower j)
+ *   w_i = inv_D_i y_i
+ *   z_i = w_i - sum_k U~_ik z_k       for i descending (strictly-upper k)
+ * Per output entry a, the sums take blocks in ascending column order and
+ * block entries c = 0..bs-1, each with a fused multiply-add; w_i[a] =
+ * inv_D[a][0] y_i[0], then fma(inv_D[a][c], y_i[c], .) for c = 1..bs-1. The
+ * factors couple no two subdomains (Section 3.2), so each subdomain range
+ * part_ptr[p] .. part_ptr[p+1] is substituted on its own.
+ */
+void oracle_apply_ildu0(int32_t n, int bs, const int32_t* row_ptr, const int32_t* col, const double* f,
+                        const double* inv_d, int32_t nparts, const int32_t* part_ptr, const double* r,
+                        double* z) {
+  const int bb = bs * bs;
+  (void)n;
+  int32_t p;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (p = 0; p < nparts; ++p) {
+    const int32_t r0 = part_ptr[p], r1 = part_ptr[p + 1];
+    for (int32_t i = r0; i < r1; ++i) {
+      double y[3];
+      for (int a = 0; a < bs; ++a) {
+        double acc = r[bs * (int64_t)i + a];
+        for (int64_t q = row_ptr[i]; q < row_ptr[i + 1] && col[q] < i; ++q)
+          for (int c = 0; c < bs; ++c) acc = fma(-f[bb * q + bs * a + c], z[bs * (int64_t)col[q] + c], acc);
+        y[a] = acc;
+      }
+      /* L results are kept in z until the backward sweep overwrites them */
+      for (int a = 0; a < bs; ++a) z[bs * (int64_t)i + a] = y[a];
+    }
+    for (int32_t i = r1 - 1; i >= r0; --i) {
+      const double* D = inv_d + bb * (int64_t)i;
+      const double* y = z + bs * (int64_t)i;
+      double w[3];
+      for (int a = 0; a < bs; ++a) {
+        double acc = D[bs * a] * y[0];
+        for (int c = 1; c < bs; ++c) acc = fma(D[bs * a + c], y[c], acc);
+        w[a] = acc;
+      }
+      for (int a = 0; a < bs; ++a) {
+        double acc = w[a];
+        for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+          if (col[q] <= i) continue;
+          for (int c = 0; c < bs; ++c) acc = fma(-f[bb * q + bs * a + c], z[bs * (int64_t)col[q] + c], acc);
+        }
+        w[a] = acc;
+      }
+      for (int a = 0; a < bs; ++a) z[bs * (int64_t)i + a] = w[a];
+    }
+  }
+}
+
 /* y = A x: per scalar row, blocks in ascending column order, c = 0..bs-1, FMA from 0. */
 void oracle_spmv(int32_t n, int bs, const int32_t* row_ptr, const int32_t* col, const double* val,
                  const double* x, double* y) {
   const int bb = bs * bs;
-  for (int32_t i = 0; i < n; ++i)
+  int32_t i;
+#pragma omp parallel for schedule(static)
+  for (i = 0; i < n; ++i)
     for (int a = 0; a < bs; ++a) {
       double acc = 0.0;
       for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q)
@@ -483,8 +681,10 @@ double oracle_dot(int32_t n, int bs, const double* x, const double* y) {
   int64_t m = 1;
   while (m < ntiles) m *= 2;
   double* tile = (double*)calloc((size_t)m, sizeof(double));
-  double q[DOT_TILE];
-  for (int64_t t = 0; t < ntiles; ++t) {
+  int64_t t;
+#pragma omp parallel for schedule(static)
+  for (t = 0; t < ntiles; ++t) {
+    double q[DOT_TILE];
     for (int r = 0; r < DOT_TILE; ++r) {
       int64_t i = t * DOT_TILE + r;
       q[r] = 0.0;
@@ -519,46 +719,88 @@ typedef struct {
 static double rel_of(double rr, double bb) { return sqrt(rr) / sqrt(bb); }
 
 /*
- * Solve A x = b with M = LU (right preconditioning), x0 = 0. A is the full
- * reordered matrix, (lrp, lcol, lu) the ILU0 factors of the dropped one. All
- * vectors are in the reordered numbering. hist (optional, maxit + 1 entries)
- * receives ||r_j|| / ||b|| with hist[0] = 1.
+ * The preconditioner M = LU of a solve, in one of two forms:
+ *   form 0: lu from oracle_ilu0, applied by oracle_apply (ILU0 form);
+ *   form 1: f and inv_d from oracle_ildu0, applied by oracle_apply_ildu0
+ *           over the subdomains part_ptr[0..nparts] (ILDU0 form, Section 4.3).
+ * Both forms are M^-1 of the same M in exact arithmetic.
  */
-int oracle_bicgstab(int32_t n, int bs, const int32_t* arp, const int32_t* acol, const double* aval,
-                    const int32_t* lrp, const int32_t* lcol, const double* lu, const double* b,
-                    double* x, int32_t maxit, double rtol, oracle_info* info, double* hist) {
+typedef struct {
+  int32_t form, nparts;
+  const int32_t* part_ptr;
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const double* lu;
+  const double* f;
+  const double* inv_d;
+} oracle_precond;
+
+static int precond_apply(int32_t n, int bs, const oracle_precond* M, const double* r, double* z) {
+  if (M->form == 0) return oracle_apply(n, bs, M->row_ptr, M->col, M->lu, r, z);
+  oracle_apply_ildu0(n, bs, M->row_ptr, M->col, M->f, M->inv_d, M->nparts, M->part_ptr, r, z);
+  return 0;
+}
+
+/*
+ * Algorithm 1 read as right preconditioning (K1 = I, K2 = M): solve A x = b.
+ * A is the full reordered matrix. x0 is the initial guess (NULL: x0 = 0,
+ * the solver runs' reading). All vectors are in the reordered numbering.
+ *   r = b - A x0, r^ = r, rho = r^ . r, p = r
+ *   per iteration j: p^ = M^-1 p, v = A p^, alpha = rho / (r^ . v),
+ *     s = r - alpha v, s^ = M^-1 s, t = A s^, omega = (t . s) / (t . t),
+ *     x = x + alpha p^ + omega s^, r = s - omega t,
+ *     stop if ||r|| / ||b|| < rtol (iterations = j + 1),
+ *     rho' = r^ . r, beta = (alpha / omega)(rho' / rho), p = r + beta (p - omega v).
+ * After the recurrence converges, the true residual b - A x is formed; if it
+ * misses rtol, the iteration restarts once from it (r = r^ = p = b - A x,
+ * rho = r^ . r), the iteration count carrying on. hist (optional, maxit + 1
+ * entries) receives ||r_j|| / ||b|| with hist[0] = ||r_0|| / ||b||.
+ */
+static int bicgstab_core(int32_t n, int bs, const int32_t* arp, const int32_t* acol, const double* aval,
+                         const oracle_precond* M, const double* b, const double* x0, double* x, int32_t maxit,
+                         double rtol, oracle_info* info, double* hist) {
   size_t m = bs * (size_t)(n > 0 ? n : 1);
   double *r = calloc(m, 8), *rh = calloc(m, 8), *p = calloc(m, 8), *v = calloc(m, 8);
   double *s = calloc(m, 8), *t = calloc(m, 8), *ph = calloc(m, 8), *sh = calloc(m, 8);
-  int64_t len = bs * (int64_t)n;
+  int64_t len = bs * (int64_t)n, e;
   memset(info, 0, sizeof *info);
-  for (int64_t e = 0; e < len; ++e) x[e] = 0.0;
+  for (e = 0; e < len; ++e) x[e] = 0.0;
   double bb = oracle_dot(n, bs, b, b);
   int status = ORC_NOT_CONVERGED;
   if (!(bb > 0.0)) {
     status = ORC_OK; /* b = 0: x = 0 is exact */
     goto done;
   }
-  for (int64_t e = 0; e < len; ++e) r[e] = b[e];
-  if (hist) hist[0] = 1.0;
+  if (x0) {
+    for (e = 0; e < len; ++e) x[e] = x0[e];
+    oracle_spmv(n, bs, arp, acol, aval, x, t);
+#pragma omp parallel for schedule(static)
+    for (e = 0; e < len; ++e) r[e] = b[e] - t[e];
+  } else {
+    for (e = 0; e < len; ++e) r[e] = b[e];
+  }
+  if (hist) hist[0] = rel_of(oracle_dot(n, bs, r, r), bb);
   int j = 0;
   for (int restart = 0; restart < 2; ++restart) {
-    for (int64_t e = 0; e < len; ++e) rh[e] = r[e], p[e] = r[e];
+#pragma omp parallel for schedule(static)
+    for (e = 0; e < len; ++e) rh[e] = r[e], p[e] = r[e];
     double rho = oracle_dot(n, bs, rh, r);
     int converged = 0;
     for (; j < maxit; ++j) {
-      if (oracle_apply(n, bs, lrp, lcol, lu, p, ph)) { status = ORC_ZERO_PIVOT; goto done; }
+      if (precond_apply(n, bs, M, p, ph)) { status = ORC_ZERO_PIVOT; goto done; }
       oracle_spmv(n, bs, arp, acol, aval, ph, v);
       double rv = oracle_dot(n, bs, rh, v);
       if (rv == 0.0 || !isfinite(rv)) { status = ORC_BREAKDOWN; goto done; }
       double alpha = rho / rv;
-      for (int64_t e = 0; e < len; ++e) s[e] = fma(-alpha, v[e], r[e]);
-      if (oracle_apply(n, bs, lrp, lcol, lu, s, sh)) { status = ORC_ZERO_PIVOT; goto done; }
+#pragma omp parallel for schedule(static)
+      for (e = 0; e < len; ++e) s[e] = fma(-alpha, v[e], r[e]);
+      if (precond_apply(n, bs, M, s, sh)) { status = ORC_ZERO_PIVOT; goto done; }
       oracle_spmv(n, bs, arp, acol, aval, sh, t);
       double ts = oracle_dot(n, bs, t, s);
       double tt = oracle_dot(n, bs, t, t);
       double omega = tt == 0.0 ? 0.0 : ts / tt;
-      for (int64_t e = 0; e < len; ++e) {
+#pragma omp parallel for schedule(static)
+      for (e = 0; e < len; ++e) {
         x[e] = fma(omega, sh[e], fma(alpha, ph[e], x[e]));
         r[e] = fma(-omega, t[e], s[e]);
       }
@@ -571,14 +813,16 @@ int oracle_bicgstab(int32_t n, int bs, const int32_t* arp, const int32_t* acol, 
       double rho_new = oracle_dot(n, bs, rh, r);
       if (rho_new == 0.0 || omega == 0.0 || !isfinite(rho_new)) { status = ORC_BREAKDOWN; goto done; }
       double beta = (alpha / omega) * (rho_new / rho);
-      for (int64_t e = 0; e < len; ++e) p[e] = fma(beta, fma(-omega, v[e], p[e]), r[e]);
+#pragma omp parallel for schedule(static)
+      for (e = 0; e < len; ++e) p[e] = fma(beta, fma(-omega, v[e], p[e]), r[e]);
       rho = rho_new;
     }
     info->iterations = j;
     if (!converged) { status = ORC_NOT_CONVERGED; goto done; }
     /* true residual r = b - A x */
     oracle_spmv(n, bs, arp, acol, aval, x, t);
-    for (int64_t e = 0; e < len; ++e) r[e] = b[e] - t[e];
+#pragma omp parallel for schedule(static)
+    for (e = 0; e < len; ++e) r[e] = b[e] - t[e];
     double rel_true = rel_of(oracle_dot(n, bs, r, r), bb);
     info->rel_res_true = rel_true;
     if (rel_true < rtol) { status = ORC_OK; goto done; }
@@ -590,3 +834,31 @@ done:
   free(r); free(rh); free(p); free(v); free(s); free(t); free(ph); free(sh);
   return status;
 }
+
+/* Algorithm 1 with the ILU0-form preconditioner (lu of oracle_ilu0), x0 = 0. */
+int oracle_bicgstab(int32_t n, int bs, const int32_t* arp, const int32_t* acol, const double* aval,
+                    const int32_t* lrp, const int32_t* lcol, const double* lu, const double* b,
+                    double* x, int32_t maxit, double rtol, oracle_info* info, double* hist) {
+  oracle_precond M = {0, 0, NULL, lrp, lcol, lu, NULL, NULL};
+  return bicgstab_core(n, bs, arp, acol, aval, &M, b, NULL, x, maxit, rtol, info, hist);
+}
+
+/*
+ * Algorithm 1 with either preconditioner form (oracle_precond above) and an
+ * initial guess x0 (NULL: zero).
+ */
+int oracle_bicgstab_general(int32_t n, int bs, const int32_t* arp, const int32_t* acol, const double* aval,
+                            const oracle_precond* M, const double* b, const double* x0, double* x,
+                            int32_t maxit, double rtol, oracle_info* info, double* hist) {
+  return bicgstab_core(n, bs, arp, acol, aval, M, b, x0, x, maxit, rtol, info, hist);
+}
+
+/* Threads of the OpenMP build (no effect without it). */
+#ifdef _OPENMP
+#include <omp.h>
+void oracle_set_threads(int k) { omp_set_num_threads(k > 0 ? k : 1); }
+int oracle_threads(void) { return omp_get_max_threads(); }
+#else
+void oracle_set_threads(int k) { (void)k; }
+int oracle_threads(void) { return 1; }
+#endif
