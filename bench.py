@@ -198,7 +198,8 @@ def run_ours(args):
 
     # ---- timed iterations (FP64; rtol 0 so no step can stop early)
     t_setup = time.perf_counter()
-    ctx = pkg.Ilu0DD(s.row_ptr, s.col, s.val, grid, sub, rtol=1e-300, maxit=10 ** 6)
+    ctx = pkg.Ilu0DD(s.row_ptr, s.col, s.val, grid, sub, rtol=1e-300, maxit=10 ** 6,
+                     factor_prec=args.factor_prec)
     setup_s = time.perf_counter() - t_setup
     apply_b = ctx.query("apply_bytes")
     spmv_b = ctx.query("spmv_bytes")
@@ -355,7 +356,8 @@ def run_ours(args):
 
     if rank != 0:
         return
-    traffic = recorded_traffic("ildu0_apply", args.workload)
+    traffic = recorded_traffic("ildu0_apply" if args.factor_prec == "f64" else f"ildu0_apply_{args.factor_prec}",
+                               args.workload)
     line = {
         "metric": METRIC,
         "value": round(apply_gbs, 2),
@@ -367,9 +369,10 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": args.factor_prec,
         "data": "synthetic (seeded layered 3x3-block 7-point stencil; no dataset)",
         "config": {"workload": args.workload, "grid": list(grid), "subdomain": list(sub),
+                   "factor_prec": args.factor_prec,
                    "block_rows": n, "blocks": s.nnzb,
                    "subdomains": int(np.prod([-(-g // sb) for g, sb in zip(grid, sub)])),
                    "step": "one BiCGSTAB iteration: 2 fused applies + 2 SpMV/dot + fused update/dot",
@@ -380,7 +383,7 @@ def run_ours(args):
                      # DRAM GB/s from the ncu bytes per launch over the mean mode P/S launch time
                      "dram_gbs_from_traffic": None if traffic is None else round(
                          traffic / (0.5 * (per_kernel["apply_p"]["ms"] + per_kernel["apply_s"]["ms"]) * 1e6), 1),
-                     "kernel": "ildu0_apply_kernel<double, P|S>", "peak_source": f"{peak_kind} hbm_gbs",
+                     "kernel": f"ildu0_apply_kernel<{args.factor_prec}, P|S>", "peak_source": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": {"apply_p": bytes_k[0], "apply_s": bytes_k[2]}},
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
@@ -785,6 +788,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precisions", default="f64,df64,f32,bf16")
+    ap.add_argument("--factor-prec", default="f64", choices=["f64", "df64", "f32", "bf16"],
+                    help="factor storage of the timed iterations (the headline is f64)")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
