@@ -68,11 +68,17 @@ extern "C" {
 /* ---- inputs ----------------------------------------------------------- */
 
 /* Block-CSR matrix in natural cell order gidx = i + nx*(j + ny*k) (grid
- * path) or any order (partitioned path). HOST pointers: row_ptr[n_brows+1],
- * col_idx[nnzb] (strictly ascending per row, diagonal block present),
- * val[bs*bs*nnzb] (row-major bs x bs blocks). block_dim = bs: 3 (also 0) for
- * 3x3 blocks, 1 for a scalar CSR matrix; vectors then hold bs*n_brows
- * doubles. */
+ * path) or any order (partitioned path): row_ptr[n_brows+1], col_idx[nnzb]
+ * (strictly ascending per row, diagonal block present), val[bs*bs*nnzb]
+ * (row-major bs x bs blocks). block_dim = bs: 3 (also 0) for 3x3 blocks, 1
+ * for a scalar CSR matrix; vectors then hold bs*n_brows doubles.
+ * Each array may be in host memory or in device memory of the current device
+ * (the library tells them apart with cudaPointerGetAttributes). The
+ * structural setup runs on the host, so device-resident row_ptr and col_idx
+ * are copied to host memory for it (a synchronous copy); device-resident
+ * values go to the device numeric setup (ilu0_dd_setup_planned with scratch)
+ * by a device-to-device copy, and are copied to the host only for the host
+ * numeric setup. The caller keeps ownership; nothing is kept after setup. */
 typedef struct {
   int32_t n_brows;
   int32_t block_dim;
@@ -99,6 +105,13 @@ typedef struct {
   int32_t use_graphs;       /* 1 = capture iterations as CUDA graphs (default), 0 = plain launches */
   int32_t keep_host;        /* 1 = keep host copies of factors and levels for ilu0_dd_export */
   int32_t trace;            /* 1 = print per-phase timings to stderr */
+  int32_t traversal;        /* apply traversal of a level (Section 4.2.3), used by ilu0_dd_apply and
+                               bicgstab_solve: 0 = vertex-centric, rows in a fixed order (default,
+                               deterministic); 1 = edge-centric, the blocks of a level spread over
+                               threads with shared-memory atomic adds (the paper's fastest kernel on
+                               MI210; its rounding order, hence the iteration count, may vary).
+                               1 is not available with ILU0DD_DF64 (ILU0DD_ERR_INVALID); batched
+                               solves always use 0. */
 } ilu0dd_opts;
 
 typedef struct {

@@ -51,7 +51,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("factor_prec", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
                 ("prefetch_bytes", ctypes.c_int32), ("maxit", ctypes.c_int32), ("rtol", ctypes.c_double),
                 ("check_every", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
-                ("keep_host", ctypes.c_int32), ("trace", ctypes.c_int32)]
+                ("keep_host", ctypes.c_int32), ("trace", ctypes.c_int32), ("traversal", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -157,26 +157,46 @@ def default_opts(**kw) -> Opts:
     return o
 
 
-def _block_dim(nnzb, val):
-    """bs of a value array: its last dimension, or sqrt(size / nnzb) when flat."""
-    if val is None or nnzb == 0:
-        return 3
-    v = np.asarray(val)
-    if v.ndim == 3:
-        return int(v.shape[-1])
-    bs = int(round((v.size / nnzb) ** 0.5))
-    if bs * bs * nnzb != v.size:
-        raise ValueError("val must hold bs*bs values per block")
-    return bs
+def _is_cuda(a) -> bool:
+    return getattr(a, "is_cuda", False)
+
+
+def _arr(a, np_dtype, torch_dtype, name):
+    """(address, keep-alive, element count) of one matrix array: a numpy-like
+    host array, or a contiguous CUDA tensor (device memory, passed by address)."""
+    if _is_cuda(a):
+        if a.dtype != torch_dtype or not a.is_contiguous():
+            raise ValueError(f"{name}: a device array must be a contiguous CUDA tensor of {torch_dtype}")
+        return a.data_ptr(), a, int(a.numel())
+    h = np.ascontiguousarray(a, np_dtype).reshape(-1)
+    return h.ctypes.data, h, int(h.size)
 
 
 def _bsr(row_ptr, col, val):
-    rp = np.ascontiguousarray(row_ptr, np.int32)
-    ci = np.ascontiguousarray(col, np.int32)
-    bs = _block_dim(int(rp[-1]), val)
-    va = None if val is None else np.ascontiguousarray(val, np.float64).reshape(-1)
-    b = Bsr(len(rp) - 1, bs, int(rp[-1]), rp.ctypes.data, ci.ctypes.data, None if va is None else va.ctypes.data)
-    return b, (rp, ci, va)
+    """ilu0dd_bsr of the matrix arrays, each in host memory (numpy) or in device
+    memory (a CUDA tensor: int32 row_ptr and col, float64 val)."""
+    import_torch = any(_is_cuda(a) for a in (row_ptr, col, val))
+    tdt = (None, None)
+    if import_torch:
+        import torch
+        tdt = (torch.int32, torch.float64)
+    rp_p, rp_k, n1 = _arr(row_ptr, np.int32, tdt[0], "row_ptr")
+    ci_p, ci_k, nnzb = _arr(col, np.int32, tdt[0], "col")
+    if val is None:
+        va_p, va_k, bs = None, None, 3
+    else:
+        if not _is_cuda(val) and np.ndim(val) == 3:
+            bs = int(np.shape(val)[-1])
+        elif nnzb == 0:
+            bs = 3
+        else:
+            nv = int(val.numel()) if _is_cuda(val) else int(np.size(val))
+            bs = int(round((nv / nnzb) ** 0.5))
+            if bs * bs * nnzb != nv:
+                raise ValueError("val must hold bs*bs values per block")
+        va_p, va_k, _ = _arr(val, np.float64, tdt[1], "val")
+    b = Bsr(n1 - 1, bs, nnzb, rp_p, ci_p, va_p)
+    return b, (rp_k, ci_k, va_k)
 
 
 def partition_bfs(row_ptr, col, part_rows: int):
@@ -241,8 +261,9 @@ def _dptr(t, n=None, what="vector"):
 class Ilu0DD:
     """Subdomain ILU0 preconditioner + BiCGSTAB solver on one GPU.
 
-    ``row_ptr``, ``col``, ``val`` are host arrays of the natural-order BSR
-    matrix (``val`` of shape (nnzb, 3, 3) or flat); ``grid`` = (nx, ny, nz),
+    ``row_ptr``, ``col``, ``val`` are the natural-order BSR matrix, host
+    arrays (``val`` of shape (nnzb, 3, 3) or flat) or CUDA tensors (device
+    memory: int32, int32, float64); ``grid`` = (nx, ny, nz),
     ``sub`` = (sx, sy, sz) are the inputs of Algorithm 2. ``device_setup``
     factors and packs on the GPU (ilu0_dd_setup_planned with scratch), else on
     the host; both give the same bits.

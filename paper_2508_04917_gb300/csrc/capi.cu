@@ -67,6 +67,57 @@ int max_smem_optin() {
 
 namespace {
 
+// The matrix arrays of ilu0dd_bsr may be host memory or device memory of the
+// current device, each on its own (told apart by cudaPointerGetAttributes;
+// without a device every pointer is host memory). The structural plan reads
+// the pattern on the host, so device-resident row_ptr and col_idx are copied
+// to host buffers first; device-resident values go straight to the device
+// numeric setup and are copied to the host only for the host numeric setup.
+bool device_resident(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice;
+}
+
+struct HostMatrix {
+  ilu0dd_bsr bsr{};  // the caller's matrix with host pointers for what was copied
+  std::vector<int32_t> rp, col;
+  std::vector<double> val;
+};
+
+// Host view of A: the pattern always, the values when `values` is set.
+int host_matrix(const ilu0dd_bsr* A, bool values, HostMatrix* h) {
+  h->bsr = *A;
+  if (A->n_brows < 0 || A->nnzb < 0) return ILU0DD_OK;  // make_plan reports it
+  const size_t n1 = (size_t)A->n_brows + 1, nb = (size_t)A->nnzb;
+  const int bs = A->block_dim == 1 ? 1 : 3;
+  cudaError_t e = cudaSuccess;
+  if (device_resident(A->row_ptr)) {
+    h->rp.resize(n1);
+    e = cudaMemcpy(h->rp.data(), A->row_ptr, sizeof(int32_t) * n1, cudaMemcpyDeviceToHost);
+    h->bsr.row_ptr = h->rp.data();
+  }
+  if (e == cudaSuccess && nb && device_resident(A->col_idx)) {
+    h->col.resize(nb);
+    e = cudaMemcpy(h->col.data(), A->col_idx, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost);
+    h->bsr.col_idx = h->col.data();
+  }
+  if (e == cudaSuccess && values && nb && device_resident(A->val)) {
+    h->val.resize((size_t)bs * bs * nb);
+    e = cudaMemcpy(h->val.data(), A->val, sizeof(double) * h->val.size(), cudaMemcpyDeviceToHost);
+    h->bsr.val = h->val.data();
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return ILU0DD_ERR_CUDA;
+  }
+  return ILU0DD_OK;
+}
+
 // The numeric half of setup (ILU0, ILDU0, packing, upload) for a context whose
 // plan is in place. d_scratch != nullptr runs ILU0 and the packing on the
 // device (setup_dev.cu); else on the host. Deletes the context on failure.
@@ -105,6 +156,13 @@ int setup_numeric(ilu0dd_ctx* c, const ilu0dd_bsr* A, const ilu0dd_opts& o, void
       return rc;
     }
   } else {
+    HostMatrix hv;  // the host numeric setup reads the values on the host
+    if (host_matrix(A, true, &hv)) {
+      c->why = "copy of the device-resident values to the host failed";
+      delete c;
+      return ILU0DD_ERR_CUDA;
+    }
+    A = &hv.bsr;
     rc = factor_ildu0(p, A->val, &F, &invD, &bad);
     if (rc) {
       if (c->trace) std::fprintf(stderr, "[ilu0dd] setup: zero pivot at reordered row %d\n", bad);
@@ -190,6 +248,7 @@ int setup_numeric(ilu0dd_ctx* c, const ilu0dd_bsr* A, const ilu0dd_opts& o, void
     d.smem_bytes = p.smem_bytes;
     d.smem_rowsync = p.smem_rowsync;
     d.bs = p.bs;
+    d.traversal = o.traversal;
     e = apply_configure(d);
     if (e == cudaSuccess) e = set_wait_us(c, kApplyWaitUs);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
@@ -274,7 +333,9 @@ int ilu0_dd_workspace_size(const ilu0dd_bsr* A, const ilu0dd_geom* geom, const i
   ilu0dd_opts o = resolved(opts);
   Plan p;
   std::string why;
-  int rc = make_plan(A, geom, &o, max_smem_optin(), &p, &why);
+  HostMatrix hv;
+  if (host_matrix(A, false, &hv)) return ILU0DD_ERR_CUDA;
+  int rc = make_plan(&hv.bsr, geom, &o, max_smem_optin(), &p, &why);
   if (rc) {
     if (o.trace) std::fprintf(stderr, "[ilu0dd] workspace_size: %s\n", why.c_str());
     return rc;
@@ -292,7 +353,12 @@ int ilu0_dd_setup(const ilu0dd_bsr* A, const ilu0dd_geom* geom, const ilu0dd_opt
   ilu0dd_ctx* c = new (std::nothrow) ilu0dd_ctx();
   if (!c) return ILU0DD_ERR_INVALID;
   c->trace = o.trace != 0;
-  int rc = make_plan(A, geom, &o, max_smem_optin(), &c->plan, &c->why);
+  HostMatrix hv;
+  if (host_matrix(A, false, &hv)) {
+    delete c;
+    return ILU0DD_ERR_CUDA;
+  }
+  int rc = make_plan(&hv.bsr, geom, &o, max_smem_optin(), &c->plan, &c->why);
   if (rc) {
     if (c->trace) std::fprintf(stderr, "[ilu0dd] setup: %s\n", c->why.c_str());
     delete c;
@@ -309,7 +375,12 @@ int ilu0dd_plan_create(const ilu0dd_bsr* A, const ilu0dd_geom* geom, const ilu0d
   if (!pl) return ILU0DD_ERR_INVALID;
   pl->t0 = wall_seconds();
   pl->opts = resolved(opts);
-  int rc = make_plan(A, geom, &pl->opts, max_smem_optin(), &pl->plan, &pl->why);
+  HostMatrix hv;
+  if (host_matrix(A, false, &hv)) {
+    delete pl;
+    return ILU0DD_ERR_CUDA;
+  }
+  int rc = make_plan(&hv.bsr, geom, &pl->opts, max_smem_optin(), &pl->plan, &pl->why);
   if (rc) {
     if (pl->opts.trace) std::fprintf(stderr, "[ilu0dd] plan: %s\n", pl->why.c_str());
     delete pl;
@@ -331,7 +402,12 @@ int ilu0dd_plan_create_partitioned(const ilu0dd_bsr* A, const int32_t* part_id, 
   if (!pl) return ILU0DD_ERR_INVALID;
   pl->t0 = wall_seconds();
   pl->opts = resolved(opts);
-  int rc = make_plan(A, nullptr, &pl->opts, max_smem_optin(), &pl->plan, &pl->why, part_id, nparts);
+  HostMatrix hv;
+  if (host_matrix(A, false, &hv)) {
+    delete pl;
+    return ILU0DD_ERR_CUDA;
+  }
+  int rc = make_plan(&hv.bsr, nullptr, &pl->opts, max_smem_optin(), &pl->plan, &pl->why, part_id, nparts);
   if (rc) {
     if (pl->opts.trace) std::fprintf(stderr, "[ilu0dd] plan: %s\n", pl->why.c_str());
     delete pl;
@@ -345,7 +421,10 @@ int ilu0dd_plan_create_partitioned(const ilu0dd_bsr* A, const int32_t* part_id, 
 }
 
 int ilu0dd_partition_bfs(const ilu0dd_bsr* A, int32_t part_rows, int32_t* part_id, int32_t* nparts) {
-  return partition_bfs(A, part_rows, part_id, nparts);
+  if (!A) return ILU0DD_ERR_INVALID;
+  HostMatrix hv;
+  if (host_matrix(A, false, &hv)) return ILU0DD_ERR_CUDA;
+  return partition_bfs(&hv.bsr, part_rows, part_id, nparts);
 }
 
 int ilu0_dd_setup_planned(ilu0dd_plan* plan, const ilu0dd_bsr* A, void* d_workspace, size_t ws_bytes,

@@ -39,12 +39,37 @@ namespace ilu0dd {
 //   T   vals[...]              per slot s: bs * bs * cnt[s] values as above
 //   pad to 16
 // T is the factor storage type (double, float, bf16 or a float pair). With
-// 3x3 blocks each warp of a block covers ten rows of a piece with lanes 0..29
-// (lane = 3 * row + a; lanes 30 and 31 idle), so the three threads of a row
-// share a warp and exchange values with shuffles; with scalar rows (bs = 1) a
-// warp covers 32 rows.
+// 3x3 FP64 or float-pair blocks each warp of a block covers ten rows of a piece with lanes
+// 0..29 (lane = 3 * row + a; lanes 30 and 31 idle), so the three threads of a
+// row share a warp and exchange values with shuffles; with scalar rows (bs = 1)
+// a warp covers 32 rows.
+//
+// Row-thread layout (3x3 blocks with FP32 or BF16 factors): one
+// thread per row (32 rows per warp) computes all three components. Every value
+// array (D^-1 of the n rows, then each slot's cnt[s] blocks) starts on a
+// 16-byte boundary and holds entry e = 3a + c of row t's block in 16-byte
+// planes of V = 16 / sizeof(T) entries: entries e < 8 in plane e / V at byte
+// (plane * count + t) * 16 + (e % V) * sizeof(T), entry 8 after the planes at
+// 8 * sizeof(T) * count + t * sizeof(T); so a thread reads its row's nine
+// entries with two (BF16) or three (FP32) loads, and the
+// threads of a warp read consecutive 16-byte vectors.
 // ---------------------------------------------------------------------------
 constexpr int kRowsPerWarp = 10;
+
+#if defined(__CUDACC__)
+#define ILU0DD_HD __host__ __device__
+#else
+#define ILU0DD_HD
+#endif
+
+// Row-thread layout: byte offset of entry e of row t in a value array of
+// `count` rows, and the array's size (padded to 16 bytes); fe = sizeof(T).
+ILU0DD_HD inline int64_t rt_value_offset(int e, int t, int count, int fe) {
+  const int v = 16 / fe;
+  return e < 8 ? ((int64_t)(e / v) * count + t) * 16 + (int64_t)(e % v) * fe
+               : 8ll * fe * count + (int64_t)t * fe;
+}
+ILU0DD_HD inline int64_t rt_slot_bytes(int count, int fe) { return (9ll * fe * count + 15) / 16 * 16; }
 constexpr int kDescSlots = 3;   // slot counts carried in the descriptor
 // Piece descriptors staged in shared memory at a time: 124 keeps the largest
 // FP64 box that fits (16x16x37 cells, 222 KiB of vector) within 227 KiB with
@@ -108,9 +133,19 @@ enum CounterId : int { kCntInit = 0, kCntSpmvV, kCntSpmvT, kCntUpdate, kCntResid
 constexpr int kSlice = 32;
 // Block rows per tile of the fixed dot order.
 constexpr int kDotTile = 256;
-// Maximum apply threads per block, and blocks per SM the register budget targets.
+// Maximum apply threads per block, and blocks per SM the register budget
+// targets: 384 and 3 (56 registers) for the three-thread and scalar
+// mappings; for the row-thread layout, whose threads hold whole 3x3 blocks,
+// 256 and 3 with FP32 factors (80 registers: three slots of blocks load
+// ahead of the level wait without spilling) and 256 and 4 with BF16 (64).
+// Measured at 160^3 (plain apply, 192 threads): FP32 0.285 ms at 64
+// registers (one slot ahead), 0.255 ms at 80; BF16 0.193 ms at 64, 0.216 ms
+// at 80.
 constexpr int kMaxApplyThreads = 384;
 constexpr int kApplyMinBlocks = 3;
+constexpr int kMaxRtThreads = 256;
+constexpr int kRtMinBlocksF32 = 3;
+constexpr int kRtMinBlocksBF16 = 4;
 // Static shared memory of the apply kernel (it uses dynamic shared memory only).
 constexpr int kApplyStaticSmem = 0;
 
@@ -150,6 +185,8 @@ struct Plan {
   int64_t nnzb = 0;
   int bs = 3;                                     // block dimension: 3 (3x3 blocks) or 1 (scalar CSR)
   int rows_per_warp = kRowsPerWarp;               // apply rows per warp: 10 (three threads a row) or 32
+  bool row_thread = false;                        // 3x3 blocks, one thread per row (row-thread stream layout)
+  int vec_row_bytes = 24;                         // shared-memory bytes per row of the subdomain vector
   ilu0dd_geom geom{};
   ilu0dd_opts opts{};
   int32_t nsub = 0;

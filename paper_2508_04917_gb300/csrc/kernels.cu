@@ -64,29 +64,179 @@ __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 // once) while one thread keeps bulk L2 prefetches (cp.async.bulk.prefetch.L2)
 // a fixed distance ahead in the subdomain's stream. Shared memory holds the
 // subdomain vector, the block's piece descriptors and one mbarrier per piece.
-// Three threads per row (lane = 3 * (row in warp) + a, ten rows per warp);
-// rows of one piece are independent. There are no block barriers between
+// Rows of one piece are independent. There are no block barriers between
 // pieces: a piece's row groups go to warps round-robin, a warp issues the
 // loads of its row group at once and then waits (suspended, not polling)
 // only until the previous level's pieces are complete, so warps with no rows
 // in the current level run ahead to load for later ones.
+// Two thread mappings: FP64 and float-pair 3x3 factors take three threads per
+// row (lane = 3 * (row in warp) + a, ten rows per warp: apply_block), whose
+// per-thread chain of multiply-adds stays short where this GPU's FP64 pipe or
+// the double-float arithmetic is the bound; FP32 and BF16 factors one thread
+// per row computing all three components (32 rows per warp, the row-thread
+// layout: apply_block_rt), which issues a third of the instructions of the
+// three-thread mapping; scalar rows take one thread each (apply_block with
+// BS = 1). Both compute each output component with the same operations in
+// the same order, so the mappings give the same bits.
 // In the DF64 mode the vector is held as float pairs, scaled by a power of two
 // per block (exact, and the apply is linear and local to the block) so that
 // the FP32 exponent range never limits it.
 // Modes: plain z = M^-1 r; P: p <- r + beta (p - omega v), z = M^-1 p;
 // S: s <- r - alpha v, z = M^-1 s. Modes P and S skip a finished solve.
 // PART 0 runs every piece (the fused apply); 1 only the L sweep, 2 only the
-// D^-1 and U~ sweep (the two launches of the unfused apply). BS = block
-// dimension: 3 (three threads per block row, ten rows per warp) or 1 (scalar
-// CSR: one thread per row, 32 rows per warp). The ablations: SYNC 1 orders
-// rows by per-row flags (Algorithm 4) instead of the per-piece mbarriers;
-// TRAV 1 traverses a level edge-centrically (one thread per block, shared-
-// memory atomics into the rows) instead of row-wise; VGLOB 1 (FP64 only)
-// keeps the subdomain vector in global memory (in z) instead of shared
-// memory, to measure what shared memory brings.
+// D^-1 and U~ sweep (the two launches of the unfused apply). The ablations:
+// SYNC 1 orders rows by per-row flags (Algorithm 4) instead of the per-piece
+// mbarriers; TRAV 1 traverses a level edge-centrically (threads over the
+// blocks of a level, shared-memory atomics into the rows) instead of
+// row-wise; VGLOB 1 (FP64 only) keeps the subdomain vector in global memory
+// (in z) instead of shared memory, to measure what shared memory brings.
+
+// Subdomain vector -> shared memory, with the fused BiCGSTAB update of modes P
+// (p <- r + beta (p - omega v), written back to p) and S (s <- r - alpha v,
+// written back to s). Entry e of the subdomain (row e / BS, component e % BS)
+// goes to y[VS * row + component]. DF64: the block's largest magnitude sets a
+// power-of-two scale 2^-k (applied here) and the function returns 2^k, the
+// factor store_vector undoes it with; otherwise it returns 1.
+template <typename TV, int MODE, int BS, int VS>
+__device__ __forceinline__ double load_vector(const SysDesc& S, const CtaDesc& cd, const double* r, TV* y,
+                                              unsigned char* smem) {
+  const int tid = threadIdx.x;
+  const int64_t base = (int64_t)BS * cd.row0;
+  const int nv = BS * cd.nrows;
+  double alpha = 0.0, beta = 0.0, omega = 0.0;
+  if (MODE == kModeP) { beta = S.scal->beta; omega = S.scal->omega; }
+  if (MODE == kModeS) alpha = S.scal->alpha;
+  const double* vv = S.vec[kVecV];
+  double* pp = S.vec[kVecP];
+  double* ss = S.vec[kVecS];
+  constexpr bool kDF = std::is_same<TV, df64>::value;
+  static_assert(!kDF || VS == BS, "float pairs keep the unpadded vector");
+  double amax = 0.0;  // DF64: largest |value| this thread loads
+  for (int e = tid; e < nv; e += blockDim.x) {
+    double val;
+    if (MODE == kModePlain) {
+      val = r[base + e];
+    } else if (MODE == kModeP) {
+      val = fma(beta, fma(-omega, vv[base + e], pp[base + e]), r[base + e]);
+      pp[base + e] = val;
+    } else {
+      val = fma(-alpha, vv[base + e], r[base + e]);
+      ss[base + e] = val;
+    }
+    if constexpr (kDF) {
+      reinterpret_cast<double*>(y)[e] = val;  // same 8 bytes; converted below
+      amax = fmax(amax, fabs(val));
+    } else if constexpr (VS == BS) {
+      y[e] = to_compute<TV>(val);
+    } else {
+      const int row = e / BS;
+      y[VS * row + (e - BS * row)] = to_compute<TV>(val);
+    }
+  }
+  double unscale = 1.0;
+  if constexpr (kDF) {
+    // block maximum -> scale 2^-k with max |value| * 2^-k in [0.5, 1)
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    double* red = reinterpret_cast<double*>(smem + S.vec_bytes);  // descriptor area, not yet in use
+    if ((tid & 31) == 0) red[tid >> 5] = amax;
+    __syncthreads();
+    amax = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) amax = fmax(amax, red[w]);
+    int k = 0;
+    if (amax > 0.0 && isfinite(amax)) frexp(amax, &k);
+    const double scale = ldexp(1.0, -k);
+    unscale = ldexp(1.0, k);
+    for (int e = tid; e < nv; e += blockDim.x) y[e] = df_from_double(reinterpret_cast<double*>(y)[e] * scale);
+  }
+  return unscale;
+}
+
+// Shared memory -> z (the subdomain's entries), undoing the DF64 scale.
+template <typename TV, int BS, int VS>
+__device__ __forceinline__ void store_vector(const CtaDesc& cd, const TV* y, double* z, double unscale) {
+  const int64_t base = (int64_t)BS * cd.row0;
+  const int nv = BS * cd.nrows;
+  constexpr bool kDF = std::is_same<TV, df64>::value;
+  for (int e = threadIdx.x; e < nv; e += blockDim.x) {
+    const int row = VS == BS ? 0 : e / BS;
+    const TV v = VS == BS ? y[e] : y[VS * row + (e - BS * row)];
+    z[base + e] = kDF ? to_double(v) * unscale : to_double(v);
+  }
+}
+
+// Stage the descriptors of pieces [k, k + min(kDescCache, k1 - k)) in shared
+// memory and, for the mbarrier-ordered apply (SYNC 0), arm one mbarrier per
+// staged piece: every thread of the piece's row groups (RPW rows each)
+// arrives once its rows are written, 32 arrivals per group (the stuck piece
+// of the failure-path tests expects one arrival too many). Called by every
+// thread; the previous window's pieces must all be complete.
+template <int RPW, int SYNC>
+__device__ __forceinline__ void stage_window(const SysDesc& S, const CtaDesc& cd, int k, int k0, int k1,
+                                             PieceDesc* dsm, uint64_t* mbar, volatile uint32_t* abort_flag) {
+  const int tid = threadIdx.x;
+  const int cnt = min(kDescCache, k1 - k);
+  if (k > k0) {
+    __syncthreads();  // every piece of the (full) window is done
+    if constexpr (SYNC == 0)
+      for (int q = tid; q < kDescCache; q += blockDim.x) mbar_inval(mbar + q);
+  }
+  const uint4* src = reinterpret_cast<const uint4*>(S.pieces + cd.piece0 + k);
+  uint4* dst = reinterpret_cast<uint4*>(dsm);
+  for (int q = tid; q < 2 * cnt; q += blockDim.x) dst[q] = __ldg(src + q);
+  if (k == k0 && tid == 0) *abort_flag = 0;
+  __syncthreads();
+  if constexpr (SYNC == 0) {
+    for (int q = tid; q < cnt; q += blockDim.x) {
+      const uint32_t groups = ((dsm[q].meta & 0xFFFFu) + RPW - 1) / RPW;
+      mbar_init(mbar + q, 32u * groups + (cd.piece0 + k + q == S.wait_stuck ? 1u : 0u));
+    }
+    __syncthreads();
+  }
+}
+
+// Wait for the previous level's pieces of this window (earlier windows are
+// done). Bounded: after S.wait_cycles SM cycles the block gives up, flags the
+// device error word and carries on (its results are then not valid).
+__device__ __forceinline__ void wait_prev_level(const SysDesc& S, const PieceDesc& pd, int win0, uint64_t* mbar,
+                                                volatile uint32_t* abort_flag) {
+  for (int j = max((int)pd.prev_first, win0); j < (int)pd.lvl_first; ++j) {
+    uint64_t* b = mbar + (j - win0);
+    if (!mbar_try_wait(b, 0)) {
+      const long long t0 = clock64();
+      while (!mbar_try_wait(b, 0)) {
+        if (*abort_flag || clock64() - t0 > (long long)S.wait_cycles) {
+          if (atomicCAS(const_cast<uint32_t*>(abort_flag), 0u, 1u) == 0u) atomicCAS(S.err, 0, kErrApplyWait);
+          break;
+        }
+      }
+    }
+  }
+}
+
+// Algorithm 4's wait (SYNC 1): spin (bounded) until row rr's flag reaches ph
+// (1: its L result is in the vector, 2: its final value).
+__device__ __forceinline__ void wait_row_flag(const SysDesc& S, volatile uint8_t* rflag, int rr, uint8_t ph,
+                                              volatile uint32_t* abort_flag) {
+  if (rflag[rr] >= ph) return;
+  const long long t0 = clock64();
+  while (rflag[rr] < ph) {
+    if (*abort_flag || clock64() - t0 > (long long)S.wait_cycles) {
+      if (atomicCAS(const_cast<uint32_t*>(abort_flag), 0u, 1u) == 0u) atomicCAS(S.err, 0, kErrApplyWait);
+      return;
+    }
+  }
+}
+
+template <typename TF, int MODE, int PART = 0, int SYNC = 0, int TRAV = 0>
+__device__ __forceinline__ void apply_block_rt(const SysDesc& S, int sub, const double* r, double* z);
+
 template <typename TF, int MODE, int PART = 0, int BS = 3, int SYNC = 0, int TRAV = 0, int VGLOB = 0>
 __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const double* r, double* z) {
   static_assert(BS == 1 || BS == 3, "block dimension 1 or 3");
+  if constexpr (BS == 3 && (std::is_same<TF, float>::value || std::is_same<TF, bf16s>::value)) {
+    static_assert(!VGLOB, "global vector: FP64 only");
+    apply_block_rt<TF, MODE, PART, SYNC, TRAV>(S, sub, r, z);
+  } else {
   constexpr int RPW = BS == 3 ? kRowsPerWarp : 32;  // rows per warp
   using TV = typename FactorLoad<TF>::compute;
   constexpr uint32_t FE = sizeof(TF);
@@ -117,50 +267,8 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
   const bool pf_thread = tid == (int)blockDim.x - 32;
   if (pf_thread) prefetch_upto(pf_end + dist);
 
-  // subdomain vector -> shared memory (with the fused BiCGSTAB update)
-  const int64_t base = (int64_t)BS * cd.row0;
-  const int nv = BS * cd.nrows;
-  double alpha = 0.0, beta = 0.0, omega = 0.0;
-  if (MODE == kModeP) { beta = S.scal->beta; omega = S.scal->omega; }
-  if (MODE == kModeS) alpha = S.scal->alpha;
-  const double* vv = S.vec[kVecV];
-  double* pp = S.vec[kVecP];
-  double* ss = S.vec[kVecS];
   constexpr bool kDF = std::is_same<TV, df64>::value;
-  double amax = 0.0;  // DF64: largest |value| this thread loads
-  for (int e = tid; e < nv; e += blockDim.x) {
-    double val;
-    if (MODE == kModePlain) {
-      val = r[base + e];
-    } else if (MODE == kModeP) {
-      val = fma(beta, fma(-omega, vv[base + e], pp[base + e]), r[base + e]);
-      pp[base + e] = val;
-    } else {
-      val = fma(-alpha, vv[base + e], r[base + e]);
-      ss[base + e] = val;
-    }
-    if constexpr (kDF) {
-      reinterpret_cast<double*>(y)[e] = val;  // same 8 bytes; converted below
-      amax = fmax(amax, fabs(val));
-    } else {
-      y[e] = to_compute<TV>(val);
-    }
-  }
-  double unscale = 1.0;
-  if constexpr (kDF) {
-    // block maximum -> scale 2^-k with max |value| * 2^-k in [0.5, 1)
-    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    double* red = reinterpret_cast<double*>(smem + S.vec_bytes);  // descriptor area, not yet in use
-    if ((tid & 31) == 0) red[tid >> 5] = amax;
-    __syncthreads();
-    amax = red[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) amax = fmax(amax, red[w]);
-    int k = 0;
-    if (amax > 0.0 && isfinite(amax)) frexp(amax, &k);
-    const double scale = ldexp(1.0, -k);
-    unscale = ldexp(1.0, k);
-    for (int e = tid; e < nv; e += blockDim.x) y[e] = df_from_double(reinterpret_cast<double*>(y)[e] * scale);
-  }
+  const double unscale = load_vector<TV, MODE, BS, BS>(S, cd, r, y, smem);
   // SYNC 1 (Algorithm 4's synchronization): one flag per row, 1 once the
   // row's L result is in the vector (at once for rows of L level 0), 2 once
   // its final value is.
@@ -175,9 +283,6 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
   const bool lane_ok = BS == 3 ? lane < 3 * kRowsPerWarp : true;
   const int base_lane = lane - comp;
 
-  // Piece descriptors are staged in shared memory, kDescCache at a time, with
-  // one mbarrier per staged piece: every thread of the piece's row groups
-  // arrives once its rows are written (32 arrivals per group).
   PieceDesc* dsm = reinterpret_cast<PieceDesc*>(smem + S.vec_bytes);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(dsm + kDescCache);
   volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(mbar + kDescCache);
@@ -190,26 +295,8 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
     if constexpr (SYNC == 1)
       if (k == cd.npieces_l && k > k0 && (k - k0) % kDescCache != 0) __syncthreads();
     if ((k - k0) % kDescCache == 0) {
-      const int cnt = min(kDescCache, k1 - k);
-      if (k > k0) {
-        __syncthreads();  // every piece of the (full) window is done
-        if constexpr (SYNC == 0)
-          for (int q = tid; q < kDescCache; q += blockDim.x) mbar_inval(mbar + q);
-      }
-      const uint4* src = reinterpret_cast<const uint4*>(S.pieces + cd.piece0 + k);
-      uint4* dst = reinterpret_cast<uint4*>(dsm);
-      for (int q = tid; q < 2 * cnt; q += blockDim.x) dst[q] = __ldg(src + q);
-      if (k == k0 && tid == 0) *abort_flag = 0;
+      stage_window<RPW, SYNC>(S, cd, k, k0, k1, dsm, mbar, abort_flag);
       win0 = k;
-      __syncthreads();
-      if constexpr (SYNC == 0) {
-        for (int q = tid; q < cnt; q += blockDim.x) {
-          // the stuck piece (failure-path tests) expects one arrival too many
-          const uint32_t groups = ((dsm[q].meta & 0xFFFFu) + RPW - 1) / RPW;
-          mbar_init(mbar + q, 32u * groups + (cd.piece0 + k + q == S.wait_stuck ? 1u : 0u));
-        }
-        __syncthreads();
-      }
     }
     const PieceDesc pd = dsm[k - win0];
     if (pf_thread) prefetch_upto(pd.off + dist);
@@ -292,36 +379,13 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
       }
       const int row = active ? gu16(gs + (pd.off + 2u * (uint32_t)w + trow2)) : 0;
       if constexpr (SYNC == 0) {
-        // Wait for the previous level's pieces of this window (earlier
-        // windows are done). Bounded: after S.wait_cycles SM cycles the block
-        // gives up and flags the error word.
-        for (int j = max((int)pd.prev_first, win0); j < (int)pd.lvl_first; ++j) {
-          uint64_t* b = mbar + (j - win0);
-          if (!mbar_try_wait(b, 0)) {
-            const long long t0 = clock64();
-            while (!mbar_try_wait(b, 0)) {
-              if (*abort_flag || clock64() - t0 > (long long)S.wait_cycles) {
-                if (atomicCAS(const_cast<uint32_t*>(abort_flag), 0u, 1u) == 0u) atomicCAS(S.err, 0, kErrApplyWait);
-                break;
-              }
-            }
-          }
-        }
+        wait_prev_level(S, pd, win0, mbar, abort_flag);
       } else {
         // Algorithm 4: wait (spin, bounded) for exactly the rows this row
         // reads: its own L result in the U sweep, then each slot's column.
         if (active) {
           const uint8_t phase = kind ? 2 : 1;
-          auto wait_row = [&](int rr, uint8_t ph) {
-            if (rflag[rr] >= ph) return;
-            const long long t0 = clock64();
-            while (rflag[rr] < ph) {
-              if (*abort_flag || clock64() - t0 > (long long)S.wait_cycles) {
-                if (atomicCAS(const_cast<uint32_t*>(abort_flag), 0u, 1u) == 0u) atomicCAS(S.err, 0, kErrApplyWait);
-                return;
-              }
-            }
-          };
+          auto wait_row = [&](int rr, uint8_t ph) { wait_row_flag(S, rflag, rr, ph, abort_flag); };
           if (kind) wait_row(row, 1);
 #pragma unroll
           for (int sl = 0; sl < kDescSlots; ++sl)
@@ -441,15 +505,324 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
   __syncthreads();
   if constexpr (SYNC == 0)
     for (int q = tid; q < k1 - win0; q += blockDim.x) mbar_inval(mbar + q);
-  if constexpr (!VGLOB)
-    for (int e = tid; e < nv; e += blockDim.x) z[base + e] = kDF ? to_double(y[e]) * unscale : to_double(y[e]);
+  if constexpr (!VGLOB) store_vector<TV, BS, BS>(cd, y, z, unscale);
+  (void)kDF;
+  }
 }
 
-// Every apply instance is compiled for three resident blocks per SM (56
-// registers): at four (40 registers) the FP32/BF16 instances spill and run
-// slower; FP64 and DF64 spill at four either way.
+
+// ---- row-thread mapping (3x3 blocks with FP32 or BF16 factors)
+
+// One block (or D^-1) of one row in the row-thread layout, as loaded: entry
+// e = 3a + c of the value array `arr` of `count` rows, row t, read with
+// 16-byte vector loads (rt_value_offset); get(e) converts entry e to the
+// compute type.
+template <typename TF>
+struct RtBlock;
+template <>
+struct RtBlock<float> {
+  float4 q0, q1;
+  float e8;
+  __device__ __forceinline__ void load(const unsigned char* arr, uint32_t count, uint32_t t) {
+    q0 = __ldg(reinterpret_cast<const float4*>(arr + 16u * t));
+    q1 = __ldg(reinterpret_cast<const float4*>(arr + 16u * (count + t)));
+    e8 = __ldg(reinterpret_cast<const float*>(arr + 32u * count + 4u * t));
+  }
+  __device__ __forceinline__ float get(int e) const {
+    switch (e) {
+      case 0: return q0.x;
+      case 1: return q0.y;
+      case 2: return q0.z;
+      case 3: return q0.w;
+      case 4: return q1.x;
+      case 5: return q1.y;
+      case 6: return q1.z;
+      case 7: return q1.w;
+      default: return e8;
+    }
+  }
+};
+template <>
+struct RtBlock<bf16s> {
+  uint4 q;  // entries 0..7, two per word (the lower half first)
+  unsigned short e8;
+  __device__ __forceinline__ void load(const unsigned char* arr, uint32_t count, uint32_t t) {
+    q = __ldg(reinterpret_cast<const uint4*>(arr + 16u * t));
+    e8 = __ldg(reinterpret_cast<const unsigned short*>(arr + 16u * count + 2u * t));
+  }
+  __device__ __forceinline__ float get(int e) const {
+    const uint32_t wd = e < 2 ? q.x : e < 4 ? q.y : e < 6 ? q.z : q.w;
+    if (e == 8) return bf16_to_f32(e8);
+    return __uint_as_float((e & 1) ? (wd & 0xFFFF0000u) : (wd << 16));
+  }
+};
+
+// Bytes of one value array of `count` rows (padded to 16).
+template <typename TF>
+__device__ __forceinline__ uint32_t rt_bytes(uint32_t count) {
+  return (9u * (uint32_t)sizeof(TF) * count + 15u) & ~15u;
+}
+
+// Three components of one row of the shared-memory vector (VS entries per row).
+template <typename TV, int VS>
+__device__ __forceinline__ void rt_get3(const TV* y, int row, TV (&x)[3]) {
+  if constexpr (std::is_same<TV, float>::value && VS == 4) {
+    const float4 v = reinterpret_cast<const float4*>(y)[row];
+    x[0] = v.x;
+    x[1] = v.y;
+    x[2] = v.z;
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) x[c] = y[VS * row + c];
+  }
+}
+template <typename TV, int VS>
+__device__ __forceinline__ void rt_put3(TV* y, int row, const TV (&x)[3]) {
+  if constexpr (std::is_same<TV, float>::value && VS == 4) {
+    reinterpret_cast<float4*>(y)[row] = make_float4(x[0], x[1], x[2], 0.f);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[VS * row + c] = x[c];
+  }
+}
+
+// acc[a] -= B x for one 3x3 block, per component a: c = 0..2 in order, each a
+// multiply-add (the three-thread mapping's operations, one thread per row).
+template <typename TF, typename TV>
+__device__ __forceinline__ void rt_sub_block(const RtBlock<TF>& b, const TV (&x)[3], TV (&acc)[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[a] = mac(-b.get(3 * a + c), x[c], acc[a]);
+}
+
+// The fused apply with one thread per row (see the comment above apply_block):
+// each thread loads its row's D^-1 block and its blocks of the first
+// kDescSlots slots before the wait for the previous level (loading the FP32
+// slots after the wait instead cost 12 % at 160^3), then forms all three
+// components of the row.
+template <typename TF, int MODE, int PART, int SYNC, int TRAV>
+__device__ __forceinline__ void apply_block_rt(const SysDesc& S, int sub, const double* r, double* z) {
+  constexpr int RPW = 32;
+  using TV = typename FactorLoad<TF>::compute;
+  constexpr int VS = std::is_same<TV, float>::value ? 4 : 3;  // vector entries per row in shared memory
+  extern __shared__ __align__(128) unsigned char smem[];
+
+  if (MODE != kModePlain && S.scal->done) return;
+  const CtaDesc cd = S.cta[sub];
+  const int tid = threadIdx.x;
+  TV* y = reinterpret_cast<TV*>(smem);
+  const unsigned char* gs = S.stream + cd.stream_off;
+  const uint32_t len = (uint32_t)cd.stream_len;
+  const uint32_t dist = (uint32_t)S.prefetch_bytes;
+  constexpr uint32_t kPf = 16384;
+  const int k0 = PART == 2 ? cd.npieces_l : 0;
+  const int k1 = PART == 1 ? cd.npieces_l : cd.npieces;
+  uint32_t pf_end = PART == 2 && k0 < k1 ? S.pieces[cd.piece0 + k0].off : 0;
+  auto prefetch_upto = [&](uint32_t upto) {
+    upto = min(upto, len);
+    while (pf_end < upto) {
+      const uint32_t bytes = min(kPf, len - pf_end);
+      prefetch_l2(gs + pf_end, bytes);
+      pf_end += bytes;
+    }
+  };
+  const bool pf_thread = tid == (int)blockDim.x - 32;
+  if (pf_thread) prefetch_upto(pf_end + dist);
+
+  const double unscale = load_vector<TV, MODE, 3, VS>(S, cd, r, y, smem);
+  volatile uint8_t* rflag = smem + S.vec_bytes + kApplyTailSmem;
+  if constexpr (SYNC == 1)
+    for (int e = tid; e < cd.nrows; e += blockDim.x) rflag[e] = S.row_l0[cd.row0 + e];
+  __syncthreads();
+
+  const int warp = tid >> 5, lane = tid & 31;
+  const int nwarps = (int)(blockDim.x >> 5);
+  PieceDesc* dsm = reinterpret_cast<PieceDesc*>(smem + S.vec_bytes);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(dsm + kDescCache);
+  volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(mbar + kDescCache);
+  int win0 = k0;
+  int rot = 0;
+  for (int k = k0; k < k1; ++k) {
+    if constexpr (SYNC == 1)
+      if (k == cd.npieces_l && k > k0 && (k - k0) % kDescCache != 0) __syncthreads();
+    if ((k - k0) % kDescCache == 0) {
+      stage_window<RPW, SYNC>(S, cd, k, k0, k1, dsm, mbar, abort_flag);
+      win0 = k;
+    }
+    const PieceDesc pd = dsm[k - win0];
+    if (pf_thread) prefetch_upto(pd.off + dist);
+    const int n = (int)(pd.meta & 0xFFFFu);
+    const int w = (int)((pd.meta >> 16) & 0xFFu);
+    const int kind = (int)(pd.meta >> 24);
+    const int ng = (n + RPW - 1) / RPW;
+    int g = warp - rot;
+    if (g < 0) g += nwarps;
+    rot += ng;
+    if (rot >= nwarps) rot -= nwarps;
+    if (g < ng) {  // warp-uniform
+      const int trow = g * RPW + lane;
+      const bool active = trow < n;
+      const unsigned char* rec = gs + pd.off;
+      const uint32_t arr0 = pd.off + pd.voff;  // first value array (D^-1 for U pieces)
+      const uint32_t cbase = pd.off + 2u * (uint32_t)(w + n);
+      uint32_t sb = arr0 + (kind ? rt_bytes<TF>((uint32_t)n) : 0u);  // current slot's value array
+      uint32_t c0 = 0;
+      int col[kDescSlots];
+      RtBlock<TF> blk[kDescSlots];
+      int nsl = 0;
+      if constexpr (TRAV == 0) {
+#pragma unroll
+        for (int sl = 0; sl < kDescSlots; ++sl) {
+          const uint32_t cs = pd.cnt[sl];  // 0 beyond w
+          const bool has = active && sl < w && (uint32_t)trow < cs;
+          nsl += has;
+          col[sl] = has ? gu16(gs + (cbase + 2u * (c0 + (uint32_t)trow))) : 0;
+          if (has) blk[sl].load(gs + sb, cs, (uint32_t)trow);
+          sb += rt_bytes<TF>(cs);
+          c0 += cs;
+        }
+      }
+      RtBlock<TF> dblk;
+      if (kind && active) dblk.load(gs + arr0, (uint32_t)n, (uint32_t)trow);
+      const int row = active ? gu16(gs + (pd.off + 2u * (uint32_t)(w + trow))) : 0;
+      if constexpr (SYNC == 0) {
+        wait_prev_level(S, pd, win0, mbar, abort_flag);
+      } else if (active) {
+        // Algorithm 4: wait for exactly the rows this row reads
+        const uint8_t phase = kind ? 2 : 1;
+        if (kind) wait_row_flag(S, rflag, row, 1, abort_flag);
+        uint32_t cc = 0;
+        for (int sl = 0; sl < w; ++sl) {
+          const uint32_t cs = sl < kDescSlots ? (uint32_t)pd.cnt[sl] : (uint32_t)gu16(rec + 2 * sl);
+          if ((uint32_t)trow >= cs) break;
+          wait_row_flag(S, rflag, gu16(gs + (cbase + 2u * (cc + (uint32_t)trow))), phase, abort_flag);
+          cc += cs;
+        }
+        __threadfence_block();
+      }
+      __syncwarp();
+      if constexpr (TRAV == 0) {
+        if (active) {
+          TV acc[3];
+          rt_get3<TV, VS>(y, row, acc);
+          if (kind) {
+            // D^-1 (Section 4.3): w = D_i^-1 y_i
+            TV t[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              t[a] = dblk.get(3 * a) * acc[0];
+              t[a] = mac(dblk.get(3 * a + 1), acc[1], t[a]);
+              t[a] = mac(dblk.get(3 * a + 2), acc[2], t[a]);
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[a] = t[a];
+          }
+#pragma unroll
+          for (int sl = 0; sl < kDescSlots; ++sl) {
+            if (sl < nsl) {
+              TV x[3];
+              rt_get3<TV, VS>(y, col[sl], x);
+              rt_sub_block<TF, TV>(blk[sl], x, acc);
+            }
+          }
+          // rows with more than kDescSlots blocks (general patterns): the
+          // further slots one at a time, their counts from the record head
+          if (w > kDescSlots && nsl == kDescSlots) {
+            for (int sl = kDescSlots; sl < w; ++sl) {
+              const uint32_t cs = (uint32_t)gu16(rec + 2 * sl);
+              if ((uint32_t)trow >= cs) break;  // counts do not grow with the slot
+              const int cl = gu16(gs + (cbase + 2u * (c0 + (uint32_t)trow)));
+              RtBlock<TF> b;
+              b.load(gs + sb, cs, (uint32_t)trow);
+              TV x[3];
+              rt_get3<TV, VS>(y, cl, x);
+              rt_sub_block<TF, TV>(b, x, acc);
+              sb += rt_bytes<TF>(cs);
+              c0 += cs;
+            }
+          }
+          rt_put3<TV, VS>(y, row, acc);
+        }
+      } else {
+        // Edge-centric traversal (TRAV 1): the row's D^-1 step first, then
+        // the (row, slot) blocks of the group are tasks spread over the lanes
+        // (task = row-in-group * w + slot, lanes in turn), each subtracting
+        // its block's product from its row with shared-memory atomics.
+        if (kind && active) {
+          TV v[3], t[3];
+          rt_get3<TV, VS>(y, row, v);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            t[a] = dblk.get(3 * a) * v[0];
+            t[a] = mac(dblk.get(3 * a + 1), v[1], t[a]);
+            t[a] = mac(dblk.get(3 * a + 2), v[2], t[a]);
+          }
+          rt_put3<TV, VS>(y, row, t);
+        }
+        __syncwarp();
+        const int rows_g = min(RPW, n - g * RPW);
+        for (int task = lane; task < rows_g * w; task += 32) {
+          const int tg = task / w, sl = task - tg * w;  // row in group, slot
+          const uint32_t tr = (uint32_t)(g * RPW + tg);
+          uint32_t cs = 0, cc = 0, sbb = arr0 + (kind ? rt_bytes<TF>((uint32_t)n) : 0u);
+          for (int q = 0; q <= sl; ++q) {
+            cs = q < kDescSlots ? (uint32_t)pd.cnt[q] : (uint32_t)gu16(rec + 2 * q);
+            if (q < sl) {
+              cc += cs;
+              sbb += rt_bytes<TF>(cs);
+            }
+          }
+          if (tr >= cs) continue;
+          const int rrow = gu16(gs + (pd.off + 2u * ((uint32_t)w + tr)));
+          const int rcol = gu16(gs + (cbase + 2u * (cc + tr)));
+          RtBlock<TF> b;
+          b.load(gs + sbb, cs, tr);
+          TV x[3];
+          rt_get3<TV, VS>(y, rcol, x);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            TV p = b.get(3 * a) * x[0];
+            p = mac(b.get(3 * a + 1), x[1], p);
+            p = mac(b.get(3 * a + 2), x[2], p);
+            atomicAdd(&y[VS * rrow + a], -p);
+          }
+        }
+      }
+      __syncwarp();
+      if constexpr (SYNC == 0) {
+        mbar_arrive(mbar + (k - win0));
+      } else {
+        __threadfence_block();
+        __syncwarp();
+        if (active) rflag[row] = kind ? 2 : 1;
+      }
+    }
+  }
+  __syncthreads();
+  if constexpr (SYNC == 0)
+    for (int q = tid; q < k1 - win0; q += blockDim.x) mbar_inval(mbar + q);
+  store_vector<TV, 3, VS>(cd, y, z, unscale);
+}
+
+// Launch bounds of an apply instance (see kMaxRtThreads): the row-thread
+// layout (3x3 blocks with FP32 or BF16 factors) at up to 256 threads and three
+// (FP32, 80 registers) or four (BF16, 64) blocks per SM, the others at up to
+// 384 threads and three (56).
+template <typename TF, int BS>
+struct ApplyLaunch {
+  static constexpr bool rt = BS == 3 && (std::is_same<TF, float>::value || std::is_same<TF, bf16s>::value);
+  static constexpr int threads = rt ? kMaxRtThreads : kMaxApplyThreads;
+  static constexpr int min_blocks =
+      !rt ? kApplyMinBlocks : std::is_same<TF, float>::value ? kRtMinBlocksF32 : kRtMinBlocksBF16;
+};
+
+// The three-thread and scalar instances are compiled for three resident
+// blocks per SM (56 registers; at four, 40 registers, the scalar and FP64
+// instances spill and run slower); the row-thread instances as ApplyLaunch
+// says.
 template <typename TF, int MODE, int BS>
-__global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
+__global__ void __launch_bounds__(ApplyLaunch<TF, BS>::threads, ApplyLaunch<TF, BS>::min_blocks)
     ildu0_apply_kernel(SysDesc S, const double* r, double* z, int sub0) {
   apply_block<TF, MODE, 0, BS>(S, sub0 + blockIdx.x, r, z);
 }
@@ -458,18 +831,19 @@ __global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
 // spin loops) instead of the per-level mbarriers: the same arithmetic in the
 // same order, for the synchronization ablation.
 template <typename TF, int BS>
-__global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
+__global__ void __launch_bounds__(ApplyLaunch<TF, BS>::threads, ApplyLaunch<TF, BS>::min_blocks)
     ildu0_apply_rowsync_kernel(SysDesc S, const double* r, double* z) {
   apply_block<TF, kModePlain, 0, BS, 1>(S, blockIdx.x, r, z);
 }
 
-// The plain apply with the edge-centric traversal of the paper (one thread
-// per block of a level, shared-memory atomics into the rows) instead of the
-// row-wise one, for the traversal ablation (FP64, FP32 and BF16 factors).
-template <typename TF, int BS>
-__global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
-    ildu0_apply_edge_kernel(SysDesc S, const double* r, double* z) {
-  apply_block<TF, kModePlain, 0, BS, 0, 1>(S, blockIdx.x, r, z);
+// The apply with the edge-centric traversal of the paper (threads over the
+// blocks of a level, shared-memory atomics into the rows) instead of the
+// row-wise one: the traversal ablation and the solver's opts.traversal = 1
+// (FP64, FP32 and BF16 factors; every mode).
+template <typename TF, int MODE, int BS>
+__global__ void __launch_bounds__(ApplyLaunch<TF, BS>::threads, ApplyLaunch<TF, BS>::min_blocks)
+    ildu0_apply_edge_kernel(SysDesc S, const double* r, double* z, int sub0) {
+  apply_block<TF, MODE, 0, BS, 0, 1>(S, sub0 + blockIdx.x, r, z);
 }
 
 // The plain FP64 apply with the subdomain vector in global memory (z itself)
@@ -484,14 +858,14 @@ __global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
 // The unfused apply's two launches (plain mode): PART 1 = L sweep, r -> z;
 // PART 2 = D^-1 and U~ sweep, z -> z in place.
 template <typename TF, int PART, int BS>
-__global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
+__global__ void __launch_bounds__(ApplyLaunch<TF, BS>::threads, ApplyLaunch<TF, BS>::min_blocks)
     ildu0_apply_part_kernel(SysDesc S, const double* r, double* z) {
   apply_block<TF, kModePlain, PART, BS>(S, blockIdx.x, r, z);
 }
 
 // Batched apply (modes P and S): persistent blocks walk (system, subdomain) items.
 template <typename TF, int MODE, int BS>
-__global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
+__global__ void __launch_bounds__(ApplyLaunch<TF, BS>::threads, ApplyLaunch<TF, BS>::min_blocks)
     ildu0_apply_batched(const SysDesc* __restrict__ sys, const BatchItem* __restrict__ items, int64_t nitems) {
   for (int64_t i = blockIdx.x; i < nitems; i += gridDim.x) {
     const BatchItem it = items[i];
@@ -530,12 +904,12 @@ static cudaError_t configure_one(size_t smem) {
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(ildu0_apply_vglobal_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     }
-    if constexpr (!std::is_same<TF, df64s>::value) {
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ildu0_apply_edge_kernel<TF, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ildu0_apply_edge_kernel<TF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    }
+  }
+  if constexpr (!std::is_same<TF, df64s>::value) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ildu0_apply_edge_kernel<TF, MODE, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ildu0_apply_edge_kernel<TF, MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   }
   return e;
 }
@@ -570,6 +944,17 @@ template <typename TF, int BS>
 static cudaError_t launch_apply_tb(const DevCtx& d, int mode, const double* r, double* z, int sub0, int nsub,
                                    cudaStream_t s) {
   dim3 grid(nsub), block(d.threads);
+  if constexpr (!std::is_same<TF, df64s>::value) {
+    if (d.traversal == 1) {  // edge-centric (opts.traversal)
+      if (mode == kModePlain)
+        ildu0_apply_edge_kernel<TF, kModePlain, BS><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
+      else if (mode == kModeP)
+        ildu0_apply_edge_kernel<TF, kModeP, BS><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
+      else
+        ildu0_apply_edge_kernel<TF, kModeS, BS><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
+      return cudaGetLastError();
+    }
+  }
   if (mode == kModePlain)
     ildu0_apply_kernel<TF, kModePlain, BS><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
   else if (mode == kModeP)
@@ -654,9 +1039,9 @@ cudaError_t launch_apply_rowsync(const DevCtx& d, const double* r, double* z, cu
 template <typename TF>
 static cudaError_t launch_edge_t(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
   if (d.bs == 1)
-    ildu0_apply_edge_kernel<TF, 1><<<d.sd.nsub, d.threads, d.smem_bytes, s>>>(d.sd, r, z);
+    ildu0_apply_edge_kernel<TF, kModePlain, 1><<<d.sd.nsub, d.threads, d.smem_bytes, s>>>(d.sd, r, z, 0);
   else
-    ildu0_apply_edge_kernel<TF, 3><<<d.sd.nsub, d.threads, d.smem_bytes, s>>>(d.sd, r, z);
+    ildu0_apply_edge_kernel<TF, kModePlain, 3><<<d.sd.nsub, d.threads, d.smem_bytes, s>>>(d.sd, r, z, 0);
   return cudaGetLastError();
 }
 

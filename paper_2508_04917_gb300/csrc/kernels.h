@@ -47,6 +47,7 @@ struct DevCtx {
   size_t smem_bytes;
   size_t smem_rowsync;  // shared memory of the row-flag apply (0: does not fit)
   int bs = 3;  // block dimension: 3 or 1 (scalar CSR)
+  int traversal = 0;  // apply traversal: 0 vertex-centric, 1 edge-centric (ilu0dd_opts.traversal)
 };
 
 // Work item of a batched launch: system index and block index inside it.

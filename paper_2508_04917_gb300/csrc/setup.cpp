@@ -42,12 +42,20 @@ void parallel_for(int64_t n, F&& f) {
   for (auto& x : th) x.join();
 }
 
-// Bytes of one piece record (see internal.h).
-int64_t record_bytes(int n, int w, int64_t nb, int kind, int felem, int bs, int64_t* voff) {
+// Bytes of one piece record (see internal.h). cnt[s] (s < w) = rows with more
+// than s blocks. In the row-thread layout every value array (D^-1, then each
+// slot) starts on a 16-byte boundary.
+int64_t record_bytes(int n, int w, int64_t nb, const int32_t* cnt, int kind, int felem, int bs, bool row_thread,
+                     int64_t* voff) {
   int64_t head = 2 * (int64_t)w + 2 * (int64_t)n + 2 * nb;
   int64_t v = align_up(head, 16);
   if (voff) *voff = v;
   const int64_t bb = (int64_t)bs * bs;
+  if (row_thread) {
+    int64_t at = v + (kind ? rt_slot_bytes(n, felem) : 0);
+    for (int s = 0; s < w; ++s) at += rt_slot_bytes(cnt[s], felem);
+    return align_up(at, 16);
+  }
   int64_t vals = (kind ? bb * n : 0) + bb * nb;
   return align_up(v + vals * felem, 16);
 }
@@ -192,7 +200,11 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   Plan& p = *P;
   p = Plan();
   p.bs = bs;
-  p.rows_per_warp = bs == 3 ? kRowsPerWarp : 32;
+  // 3x3 blocks: FP64 and float-pair factors take three threads per row (ten
+  // rows per warp), FP32 and BF16 factors one thread per row (the row-thread
+  // layout); scalar rows one
+  p.row_thread = bs == 3 && (o->factor_prec == ILU0DD_F32 || o->factor_prec == ILU0DD_BF16);
+  p.rows_per_warp = bs == 3 && !p.row_thread ? kRowsPerWarp : 32;
   // per-phase wall times (opts.trace)
   double tprev = wall_seconds();
   std::string tlog;
@@ -359,8 +371,19 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
     return ILU0DD_ERR_INVALID;
   }
   p.factor_prec = fp;
+  if (o->traversal != 0 && o->traversal != 1) {
+    *why = "traversal must be 0 (vertex-centric) or 1 (edge-centric)";
+    return ILU0DD_ERR_INVALID;
+  }
+  if (o->traversal == 1 && fp == ILU0DD_DF64) {
+    *why = "the edge-centric traversal has no float-pair form (no atomic add on pairs)";
+    return ILU0DD_ERR_INVALID;
+  }
   p.factor_elem = (fp == ILU0DD_F64 || fp == ILU0DD_DF64) ? 8 : fp == ILU0DD_F32 ? 4 : 2;
   p.vec_elem = (fp == ILU0DD_F64 || fp == ILU0DD_DF64) ? 8 : 4;
+  // shared-memory bytes per row of the subdomain vector: FP32 arithmetic in the
+  // row-thread layout pads the three entries to 16 bytes (one vector access)
+  p.vec_row_bytes = p.row_thread && p.vec_elem == 4 ? 16 : bs * p.vec_elem;
   for (int s = 0; s < p.nsub; ++s) p.rmax = std::max(p.rmax, p.part_ptr[s + 1] - p.part_ptr[s]);
   if (p.rmax > 65535) {
     *why = "a subdomain has more than 65535 rows";
@@ -389,10 +412,14 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   // 0.064 -> 0.062 ms); FP32/BF16 groups and small boxes run faster without.
   const int groups = (int)ceil_div(widest, p.rows_per_warp);
   const bool fp64_arith = o->factor_prec == ILU0DD_F64 || o->factor_prec == ILU0DD_DF64;
-  const int warps = fp64_arith && groups >= 4 ? groups + (groups + 1) / 2 : groups;
-  p.threads = o->threads_per_cta > 0 ? o->threads_per_cta : std::min(kMaxApplyThreads, 32 * warps);
-  if (p.threads % 32 || p.threads > kMaxApplyThreads || p.threads < 32) {
-    *why = "threads_per_cta must be a multiple of 32 in [32, 384]";
+  // the row-thread layout (32 rows per warp): three warps per row group of the
+  // widest level, so that two thirds of the warps load ahead for later levels
+  const int warps = p.row_thread ? std::max(1, (3 * groups + 1) / 2) : fp64_arith && groups >= 4 ? groups + (groups + 1) / 2 : groups;
+  const int max_threads = p.row_thread ? kMaxRtThreads : kMaxApplyThreads;
+  p.threads = o->threads_per_cta > 0 ? o->threads_per_cta : std::min(max_threads, 32 * warps);
+  if (p.threads % 32 || p.threads > max_threads || p.threads < 32) {
+    *why = "threads_per_cta must be a multiple of 32 in [32, " + std::to_string(max_threads) +
+           "] (384 with FP64 or scalar factors, 256 with 3x3 FP32, BF16 or DF64 factors)";
     return ILU0DD_ERR_INVALID;
   }
   p.prefetch_bytes = o->prefetch_bytes > 0 ? o->prefetch_bytes : 32768;
@@ -453,20 +480,26 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
         }
         std::sort(key.begin(), key.end());
         size_t a = 0;
+        std::vector<int32_t> scnt;
         while (a < key.size()) {
-          // grow the piece while it fits the block
+          // grow the piece while it fits the block (the size bound adds the
+          // row-thread layout's padding of at most 16 bytes per value array)
           size_t b = a;
           int64_t nb = 0;
           while (b < key.size() && (int)(b - a) < rows_cap) {
             int w = -key[a].first;
-            int64_t bytes = record_bytes((int)(b - a + 1), w, nb - key[b].first, kind, p.factor_elem, bs, nullptr);
+            int64_t bytes = record_bytes((int)(b - a + 1), w, nb - key[b].first, nullptr, kind, p.factor_elem, bs,
+                                         false, nullptr) + 16 * (int64_t)(w + 1);
             if (bytes > cap && b > a) break;
             nb += -key[b].first;
             ++b;
           }
           int n = (int)(b - a), w = -key[a].first;
+          scnt.assign((size_t)w, 0);
+          for (size_t t = a; t < b; ++t)
+            for (int sl = 0; sl < -key[t].first; ++sl) scnt[sl] += 1;
           int64_t voff;
-          int64_t bytes = record_bytes(n, w, nb, kind, p.factor_elem, bs, &voff);
+          int64_t bytes = record_bytes(n, w, nb, scnt.data(), kind, p.factor_elem, bs, p.row_thread, &voff);
           if (bytes > cap || w > 255) sub_fail[s] = 1;
           for (size_t t = a; t < b; ++t) out.push_back(key[t].second - r0);
           PieceDesc d{};
@@ -476,11 +509,7 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
           d.voff = (uint32_t)voff;
           d.lvl_first = first;
           d.prev_first = prev;
-          for (int sl = 0; sl < std::min(w, kDescSlots); ++sl) {
-            int c = 0;
-            for (size_t t = a; t < b; ++t) c += -key[t].first > sl;
-            d.cnt[sl] = (uint16_t)c;
-          }
+          for (int sl = 0; sl < std::min(w, kDescSlots); ++sl) d.cnt[sl] = (uint16_t)scnt[sl];
           sub_desc[s].push_back(d);
           sub_len[s] += bytes;
           off += (uint32_t)bytes;
@@ -533,9 +562,9 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   });
   p.stream_bytes = soff;
   p.n_pieces = (int64_t)p.pieces.size();
-  p.smem_bytes = (size_t)align_up((int64_t)bs * p.rmax * p.vec_elem, 128) + kApplyTailSmem;
+  p.smem_bytes = (size_t)align_up((int64_t)p.rmax * p.vec_row_bytes, 128) + kApplyTailSmem;
   if ((int64_t)p.smem_bytes > (int64_t)max_smem - kApplyStaticSmem) {
-    *why = "subdomain vector (" + std::to_string((int64_t)bs * p.rmax * p.vec_elem) + " B) exceeds the " +
+    *why = "subdomain vector (" + std::to_string((int64_t)p.rmax * p.vec_row_bytes) + " B) exceeds the " +
            std::to_string(max_smem) +
            " B of shared memory per block";
     return ILU0DD_ERR_SMEM;
@@ -822,6 +851,22 @@ void pack_stream(const Plan& p, const std::vector<double>& F, const std::vector<
       for (int slot = 0; slot < w; ++slot)
         for (int t = 0; t < cnt[slot]; ++t) h[cpos++] = (uint16_t)(p.dd_col[blk[t][slot]] - c.row0);
       uint8_t* v = rec + d.voff;
+      if (p.row_thread) {
+        // row-thread layout: entry e = 3a + c of row t in 16-byte planes
+        if (kind) {
+          for (int t = 0; t < n; ++t)
+            for (int e = 0; e < 9; ++e)
+              put_factor(v + rt_value_offset(e, t, n, fe), fp, invD[9 * (size_t)(c.row0 + rows[t]) + e]);
+          v += rt_slot_bytes(n, fe);
+        }
+        for (int slot = 0; slot < w; ++slot) {
+          const int cs = cnt[slot];
+          for (int t = 0; t < cs; ++t)
+            for (int e = 0; e < 9; ++e) put_factor(v + rt_value_offset(e, t, cs, fe), fp, F[9 * (size_t)blk[t][slot] + e]);
+          v += rt_slot_bytes(cs, fe);
+        }
+        continue;
+      }
       // entry [a][c] of row t's block at (c * count + t) * bs + a
       if (kind) {
         for (int cc = 0; cc < bs; ++cc)

@@ -205,14 +205,15 @@ __device__ __forceinline__ void dev_put(unsigned char* dst, int prec, double v, 
 }
 
 // One thread block per piece, its threads over the piece's rows: the record
-// head (slot counts, local rows, local columns slot-major) and the values
-// interleaved by component, entry [a][c] of row t's block at
-// (c * count + t) * bs + a.
+// head (slot counts, local rows, local columns slot-major) and the values,
+// interleaved by component (entry [a][c] of row t's block at
+// (c * count + t) * bs + a) or, in the row-thread layout (row_thread = 1),
+// in 16-byte planes per value array (rt_value_offset).
 __global__ void pack_stream_kernel(const CtaDesc* __restrict__ cta, const PieceDesc* __restrict__ pieces,
                                    const int32_t* __restrict__ piece_sub, const int32_t* __restrict__ prow_off,
                                    const int32_t* __restrict__ prows, const int32_t* __restrict__ dd_rp,
                                    const int32_t* __restrict__ dd_col, const double* __restrict__ W,
-                                   const double* __restrict__ invD, int fe, int prec, int bs,
+                                   const double* __restrict__ invD, int fe, int prec, int bs, int row_thread,
                                    unsigned char* stream, int32_t* range_bad) {
   const int bb = bs * bs;
   __shared__ int32_t cnt[256];
@@ -254,12 +255,18 @@ __global__ void pack_stream_kernel(const CtaDesc* __restrict__ cta, const PieceD
     unsigned char* v = rec + pd.voff;
     if (kind) {
       const double* di = &invD[bb * (int64_t)i];
-      for (int cc = 0; cc < bs; ++cc)
-        for (int a = 0; a < bs; ++a)
-          dev_put(v + (((int64_t)cc * n + t) * bs + a) * fe, prec, di[bs * a + cc], range_bad);
-      v += (int64_t)bb * n * fe;
+      if (row_thread) {
+        for (int e = 0; e < 9; ++e) dev_put(v + rt_value_offset(e, t, n, fe), prec, di[e], range_bad);
+        v += rt_slot_bytes(n, fe);
+      } else {
+        for (int cc = 0; cc < bs; ++cc)
+          for (int a = 0; a < bs; ++a)
+            dev_put(v + (((int64_t)cc * n + t) * bs + a) * fe, prec, di[bs * a + cc], range_bad);
+        v += (int64_t)bb * n * fe;
+      }
     }
     int64_t c0 = 0;
+    unsigned char* vs = v;  // this slot's value array
     for (int sl = 0; sl < nblk; ++sl) {
       const int32_t q = qa + sl;
       const int cs = cnt[sl];
@@ -270,10 +277,15 @@ __global__ void pack_stream_kernel(const CtaDesc* __restrict__ cta, const PieceD
       } else {
         for (int e = 0; e < bb; ++e) F[e] = W[bb * (int64_t)q + e];
       }
-      unsigned char* vs = v + bb * c0 * fe;
-      for (int cc = 0; cc < bs; ++cc)
-        for (int a = 0; a < bs; ++a)
-          dev_put(vs + (((int64_t)cc * cs + t) * bs + a) * fe, prec, F[bs * a + cc], range_bad);
+      if (row_thread) {
+        for (int e = 0; e < 9; ++e) dev_put(vs + rt_value_offset(e, t, cs, fe), prec, F[e], range_bad);
+        vs += rt_slot_bytes(cs, fe);
+      } else {
+        vs = v + bb * c0 * fe;
+        for (int cc = 0; cc < bs; ++cc)
+          for (int a = 0; a < bs; ++a)
+            dev_put(vs + (((int64_t)cc * cs + t) * bs + a) * fe, prec, F[bs * a + cc], range_bad);
+      }
       c0 += cs;
     }
   }
@@ -367,7 +379,7 @@ size_t device_setup_scratch_bytes(const Plan& p) {
   return scratch_layout(p, total_levels_of(p), total_prows_of(p)).total;
 }
 
-int setup_on_device(const Plan& p, const double* aval_host, unsigned char* scratch, size_t scratch_bytes,
+int setup_on_device(const Plan& p, const double* aval_in, unsigned char* scratch, size_t scratch_bytes,
                     unsigned char* ws, cudaStream_t s, DeviceSetupResult* res) {
   res->bad_row = -1;
   res->range_bad = false;
@@ -414,7 +426,9 @@ int setup_on_device(const Plan& p, const double* aval_host, unsigned char* scrat
     if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(scratch + off, src, bytes, cudaMemcpyHostToDevice, s);
   };
   const int bs = p.bs, bb = bs * bs;
-  up(L.aval, aval_host, sizeof(double) * bb * (size_t)p.nnzb);
+  // the caller's values: host memory, or device memory (a device-to-device copy)
+  if (e == cudaSuccess && p.nnzb)
+    e = cudaMemcpyAsync(scratch + L.aval, aval_in, sizeof(double) * bb * (size_t)p.nnzb, cudaMemcpyDefault, s);
   up(L.dd_src, dd_src.data(), sizeof(int64_t) * dd_src.size());
   up(L.dd_rp, p.dd_rp.data(), sizeof(int32_t) * p.dd_rp.size());
   up(L.dd_col, p.dd_col.data(), sizeof(int32_t) * p.dd_col.size());
@@ -481,7 +495,7 @@ int setup_on_device(const Plan& p, const double* aval_host, unsigned char* scrat
     pack_stream_kernel<<<(unsigned)p.n_pieces, 128, 0, s>>>(
         reinterpret_cast<const CtaDesc*>(ws + p.lay.cta), reinterpret_cast<const PieceDesc*>(ws + p.lay.pieces),
         I32(L.piece_sub), I32(L.prow_off), I32(L.prows), I32(L.dd_rp), I32(L.dd_col), W, invD, p.factor_elem,
-        p.factor_prec, bs, ws + p.lay.stream, flags + 1);
+        p.factor_prec, bs, p.row_thread ? 1 : 0, ws + p.lay.stream, flags + 1);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(hflags, flags, sizeof hflags, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -21,13 +21,14 @@ size_t device_setup_scratch_bytes(const Plan& p);
 
 // Fill the workspace's factor stream, SpMV matrix, CtaDesc and PieceDesc
 // arrays and slice offsets from the caller's natural-order values
-// `aval_host` (HOST pointer, 9 * nnzb doubles). `scratch` is device memory of
+// `aval_in` (bs * bs * nnzb doubles in host memory or in device memory of the
+// current device). `scratch` is device memory of
 // at least device_setup_scratch_bytes(p) bytes, 256-byte aligned; it may be
 // released after the call (res->w and res->invd point into it). Synchronises
 // `s`. Returns ILU0DD_OK, ILU0DD_ERR_ZERO_PIVOT, ILU0DD_ERR_INVALID (DF64
 // range), ILU0DD_ERR_WORKSPACE (scratch too small or misaligned) or
 // ILU0DD_ERR_CUDA.
-int setup_on_device(const Plan& p, const double* aval_host, unsigned char* scratch, size_t scratch_bytes,
+int setup_on_device(const Plan& p, const double* aval_in, unsigned char* scratch, size_t scratch_bytes,
                     unsigned char* ws, cudaStream_t s, DeviceSetupResult* res);
 
 // Level sets of the lower (upper = 0) or upper (upper = 1) triangle of a

@@ -8,9 +8,11 @@ reduction scratch in a static device array that ships with the library instead
 of in a caller-allocated workspace.
 
 The result must equal the context-based dot product bit for bit (both follow
-the same fixed summation order), on two calls in a row: the second call is
-smaller than the first, so it also checks that leftovers in the shared array
-from the first call do not leak into the second.
+the same fixed summation order), on calls in a row of shrinking size: the
+second call's 300 tile partials are padded with zeros to 512, inside the range
+the first call (1,104 tiles) left its partials in, so it checks that the zero
+padding is written and leftovers in the shared array do not leak into a later
+call; a one-tile call follows.
 """
 import ctypes
 
@@ -33,8 +35,9 @@ def _noalloc(lib, x, y, out):
 
 def test_noalloc_dot_matches_context_dot_on_two_calls():
     lib = g.load()
-    # larger system first (1,131 tiles), then a smaller one (1 tile)
-    cases = [((64, 64, 69), (16, 16, 8)), ((17, 16, 1), (17, 16, 1))]
+    # 1,104 tiles, then 300 tiles (padded to 512: within the first call's
+    # leftovers), then 1 tile
+    cases = [((64, 64, 69), (16, 16, 8)), ((80, 60, 16), (16, 16, 8)), ((16, 16, 1), (16, 16, 1))]
     for i, (grid, sub) in enumerate(cases):
         s = synth.system(*grid, 3)
         ctx = g.Ilu0DD(s.row_ptr, s.col, s.val, grid, sub)
@@ -42,6 +45,7 @@ def test_noalloc_dot_matches_context_dot_on_two_calls():
         x = torch.from_numpy(rng.normal(size=3 * s.n)).cuda()
         y = torch.from_numpy(rng.normal(size=3 * s.n) * 1e2).cuda()
         ref = ctx.dot(x, y)
+        assert (s.n + 255) // 256 == [1104, 300, 1][i]
         out = torch.empty(1, dtype=torch.float64, device="cuda")
         assert _noalloc(lib, x, y, out) == 0
         torch.cuda.synchronize()
