@@ -97,6 +97,78 @@ __device__ __forceinline__ df64 df_from_double(double v) {
 }
 __device__ __forceinline__ double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
 
+// The same two conversions by integer and FP32 operations, from the bit
+// layouts of IEEE 754 binary64 and binary32, for the apply's load and store of
+// its subdomain vector: on this GPU every FP64 operation, conversions
+// included, takes the FP64 pipe, which the DF64 apply otherwise leaves idle
+// (measured: the load and store phases cost 13 % of the DF64 apply at 160^3).
+// They give the FP64 operations' bits exactly where every intermediate is a
+// normal number and return false elsewhere (zero, subnormal, infinite or NaN
+// values, exponents at the ends of the ranges), where the caller uses the FP64
+// operations.
+
+// A float from its integer bits' sum x < 2^23 (exact: 2^23 + x - 2^23).
+__device__ __forceinline__ float small_uint_to_float(uint32_t x) {
+  return __fsub_rn(__uint_as_float(0x4B000000u | x), 8388608.0f);
+}
+
+// df_from_double(v * 2^-k): hi = v * 2^-k rounded to nearest float (ties to
+// even), lo = (v * 2^-k - hi) rounded to nearest float.
+__device__ __forceinline__ bool df_from_double_scaled_bits(double v, int k, df64* out) {
+  const uint64_t u = (uint64_t)__double_as_longlong(v);
+  const uint32_t h32 = (uint32_t)(u >> 32), l32 = (uint32_t)u;
+  const int eb = (int)((h32 >> 20) & 0x7FFu);  // biased binary64 exponent of v
+  const int e = eb - k;                         // ... of v * 2^-k (exact while it stays normal)
+  const int E = e - 896;                        // binary32 biased exponent (bias 127 = 1023 - 896)
+  if (eb == 0 || eb == 0x7FF || E < 1 || E > 253) return false;
+  const uint32_t sign = h32 & 0x80000000u;
+  const uint32_t m23 = ((h32 & 0xFFFFFu) << 3) | (l32 >> 29);  // the 23 stored bits binary32 keeps
+  const uint32_t rest = l32 & 0x1FFFFFFFu;                      // the 29 bits it drops
+  const bool up = rest > 0x10000000u || (rest == 0x10000000u && (m23 & 1u));
+  // rounding up carries into the exponent field when m23 is all ones
+  out->hi = __uint_as_float(sign | ((((uint32_t)E << 23) | m23) + (up ? 1u : 0u)));
+  // v * 2^-k - hi = +-R units of 2^(e - 1075): the dropped bits, or their
+  // complement to 2^29 when hi was rounded up (R <= 2^28 either way)
+  const uint32_t R = up ? 0x20000000u - rest : rest;
+  if (R == 0) {
+    out->lo = 0.0f;
+    return true;
+  }
+  const int se = e - 1075;
+  if (se < -126) return false;  // lo would not be a normal float
+  // RNE(R) as a float: R = a 2^16 + b, a and b exact, one rounding in the fma
+  const float r = __fmaf_rn(small_uint_to_float(R >> 16), 65536.0f, small_uint_to_float(R & 0xFFFFu));
+  const float mag = __fmul_rn(r, __uint_as_float((uint32_t)(se + 127) << 23));  // exact: normal result
+  out->lo = __uint_as_float(__float_as_uint(mag) ^ (up ? sign ^ 0x80000000u : sign));
+  return true;
+}
+
+// The binary64 value of a normal binary32 f times 2^k, by its bits (exact),
+// when its biased binary64 exponent lies in [min_e, 2046].
+__device__ __forceinline__ bool double_from_float_scaled_bits(float f, int k, int min_e, double* out) {
+  const uint32_t b = __float_as_uint(f);
+  const int E = (int)((b >> 23) & 0xFFu);
+  const int e = E + 896 + k;
+  if (E == 0 || E == 0xFF || e < min_e || e > 2046) return false;
+  const uint64_t bits = ((uint64_t)(b & 0x80000000u) << 32) | ((uint64_t)e << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29);
+  *out = __longlong_as_double((long long)bits);
+  return true;
+}
+
+// df_to_double(a) * 2^k with one FP64 operation (the add) where both floats
+// and their scaled values are normal numbers: rounding hi 2^k + lo 2^k once
+// gives the bits of rounding hi + lo and scaling by 2^k, since nothing
+// leaves the normal range (hi's scaled exponent is kept 64 above the bottom,
+// so even a cancelling lo cannot take the sum out of it).
+__device__ __forceinline__ double df_to_double_scaled(df64 a, int k) {
+  double h, l;
+  if (double_from_float_scaled_bits(a.hi, k, 64, &h)) {
+    if (a.lo == 0.0f) return h;  // hi + (+-0) = hi for a normal hi
+    if (double_from_float_scaled_bits(a.lo, k, 1, &l)) return h + l;
+  }
+  return df_to_double(a) * ldexp(1.0, k);
+}
+
 __device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
 
 // a * b (the lo * lo term, below 2^-48 relative, is dropped)

@@ -95,11 +95,13 @@ __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 // (p <- r + beta (p - omega v), written back to p) and S (s <- r - alpha v,
 // written back to s). Entry e of the subdomain (row e / BS, component e % BS)
 // goes to y[VS * row + component]. DF64: the block's largest magnitude sets a
-// power-of-two scale 2^-k (applied here) and the function returns 2^k, the
-// factor store_vector undoes it with; otherwise it returns 1.
+// power-of-two scale 2^-k (applied here) and the function returns k, which
+// store_vector undoes; otherwise it returns 0. The DF64 maximum and split run
+// on integer and FP32 operations (df_from_double_scaled_bits), with the FP64
+// operations only where that path declines.
 template <typename TV, int MODE, int BS, int VS>
-__device__ __forceinline__ double load_vector(const SysDesc& S, const CtaDesc& cd, const double* r, TV* y,
-                                              unsigned char* smem) {
+__device__ __forceinline__ int load_vector(const SysDesc& S, const CtaDesc& cd, const double* r, TV* y,
+                                           unsigned char* smem) {
   const int tid = threadIdx.x;
   const int64_t base = (int64_t)BS * cd.row0;
   const int nv = BS * cd.nrows;
@@ -111,7 +113,9 @@ __device__ __forceinline__ double load_vector(const SysDesc& S, const CtaDesc& c
   double* ss = S.vec[kVecS];
   constexpr bool kDF = std::is_same<TV, df64>::value;
   static_assert(!kDF || VS == BS, "float pairs keep the unpadded vector");
-  double amax = 0.0;  // DF64: largest |value| this thread loads
+  // DF64: bits of the largest |value| this thread loads (for non-NaN values
+  // the magnitude bits order like the magnitudes; NaNs are skipped, as fmax does)
+  unsigned long long amax_bits = 0ull;
   for (int e = tid; e < nv; e += blockDim.x) {
     double val;
     if (MODE == kModePlain) {
@@ -125,7 +129,8 @@ __device__ __forceinline__ double load_vector(const SysDesc& S, const CtaDesc& c
     }
     if constexpr (kDF) {
       reinterpret_cast<double*>(y)[e] = val;  // same 8 bytes; converted below
-      amax = fmax(amax, fabs(val));
+      const unsigned long long mag = (unsigned long long)__double_as_longlong(val) & 0x7FFFFFFFFFFFFFFFull;
+      if (mag <= 0x7FF0000000000000ull && mag > amax_bits) amax_bits = mag;
     } else if constexpr (VS == BS) {
       y[e] = to_compute<TV>(val);
     } else {
@@ -133,35 +138,46 @@ __device__ __forceinline__ double load_vector(const SysDesc& S, const CtaDesc& c
       y[VS * row + (e - BS * row)] = to_compute<TV>(val);
     }
   }
-  double unscale = 1.0;
+  int k = 0;
   if constexpr (kDF) {
     // block maximum -> scale 2^-k with max |value| * 2^-k in [0.5, 1)
-    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    double* red = reinterpret_cast<double*>(smem + S.vec_bytes);  // descriptor area, not yet in use
-    if ((tid & 31) == 0) red[tid >> 5] = amax;
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long other = __shfl_xor_sync(0xffffffffu, amax_bits, o);
+      if (other > amax_bits) amax_bits = other;
+    }
+    unsigned long long* red = reinterpret_cast<unsigned long long*>(smem + S.vec_bytes);  // descriptor area, not yet in use
+    if ((tid & 31) == 0) red[tid >> 5] = amax_bits;
     __syncthreads();
-    amax = red[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) amax = fmax(amax, red[w]);
-    int k = 0;
+    amax_bits = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (red[w] > amax_bits) amax_bits = red[w];
+    const double amax = __longlong_as_double((long long)amax_bits);
     if (amax > 0.0 && isfinite(amax)) frexp(amax, &k);
     const double scale = ldexp(1.0, -k);
-    unscale = ldexp(1.0, k);
-    for (int e = tid; e < nv; e += blockDim.x) y[e] = df_from_double(reinterpret_cast<double*>(y)[e] * scale);
+    for (int e = tid; e < nv; e += blockDim.x) {
+      const double v = reinterpret_cast<double*>(y)[e];
+      df64 pair;
+      if (!df_from_double_scaled_bits(v, k, &pair)) pair = df_from_double(v * scale);
+      y[e] = pair;
+    }
   }
-  return unscale;
+  return k;
 }
 
-// Shared memory -> z (the subdomain's entries), undoing the DF64 scale.
+// Shared memory -> z (the subdomain's entries), undoing the DF64 scale 2^-k.
 template <typename TV, int BS, int VS>
-__device__ __forceinline__ void store_vector(const CtaDesc& cd, const TV* y, double* z, double unscale) {
+__device__ __forceinline__ void store_vector(const CtaDesc& cd, const TV* y, double* z, int k) {
   const int64_t base = (int64_t)BS * cd.row0;
   const int nv = BS * cd.nrows;
-  constexpr bool kDF = std::is_same<TV, df64>::value;
   for (int e = threadIdx.x; e < nv; e += blockDim.x) {
     const int row = VS == BS ? 0 : e / BS;
     const TV v = VS == BS ? y[e] : y[VS * row + (e - BS * row)];
-    z[base + e] = kDF ? to_double(v) * unscale : to_double(v);
+    if constexpr (std::is_same<TV, df64>::value)
+      z[base + e] = df_to_double_scaled(v, k);
+    else
+      z[base + e] = to_double(v);
   }
+  (void)k;
 }
 
 // Stage the descriptors of pieces [k, k + min(kDescCache, k1 - k)) in shared
@@ -268,7 +284,7 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
   if (pf_thread) prefetch_upto(pf_end + dist);
 
   constexpr bool kDF = std::is_same<TV, df64>::value;
-  const double unscale = load_vector<TV, MODE, BS, BS>(S, cd, r, y, smem);
+  const int kscale = load_vector<TV, MODE, BS, BS>(S, cd, r, y, smem);
   // SYNC 1 (Algorithm 4's synchronization): one flag per row, 1 once the
   // row's L result is in the vector (at once for rows of L level 0), 2 once
   // its final value is.
@@ -505,7 +521,7 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
   __syncthreads();
   if constexpr (SYNC == 0)
     for (int q = tid; q < k1 - win0; q += blockDim.x) mbar_inval(mbar + q);
-  if constexpr (!VGLOB) store_vector<TV, BS, BS>(cd, y, z, unscale);
+  if constexpr (!VGLOB) store_vector<TV, BS, BS>(cd, y, z, kscale);
   (void)kDF;
   }
 }
@@ -630,7 +646,7 @@ __device__ __forceinline__ void apply_block_rt(const SysDesc& S, int sub, const 
   const bool pf_thread = tid == (int)blockDim.x - 32;
   if (pf_thread) prefetch_upto(pf_end + dist);
 
-  const double unscale = load_vector<TV, MODE, 3, VS>(S, cd, r, y, smem);
+  const int kscale = load_vector<TV, MODE, 3, VS>(S, cd, r, y, smem);
   volatile uint8_t* rflag = smem + S.vec_bytes + kApplyTailSmem;
   if constexpr (SYNC == 1)
     for (int e = tid; e < cd.nrows; e += blockDim.x) rflag[e] = S.row_l0[cd.row0 + e];
@@ -802,7 +818,7 @@ __device__ __forceinline__ void apply_block_rt(const SysDesc& S, int sub, const 
   __syncthreads();
   if constexpr (SYNC == 0)
     for (int q = tid; q < k1 - win0; q += blockDim.x) mbar_inval(mbar + q);
-  store_vector<TV, 3, VS>(cd, y, z, unscale);
+  store_vector<TV, 3, VS>(cd, y, z, kscale);
 }
 
 // Launch bounds of an apply instance (see kMaxRtThreads): the row-thread
