@@ -80,6 +80,28 @@ def test_df64_apply_is_scale_free(factor):
     assert nrel(z, oracle.apply(d.LU, r)) <= FP64_TOL
 
 
+@pytest.mark.parametrize("kind", ["wide", "tiny_and_zero", "pow2"])
+def test_df64_apply_wide_dynamic_range(kind):
+    """Entries spread over many binades inside each subdomain: the float-pair
+    split and its inverse (done by integer operations where every step stays
+    normal, by FP64 operations elsewhere: zeros, values too small for a
+    normal float after the block's scaling) give the oracle's result."""
+    grid, sub, model = GEOMS[2]
+    s, d, ctx = case(grid, sub, model)
+    rng = np.random.default_rng(11)
+    n3 = 3 * s.n
+    if kind == "wide":
+        r = rng.uniform(-1, 1, n3) * np.exp2(rng.uniform(-90, 10, n3))
+    elif kind == "tiny_and_zero":
+        r = np.where(rng.uniform(0, 1, n3) < 0.3, 0.0,
+                     rng.uniform(-1, 1, n3) * np.exp2(rng.integers(-140, 5, n3).astype(float)))
+    else:
+        r = np.exp2(rng.integers(-40, 40, n3).astype(float)) * rng.choice([-1.0, 1.0], n3)
+    z = ctx.apply(cu(r)).cpu().numpy()
+    assert np.all(np.isfinite(z))
+    assert nrel(z, oracle.apply(d.LU, r)) <= FP64_TOL
+
+
 def test_df64_apply_of_zero_and_mixed_blocks():
     """An all-zero subdomain next to ordinary ones: zeros stay exact zeros."""
     grid, sub, model = GEOMS[3]
