@@ -398,6 +398,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_apply_baseline(odec, grid, apply_b, budget_s=args.cpu_seconds)
+        cpu["single_thread_small_configs"] = oracle_small_configs()
 
     if rank != 0:
         return
@@ -880,6 +881,33 @@ def oracle_apply_baseline(d, grid, apply_bytes, budget_s=15.0):
                       f"median {t * 1e3:.1f} ms",
             "single_thread": {"value": round(apply_bytes / min(t1) / 1e9, 4), "unit": "GB/s", "cores": 1,
                               "sample": f"2 applies, best {min(t1) * 1e3:.1f} ms"}}
+
+
+def oracle_small_configs(budget_s=2.0):
+    """The oracle's apply on one thread for the 16^3 correctness system and the
+    64^3 subdomain-size sweep (the configurations small enough for one core)."""
+    import oracle
+    oracle.set_threads(1)
+    out = {}
+    for wl in ("laplace16_sub8x8x4", "laplace64_sub4", "laplace64_sub8", "laplace64_sub16x16x8"):
+        s, w = workload_system(wl)
+        d = oracle.decompose(s.row_ptr, s.col, s.val, w["grid"], w["sub"], factor=False)
+        M = d.ildu()
+        n = s.n
+        nl = int(np.sum(d.Add.col < np.repeat(np.arange(n), np.diff(d.Add.row_ptr))))
+        nu = d.Add.nnzb - nl - n
+        apply_bytes = 72 * (nl + nu + n) + 4 * (nl + nu) + 8 * (n + 1) + 48 * n
+        r = np.random.default_rng(3).uniform(-1, 1, 3 * n)
+        times = []
+        t_end = time.perf_counter() + budget_s / 4
+        while not times or time.perf_counter() < t_end:
+            t0 = time.perf_counter()
+            oracle.apply_ildu0(M, r)
+            times.append(time.perf_counter() - t0)
+        t = float(np.median(times))
+        out[wl] = {"gbs": round(apply_bytes / t / 1e9, 3), "ms": round(t * 1e3, 3), "applies": len(times)}
+    oracle.set_threads(oracle_threads())
+    return out
 
 
 # --------------------------------------------------------------------------- reference arm
