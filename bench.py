@@ -459,7 +459,7 @@ def run_batched(args, dev):
     """64 laplace systems with sides drawn from 24..96 (seed 5000 + s), FP32 factors,
     FP64 solver; subdomain box picked by the autotuner per size class of the
     batch (three classes of equal count, each tuned on its median system,
-    median of three timed solves per candidate) and the batch's block size on
+    median of five timed solves per candidate) and the batch's block size on
     the batched solve itself; all systems solved to 1e-8 by
     bicgstab_solve_batched. The tuning runs twice: the choices of the two runs
     are reported side by side (stability)."""

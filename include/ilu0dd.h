@@ -97,7 +97,11 @@ typedef struct {
 
 typedef struct {
   int32_t factor_prec;      /* ILU0DD_F64 / ILU0DD_F32 / ILU0DD_BF16 / ILU0DD_DF64 */
-  int32_t threads_per_cta;  /* apply block size; 0 = one warp per row group of the widest level, 1.5x for FP64/DF64 (<= 384) */
+  int32_t threads_per_cta;  /* apply block size, a multiple of 32; 0 = from the widest level: 3x3 FP64 / DF64
+                               factors (three threads per row, ten rows per warp) one warp per row group,
+                               1.5x from four groups, at most 384; 3x3 FP32 / BF16 factors (one thread per
+                               row, 32 rows per warp) 1.5 warps per row group, at most 256; scalar rows (32
+                               per warp) one warp per row group, at most 384 */
   int32_t prefetch_bytes;   /* apply: L2 prefetch distance per block, bytes (multiple of 16); 0 = 32768 (16384 for BF16) */
   int32_t maxit;            /* BiCGSTAB iteration limit; 0 = 10000 */
   double rtol;              /* stop when ||r||_2/||b||_2 < rtol; 0 = 1e-8 */

@@ -10,11 +10,12 @@ measures time to solution through the library:
   does not fit (shared memory, block size) are dropped by the library's
   host-side structural plan (``workspace_size``) before any device work;
 * each remaining candidate gets a context, one warm-up solve (CUDA-graph
-  capture) and ``repeats`` timed solves; its time is the median, with the
+  capture) and ``repeats`` (5) timed solves; its time is the median, with the
   minimum and maximum kept as its spread;
 * the choice is the first candidate (in candidate order) whose median lies
-  within ``tie`` (2 %) of the fastest one, so that near-equal candidates do
-  not swap places from run to run on noise;
+  within ``tie`` (5 %) of the fastest one, so that near-equal candidates do
+  not swap places from run to run on timer noise (solves of the smallest
+  systems take about a millisecond);
 * a ragged batch is tuned per size class: the systems are sorted by size and
   cut into classes of equal count, and each class's subdomain box is tuned on
   its median system (``autotune_batch``); the batch's block size, one for all
@@ -52,13 +53,13 @@ def candidates(system, subs=DEFAULT_SUBS, threads=DEFAULT_THREADS, factor_prec="
     return out
 
 
-def pick(trials, tie=0.02):
+def pick(trials, tie=0.05):
     """The first trial whose median is within `tie` of the fastest median."""
     fastest = min(t["seconds"] for t in trials)
     return next(t for t in trials if t["seconds"] <= (1.0 + tie) * fastest)
 
 
-def autotune(system, subs=DEFAULT_SUBS, threads=DEFAULT_THREADS, factor_prec="f32", repeats=3, tie=0.02,
+def autotune(system, subs=DEFAULT_SUBS, threads=DEFAULT_THREADS, factor_prec="f32", repeats=5, tie=0.05,
              **opts):
     """Return (best, trials) for a synth.System-like object (row_ptr, col, val,
     nx, ny, nz, b). Each trial: sub, threads_per_cta (as resolved by the
@@ -124,7 +125,7 @@ def autotune_batch(systems, nclasses=3, **kw):
     return classes, choice
 
 
-def tune_batch_threads(systems, boxes, threads=(128, 192, 256), factor_prec="f32", repeats=3, tie=0.02, **opts):
+def tune_batch_threads(systems, boxes, threads=(128, 192, 256), factor_prec="f32", repeats=3, tie=0.05, **opts):
     """Block size of a batched launch (one for every system of the batch):
     for each candidate, contexts with the given per-system boxes and that
     block size, one warm-up batched solve (graph capture) and `repeats` timed

@@ -412,14 +412,16 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   // 0.064 -> 0.062 ms); FP32/BF16 groups and small boxes run faster without.
   const int groups = (int)ceil_div(widest, p.rows_per_warp);
   const bool fp64_arith = o->factor_prec == ILU0DD_F64 || o->factor_prec == ILU0DD_DF64;
-  // the row-thread layout (32 rows per warp): three warps per row group of the
-  // widest level, so that two thirds of the warps load ahead for later levels
+  // the row-thread layout (32 rows per warp): 1.5 warps per row group of the
+  // widest level, the spare warps loading ahead for later levels (measured at
+  // 160^3: 192 threads for the 16x16x8 box; 128 / 160 / 224 / 256 are slower
+  // or within 1 %)
   const int warps = p.row_thread ? std::max(1, (3 * groups + 1) / 2) : fp64_arith && groups >= 4 ? groups + (groups + 1) / 2 : groups;
   const int max_threads = p.row_thread ? kMaxRtThreads : kMaxApplyThreads;
   p.threads = o->threads_per_cta > 0 ? o->threads_per_cta : std::min(max_threads, 32 * warps);
   if (p.threads % 32 || p.threads > max_threads || p.threads < 32) {
     *why = "threads_per_cta must be a multiple of 32 in [32, " + std::to_string(max_threads) +
-           "] (384 with FP64 or scalar factors, 256 with 3x3 FP32, BF16 or DF64 factors)";
+           "] (256 with 3x3 FP32 or BF16 factors, else 384)";
     return ILU0DD_ERR_INVALID;
   }
   // default L2 prefetch distance: 32 KiB of stream, 16 KiB for BF16 whose
