@@ -99,9 +99,11 @@ typedef struct {
   int32_t factor_prec;      /* ILU0DD_F64 / ILU0DD_F32 / ILU0DD_BF16 / ILU0DD_DF64 */
   int32_t threads_per_cta;  /* apply block size, a multiple of 32; 0 = from the widest level: 3x3 FP64 / DF64
                                factors (three threads per row, ten rows per warp) one warp per row group,
-                               1.5x from four groups, at most 384; 3x3 FP32 / BF16 factors (one thread per
-                               row, 32 rows per warp) 1.5 warps per row group, at most 256; scalar rows (32
-                               per warp) one warp per row group, at most 384 */
+                               1.5x from four groups, at most 384; 3x3 FP32 / BF16 factors with no row of
+                               more than three blocks on either side (one thread per row, 32 rows per warp,
+                               ILU0DD_Q_ROW_THREAD = 1) 1.5 warps per row group, at most 256; other 3x3
+                               FP32 / BF16 systems (three threads per row) one warp per row group, at most
+                               384; scalar rows (32 per warp) one warp per row group, at most 384 */
   int32_t prefetch_bytes;   /* apply: L2 prefetch distance per block, bytes (multiple of 16); 0 = 32768 (16384 for BF16) */
   int32_t maxit;            /* BiCGSTAB iteration limit; 0 = 10000 */
   double rtol;              /* stop when ||r||_2/||b||_2 < rtol; 0 = 1e-8 */
@@ -389,7 +391,8 @@ int bicgstab_state(ilu0dd_ctx* ctx, ilu0dd_info* info, void* stream);
  * Batched BiCGSTAB over many independent systems (the batching pattern; the
  * paper has no batched solver). Each system is an ilu0dd_ctx from
  * ilu0_dd_setup (any grid and subdomain size; all with the same block dimension,
- * 3x3 or scalar, the same factor_prec and the current device; otherwise
+ * 3x3 or scalar, the same factor_prec, the same apply mapping
+ * (ILU0DD_Q_ROW_THREAD) and the current device; otherwise
  * ilu0dd_batch_create returns ILU0DD_ERR_INVALID). It records them in a small device
  * workspace (ilu0dd_batch_workspace_size bytes, 256-byte aligned, caller-owned)
  * and keeps pointers to the contexts: they must outlive the batch, and a
@@ -461,6 +464,9 @@ int ilu0_dd_export(const ilu0dd_ctx* ctx, int what, void* host_dst, size_t bytes
 #define ILU0DD_Q_ITER_KERNELS 16  /* kernel launches per BiCGSTAB iteration */
 #define ILU0DD_Q_SELL_SLOTS 17    /* slots of the sliced-ELL SpMV matrix (32 entries each) */
 #define ILU0DD_Q_BLOCK_DIM 18     /* block dimension bs (3 or 1); vectors hold bs*N doubles */
+#define ILU0DD_Q_ROW_THREAD 19    /* apply mapping: 1 one thread per 3x3 row (FP32/BF16 factors, no row
+                                     with more than three blocks on either side), 0 three threads per
+                                     3x3 row (or one per scalar row) */
 
 int ilu0_dd_query(const ilu0dd_ctx* ctx, int what, int64_t* value);
 

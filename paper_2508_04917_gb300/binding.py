@@ -29,7 +29,7 @@ X_STREAM, X_SELL_COL, X_SELL_VAL = 13, 14, 15
 
 Q = dict(n=0, nnzb=1, kept=2, nsub=3, nl=4, nu=5, apply_bytes=6, spmv_bytes=7, stream_bytes=8,
          threads=9, smem=10, pieces=11, cuda_error=12, max_levels=13, workspace=14,
-         apply_kernels=15, iter_kernels=16, sell_slots=17, block_dim=18)
+         apply_kernels=15, iter_kernels=16, sell_slots=17, block_dim=18, row_thread=19)
 
 
 class Ilu0DDError(RuntimeError):

@@ -27,6 +27,7 @@ struct ilu0dd_batch {
   int32_t* d_flags = nullptr;
   int64_t n_apply = 0, n_tile = 0;
   int factor_prec = 0, bs = 3, threads = 0;
+  int row_thread = 0;  // the systems' stream layout (SysDesc.row_thread, the same for all)
   size_t smem = 0;
   int grid_apply = 1, grid_tile = 1;
   double rtol = 1e-8;
@@ -73,13 +74,13 @@ BatchLayout batch_layout(ilu0dd_ctx* const* ctxs, int32_t nsys, int64_t* n_apply
 
 cudaError_t batch_iteration(const ilu0dd_batch* b, cudaStream_t s) {
   cudaError_t e;
-  if ((e = launch_apply_batched(b->d_sys, b->d_apply_items, b->n_apply, kModeP, b->factor_prec, b->bs, b->threads,
-                                b->smem, b->grid_apply, s)) != cudaSuccess)
+  if ((e = launch_apply_batched(b->d_sys, b->d_apply_items, b->n_apply, kModeP, b->factor_prec, b->bs, b->row_thread,
+                                b->threads, b->smem, b->grid_apply, s)) != cudaSuccess)
     return e;
   if ((e = launch_spmv_batched(b->d_sys, b->d_tile_items, b->n_tile, 1, b->bs, b->grid_tile, s)) != cudaSuccess)
     return e;
-  if ((e = launch_apply_batched(b->d_sys, b->d_apply_items, b->n_apply, kModeS, b->factor_prec, b->bs, b->threads,
-                                b->smem, b->grid_apply, s)) != cudaSuccess)
+  if ((e = launch_apply_batched(b->d_sys, b->d_apply_items, b->n_apply, kModeS, b->factor_prec, b->bs, b->row_thread,
+                                b->threads, b->smem, b->grid_apply, s)) != cudaSuccess)
     return e;
   if ((e = launch_spmv_batched(b->d_sys, b->d_tile_items, b->n_tile, 2, b->bs, b->grid_tile, s)) != cudaSuccess)
     return e;
@@ -135,8 +136,8 @@ int ilu0dd_batch_create(ilu0dd_ctx* const* ctxs, int32_t nsys, const ilu0dd_opts
   *out = nullptr;
   for (int32_t i = 0; i < nsys; ++i)
     if (!ctxs[i] || ctxs[i]->dev.factor_prec != ctxs[0]->dev.factor_prec || ctxs[i]->device != ctxs[0]->device ||
-        ctxs[i]->dev.bs != ctxs[0]->dev.bs)
-      return ILU0DD_ERR_INVALID;  // one device, one factor precision, one block dimension per batch
+        ctxs[i]->dev.bs != ctxs[0]->dev.bs || ctxs[i]->dev.sd.row_thread != ctxs[0]->dev.sd.row_thread)
+      return ILU0DD_ERR_INVALID;  // one device, factor precision, block dimension and apply mapping per batch
   int64_t na = 0, nt = 0;
   const BatchLayout L = batch_layout(ctxs, nsys, &na, &nt);
   if (!d_workspace || ws_bytes < L.total || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
@@ -156,6 +157,7 @@ int ilu0dd_batch_create(ilu0dd_ctx* const* ctxs, int32_t nsys, const ilu0dd_opts
   b->n_tile = nt;
   b->factor_prec = ctxs[0]->dev.factor_prec;
   b->bs = ctxs[0]->dev.bs;
+  b->row_thread = ctxs[0]->dev.sd.row_thread;
   ilu0dd_opts o;
   ilu0dd_default_opts(&o);
   if (opts) o = *opts;
@@ -204,7 +206,7 @@ int ilu0dd_batch_create(ilu0dd_ctx* const* ctxs, int32_t nsys, const ilu0dd_opts
     return ILU0DD_ERR_CUDA;
   }
   b->grid_apply = (int)std::min<int64_t>(std::max<int64_t>(1, na),
-                                         (int64_t)nsm * apply_blocks_per_sm(b->factor_prec, b->bs, b->threads, b->smem));
+                                         (int64_t)nsm * apply_blocks_per_sm(b->factor_prec, b->bs, b->row_thread, b->threads, b->smem));
   b->grid_tile = (int)std::min<int64_t>(std::max<int64_t>(1, nt), (int64_t)nsm * tile_blocks_per_sm(b->bs));
   b->h_status.resize(nsys);
   *out = b;

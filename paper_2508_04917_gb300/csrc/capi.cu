@@ -227,6 +227,7 @@ int setup_numeric(ilu0dd_ctx* c, const ilu0dd_bsr* A, const ilu0dd_opts& o, void
     S.prefetch_bytes = p.prefetch_bytes;
     S.vec_bytes = (int)(p.smem_bytes - kApplyTailSmem);
     S.wait_stuck = -1;
+    S.row_thread = p.row_thread ? 1 : 0;
     S.slice_off = reinterpret_cast<const int32_t*>(c->ws + L.sell_off);
     S.sell_col = reinterpret_cast<const int32_t*>(c->ws + L.sell_col);
     S.sell_val = reinterpret_cast<const double*>(c->ws + L.sell_val);
@@ -827,6 +828,7 @@ int ilu0_dd_query(const ilu0dd_ctx* c, int what, int64_t* v) {
     case ILU0DD_Q_ITER_KERNELS: *v = 5; break;
     case ILU0DD_Q_SELL_SLOTS: *v = p.sell_slots; break;
     case ILU0DD_Q_BLOCK_DIM: *v = p.bs; break;
+    case ILU0DD_Q_ROW_THREAD: *v = p.row_thread ? 1 : 0; break;
     default: return ILU0DD_ERR_INVALID;
   }
   return ILU0DD_OK;

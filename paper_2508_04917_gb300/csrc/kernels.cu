@@ -246,11 +246,13 @@ __device__ __forceinline__ void wait_row_flag(const SysDesc& S, volatile uint8_t
 template <typename TF, int MODE, int PART = 0, int SYNC = 0, int TRAV = 0>
 __device__ __forceinline__ void apply_block_rt(const SysDesc& S, int sub, const double* r, double* z);
 
-template <typename TF, int MODE, int PART = 0, int BS = 3, int SYNC = 0, int TRAV = 0, int VGLOB = 0>
+// RT 1: the row-thread layout (apply_block_rt); RT 0: three threads per 3x3
+// row, one per scalar row.
+template <typename TF, int MODE, int PART = 0, int BS = 3, int SYNC = 0, int TRAV = 0, int VGLOB = 0, int RT = 0>
 __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const double* r, double* z) {
   static_assert(BS == 1 || BS == 3, "block dimension 1 or 3");
-  if constexpr (BS == 3 && (std::is_same<TF, float>::value || std::is_same<TF, bf16s>::value)) {
-    static_assert(!VGLOB, "global vector: FP64 only");
+  if constexpr (RT) {
+    static_assert(BS == 3 && !VGLOB, "row-thread layout: 3x3 blocks, vector in shared memory");
     apply_block_rt<TF, MODE, PART, SYNC, TRAV>(S, sub, r, z);
   } else {
   constexpr int RPW = BS == 3 ? kRowsPerWarp : 32;  // rows per warp
@@ -467,10 +469,16 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
         }
         // Rows with more than kDescSlots blocks (general patterns): the further
         // slots, G at a time with all their loads issued first (the slot
-        // counts come from the record head), into two alternating
-        // accumulators added at the end.
+        // counts come from the record head). FP64-arithmetic applies (FP64,
+        // DF64) multiply-add them in slot (ascending column) order into the
+        // one accumulator, as the first slots; FP32 arithmetic alternates
+        // two accumulators, added at the end, to shorten the dependency
+        // chain (measured on GB300, unstructured 128^3: FP64 0.779 -> 0.770
+        // ms and DF64 0.629 -> 0.608 with one accumulator; FP32 0.336 with
+        // two against 0.388 with one).
         if (w > kDescSlots && nsl == kDescSlots) {
           constexpr int G = sizeof(TV) >= 8 ? 4 : 3;
+          constexpr bool two = sizeof(TV) < 8;
           TV acc_b = TV(0);
           for (int sl = kDescSlots; sl < w; sl += G) {
             uint32_t cs[G], off[G];
@@ -496,7 +504,7 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
 #pragma unroll
             for (int u = 0; u < G; ++u) {
               if (has[u]) {
-                TV& a2 = (u & 1) ? acc_b : acc;
+                TV& a2 = two && (u & 1) ? acc_b : acc;
 #pragma unroll
                 for (int c = 0; c < BS; ++c) a2 = mac(-v[u][c], y[BS * cl[u] + c], a2);
               }
@@ -504,7 +512,7 @@ __device__ __forceinline__ void apply_block(const SysDesc& S, int sub, const dou
             c0 = cc;
             if (!has[G - 1]) break;
           }
-          acc = mac(TV(1), acc_b, acc);
+          if constexpr (two) acc = mac(TV(1), acc_b, acc);
         }
         y[BS * row + comp] = acc;
       }
@@ -613,10 +621,11 @@ __device__ __forceinline__ void rt_sub_block(const RtBlock<TF>& b, const TV (&x)
 }
 
 // The fused apply with one thread per row (see the comment above apply_block):
-// each thread loads its row's D^-1 block and its blocks of the first
-// kDescSlots slots before the wait for the previous level (loading the FP32
-// slots after the wait instead cost 12 % at 160^3), then forms all three
-// components of the row.
+// each thread loads its row's D^-1 block and all its blocks (the plan takes
+// this mapping only when no row has more than kDescSlots blocks on either
+// side) before the wait for the previous level (loading the FP32 slots after
+// the wait instead cost 12 % at 160^3), then forms all three components of
+// the row.
 template <typename TF, int MODE, int PART, int SYNC, int TRAV>
 __device__ __forceinline__ void apply_block_rt(const SysDesc& S, int sub, const double* r, double* z) {
   constexpr int RPW = 32;
@@ -742,22 +751,6 @@ __device__ __forceinline__ void apply_block_rt(const SysDesc& S, int sub, const 
               rt_sub_block<TF, TV>(blk[sl], x, acc);
             }
           }
-          // rows with more than kDescSlots blocks (general patterns): the
-          // further slots one at a time, their counts from the record head
-          if (w > kDescSlots && nsl == kDescSlots) {
-            for (int sl = kDescSlots; sl < w; ++sl) {
-              const uint32_t cs = (uint32_t)gu16(rec + 2 * sl);
-              if ((uint32_t)trow >= cs) break;  // counts do not grow with the slot
-              const int cl = gu16(gs + (cbase + 2u * (c0 + (uint32_t)trow)));
-              RtBlock<TF> b;
-              b.load(gs + sb, cs, (uint32_t)trow);
-              TV x[3];
-              rt_get3<TV, VS>(y, cl, x);
-              rt_sub_block<TF, TV>(b, x, acc);
-              sb += rt_bytes<TF>(cs);
-              c0 += cs;
-            }
-          }
           rt_put3<TV, VS>(y, row, acc);
         }
       } else {
@@ -821,45 +814,49 @@ __device__ __forceinline__ void apply_block_rt(const SysDesc& S, int sub, const 
   store_vector<TV, 3, VS>(cd, y, z, kscale);
 }
 
+// Kernel instances come per (factor type, block dimension BS, mapping RT):
+// RT 1 is the row-thread layout (3x3 blocks, FP32 or BF16 factors, rows of at
+// most kDescSlots blocks a side), RT 0 three threads per 3x3 row or one per
+// scalar row. The plan's row_thread flag picks the instance at launch.
+template <typename TF>
+constexpr bool kHasRowThread = std::is_same<TF, float>::value || std::is_same<TF, bf16s>::value;
+
 // Launch bounds of an apply instance (see kMaxRtThreads): the row-thread
-// layout (3x3 blocks with FP32 or BF16 factors) at up to 256 threads and three
-// (FP32, 80 registers) or four (BF16, 64) blocks per SM, the others at up to
-// 384 threads and three (56).
-template <typename TF, int BS>
+// instances at up to 256 threads and three (FP32, 80 registers) or four
+// (BF16, 64) blocks per SM; the three-thread and scalar instances at up to
+// 384 threads and three (56 registers; at four, 40 registers, the scalar and
+// FP64 instances spill and run slower).
+template <typename TF, int BS, int RT>
 struct ApplyLaunch {
-  static constexpr bool rt = BS == 3 && (std::is_same<TF, float>::value || std::is_same<TF, bf16s>::value);
-  static constexpr int threads = rt ? kMaxRtThreads : kMaxApplyThreads;
+  static_assert(!RT || (BS == 3 && kHasRowThread<TF>), "row-thread layout: 3x3 blocks, FP32 or BF16 factors");
+  static constexpr int threads = RT ? kMaxRtThreads : kMaxApplyThreads;
   static constexpr int min_blocks =
-      !rt ? kApplyMinBlocks : std::is_same<TF, float>::value ? kRtMinBlocksF32 : kRtMinBlocksBF16;
+      !RT ? kApplyMinBlocks : std::is_same<TF, float>::value ? kRtMinBlocksF32 : kRtMinBlocksBF16;
 };
 
-// The three-thread and scalar instances are compiled for three resident
-// blocks per SM (56 registers; at four, 40 registers, the scalar and FP64
-// instances spill and run slower); the row-thread instances as ApplyLaunch
-// says.
-template <typename TF, int MODE, int BS>
-__global__ void __launch_bounds__(ApplyLaunch<TF, BS>::threads, ApplyLaunch<TF, BS>::min_blocks)
+template <typename TF, int MODE, int BS, int RT>
+__global__ void __launch_bounds__(ApplyLaunch<TF, BS, RT>::threads, ApplyLaunch<TF, BS, RT>::min_blocks)
     ildu0_apply_kernel(SysDesc S, const double* r, double* z, int sub0) {
-  apply_block<TF, MODE, 0, BS>(S, sub0 + blockIdx.x, r, z);
+  apply_block<TF, MODE, 0, BS, 0, 0, 0, RT>(S, sub0 + blockIdx.x, r, z);
 }
 
 // The plain apply with Algorithm 4's synchronization (row flags, bounded
 // spin loops) instead of the per-level mbarriers: the same arithmetic in the
 // same order, for the synchronization ablation.
-template <typename TF, int BS>
-__global__ void __launch_bounds__(ApplyLaunch<TF, BS>::threads, ApplyLaunch<TF, BS>::min_blocks)
+template <typename TF, int BS, int RT>
+__global__ void __launch_bounds__(ApplyLaunch<TF, BS, RT>::threads, ApplyLaunch<TF, BS, RT>::min_blocks)
     ildu0_apply_rowsync_kernel(SysDesc S, const double* r, double* z) {
-  apply_block<TF, kModePlain, 0, BS, 1>(S, blockIdx.x, r, z);
+  apply_block<TF, kModePlain, 0, BS, 1, 0, 0, RT>(S, blockIdx.x, r, z);
 }
 
 // The apply with the edge-centric traversal of the paper (threads over the
 // blocks of a level, shared-memory atomics into the rows) instead of the
 // row-wise one: the traversal ablation and the solver's opts.traversal = 1
 // (FP64, FP32 and BF16 factors; every mode).
-template <typename TF, int MODE, int BS>
-__global__ void __launch_bounds__(ApplyLaunch<TF, BS>::threads, ApplyLaunch<TF, BS>::min_blocks)
+template <typename TF, int MODE, int BS, int RT>
+__global__ void __launch_bounds__(ApplyLaunch<TF, BS, RT>::threads, ApplyLaunch<TF, BS, RT>::min_blocks)
     ildu0_apply_edge_kernel(SysDesc S, const double* r, double* z, int sub0) {
-  apply_block<TF, MODE, 0, BS, 0, 1>(S, sub0 + blockIdx.x, r, z);
+  apply_block<TF, MODE, 0, BS, 0, 1, 0, RT>(S, sub0 + blockIdx.x, r, z);
 }
 
 // The plain FP64 apply with the subdomain vector in global memory (z itself)
@@ -873,60 +870,49 @@ __global__ void __launch_bounds__(kMaxApplyThreads, kApplyMinBlocks)
 
 // The unfused apply's two launches (plain mode): PART 1 = L sweep, r -> z;
 // PART 2 = D^-1 and U~ sweep, z -> z in place.
-template <typename TF, int PART, int BS>
-__global__ void __launch_bounds__(ApplyLaunch<TF, BS>::threads, ApplyLaunch<TF, BS>::min_blocks)
+template <typename TF, int PART, int BS, int RT>
+__global__ void __launch_bounds__(ApplyLaunch<TF, BS, RT>::threads, ApplyLaunch<TF, BS, RT>::min_blocks)
     ildu0_apply_part_kernel(SysDesc S, const double* r, double* z) {
-  apply_block<TF, kModePlain, PART, BS>(S, blockIdx.x, r, z);
+  apply_block<TF, kModePlain, PART, BS, 0, 0, 0, RT>(S, blockIdx.x, r, z);
 }
 
-// Batched apply (modes P and S): persistent blocks walk (system, subdomain) items.
-template <typename TF, int MODE, int BS>
-__global__ void __launch_bounds__(ApplyLaunch<TF, BS>::threads, ApplyLaunch<TF, BS>::min_blocks)
+// Batched apply (modes P and S): persistent blocks walk (system, subdomain)
+// items; every system of a batch has the same mapping.
+template <typename TF, int MODE, int BS, int RT>
+__global__ void __launch_bounds__(ApplyLaunch<TF, BS, RT>::threads, ApplyLaunch<TF, BS, RT>::min_blocks)
     ildu0_apply_batched(const SysDesc* __restrict__ sys, const BatchItem* __restrict__ items, int64_t nitems) {
   for (int64_t i = blockIdx.x; i < nitems; i += gridDim.x) {
     const BatchItem it = items[i];
     const SysDesc& S = sys[it.sys];
-    apply_block<TF, MODE, 0, BS>(S, it.local, S.vec[kVecR], S.vec[MODE == kModeP ? kVecPh : kVecSh]);
+    apply_block<TF, MODE, 0, BS, 0, 0, 0, RT>(S, it.local, S.vec[kVecR], S.vec[MODE == kModeP ? kVecPh : kVecSh]);
     __syncthreads();  // the next item reuses shared memory
   }
+}
+
+template <typename TF, int MODE, int BS, int RT>
+static cudaError_t configure_layout(int sm) {
+  constexpr cudaFuncAttribute kSmem = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(ildu0_apply_kernel<TF, MODE, BS, RT>, kSmem, sm);
+  if (e == cudaSuccess && MODE != kModePlain) e = cudaFuncSetAttribute(ildu0_apply_batched<TF, MODE, BS, RT>, kSmem, sm);
+  if constexpr (MODE == kModePlain) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(ildu0_apply_part_kernel<TF, 1, BS, RT>, kSmem, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(ildu0_apply_part_kernel<TF, 2, BS, RT>, kSmem, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(ildu0_apply_rowsync_kernel<TF, BS, RT>, kSmem, sm);
+    if constexpr (std::is_same<TF, double>::value)
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(ildu0_apply_vglobal_kernel<BS>, kSmem, sm);
+  }
+  if constexpr (!std::is_same<TF, df64s>::value)
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(ildu0_apply_edge_kernel<TF, MODE, BS, RT>, kSmem, sm);
+  return e;
 }
 
 template <typename TF, int MODE>
 static cudaError_t configure_one(size_t smem) {
   const int sm = (int)smem;
-  cudaError_t e = cudaFuncSetAttribute(ildu0_apply_kernel<TF, MODE, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(ildu0_apply_kernel<TF, MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess && MODE != kModePlain)
-    e = cudaFuncSetAttribute(ildu0_apply_batched<TF, MODE, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess && MODE != kModePlain)
-    e = cudaFuncSetAttribute(ildu0_apply_batched<TF, MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (MODE == kModePlain) {
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ildu0_apply_part_kernel<TF, 1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ildu0_apply_part_kernel<TF, 2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ildu0_apply_part_kernel<TF, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ildu0_apply_part_kernel<TF, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ildu0_apply_rowsync_kernel<TF, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ildu0_apply_rowsync_kernel<TF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if constexpr (std::is_same<TF, double>::value) {
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ildu0_apply_vglobal_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ildu0_apply_vglobal_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    }
-  }
-  if constexpr (!std::is_same<TF, df64s>::value) {
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ildu0_apply_edge_kernel<TF, MODE, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ildu0_apply_edge_kernel<TF, MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  }
+  cudaError_t e = configure_layout<TF, MODE, 3, 0>(sm);
+  if (e == cudaSuccess) e = configure_layout<TF, MODE, 1, 0>(sm);
+  if constexpr (kHasRowThread<TF>)
+    if (e == cudaSuccess) e = configure_layout<TF, MODE, 3, 1>(sm);
   return e;
 }
 
@@ -956,35 +942,52 @@ cudaError_t apply_configure(const DevCtx& d) {
   return e;
 }
 
-template <typename TF, int BS>
-static cudaError_t launch_apply_tb(const DevCtx& d, int mode, const double* r, double* z, int sub0, int nsub,
-                                   cudaStream_t s) {
-  dim3 grid(nsub), block(d.threads);
-  if constexpr (!std::is_same<TF, df64s>::value) {
-    if (d.traversal == 1) {  // edge-centric (opts.traversal)
-      if (mode == kModePlain)
-        ildu0_apply_edge_kernel<TF, kModePlain, BS><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
-      else if (mode == kModeP)
-        ildu0_apply_edge_kernel<TF, kModeP, BS><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
-      else
-        ildu0_apply_edge_kernel<TF, kModeS, BS><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
-      return cudaGetLastError();
-    }
-  }
-  if (mode == kModePlain)
-    ildu0_apply_kernel<TF, kModePlain, BS><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
-  else if (mode == kModeP)
-    ildu0_apply_kernel<TF, kModeP, BS><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
-  else
-    ildu0_apply_kernel<TF, kModeS, BS><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
-  return cudaGetLastError();
+// Calls L.template run<BS, RT>() for the instance that fits a system with
+// block dimension bs and row-thread flag rt.
+template <typename TF, typename L>
+static cudaError_t by_layout(int bs, int rt, const L& l) {
+  if (bs == 1) return l.template run<1, 0>();
+  if constexpr (kHasRowThread<TF>)
+    if (rt) return l.template run<3, 1>();
+  return l.template run<3, 0>();
 }
+
+template <typename TF>
+struct ApplyRun {
+  const DevCtx& d;
+  int mode;
+  const double* r;
+  double* z;
+  int sub0, nsub;
+  cudaStream_t s;
+  template <int BS, int RT>
+  cudaError_t run() const {
+    dim3 grid(nsub), block(d.threads);
+    if constexpr (!std::is_same<TF, df64s>::value) {
+      if (d.traversal == 1) {  // edge-centric (opts.traversal)
+        if (mode == kModePlain)
+          ildu0_apply_edge_kernel<TF, kModePlain, BS, RT><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
+        else if (mode == kModeP)
+          ildu0_apply_edge_kernel<TF, kModeP, BS, RT><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
+        else
+          ildu0_apply_edge_kernel<TF, kModeS, BS, RT><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
+        return cudaGetLastError();
+      }
+    }
+    if (mode == kModePlain)
+      ildu0_apply_kernel<TF, kModePlain, BS, RT><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
+    else if (mode == kModeP)
+      ildu0_apply_kernel<TF, kModeP, BS, RT><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
+    else
+      ildu0_apply_kernel<TF, kModeS, BS, RT><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z, sub0);
+    return cudaGetLastError();
+  }
+};
 
 template <typename TF>
 static cudaError_t launch_apply_t(const DevCtx& d, int mode, const double* r, double* z, int sub0, int nsub,
                                   cudaStream_t s) {
-  return d.bs == 1 ? launch_apply_tb<TF, 1>(d, mode, r, z, sub0, nsub, s)
-                   : launch_apply_tb<TF, 3>(d, mode, r, z, sub0, nsub, s);
+  return by_layout<TF>(d.bs, d.sd.row_thread, ApplyRun<TF>{d, mode, r, z, sub0, nsub, s});
 }
 
 cudaError_t launch_apply_range(const DevCtx& d, int mode, const double* r, double* z, int sub0, int nsub,
@@ -1000,19 +1003,26 @@ cudaError_t launch_apply(const DevCtx& d, int mode, const double* r, double* z, 
   return launch_apply_range(d, mode, r, z, 0, d.sd.nsub, s);
 }
 
-template <typename TF, int BS>
-static cudaError_t launch_unfused_tb(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
-  dim3 grid(d.sd.nsub), block(d.threads);
-  ildu0_apply_part_kernel<TF, 1, BS><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  ildu0_apply_part_kernel<TF, 2, BS><<<grid, block, d.smem_bytes, s>>>(d.sd, z, z);
-  return cudaGetLastError();
-}
+template <typename TF>
+struct UnfusedRun {
+  const DevCtx& d;
+  const double* r;
+  double* z;
+  cudaStream_t s;
+  template <int BS, int RT>
+  cudaError_t run() const {
+    dim3 grid(d.sd.nsub), block(d.threads);
+    ildu0_apply_part_kernel<TF, 1, BS, RT><<<grid, block, d.smem_bytes, s>>>(d.sd, r, z);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ildu0_apply_part_kernel<TF, 2, BS, RT><<<grid, block, d.smem_bytes, s>>>(d.sd, z, z);
+    return cudaGetLastError();
+  }
+};
 
 template <typename TF>
 static cudaError_t launch_unfused_t(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
-  return d.bs == 1 ? launch_unfused_tb<TF, 1>(d, r, z, s) : launch_unfused_tb<TF, 3>(d, r, z, s);
+  return by_layout<TF>(d.bs, d.sd.row_thread, UnfusedRun<TF>{d, r, z, s});
 }
 
 cudaError_t launch_apply_unfused(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
@@ -1023,43 +1033,40 @@ cudaError_t launch_apply_unfused(const DevCtx& d, const double* r, double* z, cu
   return launch_unfused_t<bf16s>(d, r, z, s);
 }
 
-template <typename TF, int BS>
-static cudaError_t launch_apply_batched_tb(const SysDesc* sys, const BatchItem* items, int64_t nitems, int mode,
-                                           int threads, size_t smem, int grid, cudaStream_t s) {
-  if (mode == kModeP)
-    ildu0_apply_batched<TF, kModeP, BS><<<grid, threads, smem, s>>>(sys, items, nitems);
-  else
-    ildu0_apply_batched<TF, kModeS, BS><<<grid, threads, smem, s>>>(sys, items, nitems);
-  return cudaGetLastError();
-}
-
-template <typename TF, int BS>
-static cudaError_t launch_rowsync_tb(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
-  ildu0_apply_rowsync_kernel<TF, BS><<<d.sd.nsub, d.threads, d.smem_rowsync, s>>>(d.sd, r, z);
-  return cudaGetLastError();
-}
-
 template <typename TF>
-static cudaError_t launch_rowsync_t(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
-  return d.bs == 1 ? launch_rowsync_tb<TF, 1>(d, r, z, s) : launch_rowsync_tb<TF, 3>(d, r, z, s);
-}
+struct RowsyncRun {
+  const DevCtx& d;
+  const double* r;
+  double* z;
+  cudaStream_t s;
+  template <int BS, int RT>
+  cudaError_t run() const {
+    ildu0_apply_rowsync_kernel<TF, BS, RT><<<d.sd.nsub, d.threads, d.smem_rowsync, s>>>(d.sd, r, z);
+    return cudaGetLastError();
+  }
+};
 
 cudaError_t launch_apply_rowsync(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
   if (d.sd.nsub == 0) return cudaSuccess;
-  if (d.factor_prec == ILU0DD_F64) return launch_rowsync_t<double>(d, r, z, s);
-  if (d.factor_prec == ILU0DD_F32) return launch_rowsync_t<float>(d, r, z, s);
-  if (d.factor_prec == ILU0DD_DF64) return launch_rowsync_t<df64s>(d, r, z, s);
-  return launch_rowsync_t<bf16s>(d, r, z, s);
+  const int bs = d.bs, rt = d.sd.row_thread;
+  if (d.factor_prec == ILU0DD_F64) return by_layout<double>(bs, rt, RowsyncRun<double>{d, r, z, s});
+  if (d.factor_prec == ILU0DD_F32) return by_layout<float>(bs, rt, RowsyncRun<float>{d, r, z, s});
+  if (d.factor_prec == ILU0DD_DF64) return by_layout<df64s>(bs, rt, RowsyncRun<df64s>{d, r, z, s});
+  return by_layout<bf16s>(bs, rt, RowsyncRun<bf16s>{d, r, z, s});
 }
 
 template <typename TF>
-static cudaError_t launch_edge_t(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
-  if (d.bs == 1)
-    ildu0_apply_edge_kernel<TF, kModePlain, 1><<<d.sd.nsub, d.threads, d.smem_bytes, s>>>(d.sd, r, z, 0);
-  else
-    ildu0_apply_edge_kernel<TF, kModePlain, 3><<<d.sd.nsub, d.threads, d.smem_bytes, s>>>(d.sd, r, z, 0);
-  return cudaGetLastError();
-}
+struct EdgeRun {
+  const DevCtx& d;
+  const double* r;
+  double* z;
+  cudaStream_t s;
+  template <int BS, int RT>
+  cudaError_t run() const {
+    ildu0_apply_edge_kernel<TF, kModePlain, BS, RT><<<d.sd.nsub, d.threads, d.smem_bytes, s>>>(d.sd, r, z, 0);
+    return cudaGetLastError();
+  }
+};
 
 cudaError_t launch_apply_vglobal(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
   if (d.sd.nsub == 0) return cudaSuccess;
@@ -1073,48 +1080,68 @@ cudaError_t launch_apply_vglobal(const DevCtx& d, const double* r, double* z, cu
 
 cudaError_t launch_apply_edge(const DevCtx& d, const double* r, double* z, cudaStream_t s) {
   if (d.sd.nsub == 0) return cudaSuccess;
-  if (d.factor_prec == ILU0DD_F64) return launch_edge_t<double>(d, r, z, s);
-  if (d.factor_prec == ILU0DD_F32) return launch_edge_t<float>(d, r, z, s);
-  if (d.factor_prec == ILU0DD_BF16) return launch_edge_t<bf16s>(d, r, z, s);
+  const int bs = d.bs, rt = d.sd.row_thread;
+  if (d.factor_prec == ILU0DD_F64) return by_layout<double>(bs, rt, EdgeRun<double>{d, r, z, s});
+  if (d.factor_prec == ILU0DD_F32) return by_layout<float>(bs, rt, EdgeRun<float>{d, r, z, s});
+  if (d.factor_prec == ILU0DD_BF16) return by_layout<bf16s>(bs, rt, EdgeRun<bf16s>{d, r, z, s});
   return cudaErrorInvalidValue;  // DF64 pairs have no atomic add
 }
 
 template <typename TF>
-static cudaError_t launch_apply_batched_t(const SysDesc* sys, const BatchItem* items, int64_t nitems, int mode,
-                                          int bs, int threads, size_t smem, int grid, cudaStream_t s) {
-  return bs == 1 ? launch_apply_batched_tb<TF, 1>(sys, items, nitems, mode, threads, smem, grid, s)
-                 : launch_apply_batched_tb<TF, 3>(sys, items, nitems, mode, threads, smem, grid, s);
-}
+struct BatchedRun {
+  const SysDesc* sys;
+  const BatchItem* items;
+  int64_t nitems;
+  int mode, threads;
+  size_t smem;
+  int grid;
+  cudaStream_t s;
+  template <int BS, int RT>
+  cudaError_t run() const {
+    if (mode == kModeP)
+      ildu0_apply_batched<TF, kModeP, BS, RT><<<grid, threads, smem, s>>>(sys, items, nitems);
+    else
+      ildu0_apply_batched<TF, kModeS, BS, RT><<<grid, threads, smem, s>>>(sys, items, nitems);
+    return cudaGetLastError();
+  }
+};
 
 cudaError_t launch_apply_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int mode,
-                                 int factor_prec, int bs, int threads, size_t smem, int grid, cudaStream_t s) {
+                                 int factor_prec, int bs, int row_thread, int threads, size_t smem, int grid,
+                                 cudaStream_t s) {
   if (nitems == 0) return cudaSuccess;
+  const int rt = row_thread;
   if (factor_prec == ILU0DD_F64)
-    return launch_apply_batched_t<double>(sys, items, nitems, mode, bs, threads, smem, grid, s);
+    return by_layout<double>(bs, rt, BatchedRun<double>{sys, items, nitems, mode, threads, smem, grid, s});
   if (factor_prec == ILU0DD_F32)
-    return launch_apply_batched_t<float>(sys, items, nitems, mode, bs, threads, smem, grid, s);
+    return by_layout<float>(bs, rt, BatchedRun<float>{sys, items, nitems, mode, threads, smem, grid, s});
   if (factor_prec == ILU0DD_DF64)
-    return launch_apply_batched_t<df64s>(sys, items, nitems, mode, bs, threads, smem, grid, s);
-  return launch_apply_batched_t<bf16s>(sys, items, nitems, mode, bs, threads, smem, grid, s);
+    return by_layout<df64s>(bs, rt, BatchedRun<df64s>{sys, items, nitems, mode, threads, smem, grid, s});
+  return by_layout<bf16s>(bs, rt, BatchedRun<bf16s>{sys, items, nitems, mode, threads, smem, grid, s});
 }
 
 template <typename TF>
-static cudaError_t batched_occupancy(int* n, int bs, int threads, size_t smem) {
-  return bs == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, ildu0_apply_batched<TF, kModeP, 1>, threads, smem)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, ildu0_apply_batched<TF, kModeP, 3>, threads, smem);
-}
+struct OccupancyRun {
+  int* n;
+  int threads;
+  size_t smem;
+  template <int BS, int RT>
+  cudaError_t run() const {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, ildu0_apply_batched<TF, kModeP, BS, RT>, threads, smem);
+  }
+};
 
-int apply_blocks_per_sm(int factor_prec, int bs, int threads, size_t smem) {
+int apply_blocks_per_sm(int factor_prec, int bs, int row_thread, int threads, size_t smem) {
   int n = 0;
   cudaError_t e;
   if (factor_prec == ILU0DD_F64)
-    e = batched_occupancy<double>(&n, bs, threads, smem);
+    e = by_layout<double>(bs, row_thread, OccupancyRun<double>{&n, threads, smem});
   else if (factor_prec == ILU0DD_F32)
-    e = batched_occupancy<float>(&n, bs, threads, smem);
+    e = by_layout<float>(bs, row_thread, OccupancyRun<float>{&n, threads, smem});
   else if (factor_prec == ILU0DD_DF64)
-    e = batched_occupancy<df64s>(&n, bs, threads, smem);
+    e = by_layout<df64s>(bs, row_thread, OccupancyRun<df64s>{&n, threads, smem});
   else
-    e = batched_occupancy<bf16s>(&n, bs, threads, smem);
+    e = by_layout<bf16s>(bs, row_thread, OccupancyRun<bf16s>{&n, threads, smem});
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;

@@ -38,6 +38,9 @@ struct SysDesc {
   // completion is never reached (-1: none; failure-path tests only)
   uint64_t wait_cycles;
   int32_t wait_stuck;
+  // 1: the stream is in the row-thread layout (3x3 blocks, FP32 or BF16
+  // factors, no row with more than kDescSlots blocks on either side)
+  int32_t row_thread;
 };
 
 // Host view of one context: the system and its launch configuration.
@@ -106,9 +109,11 @@ cudaError_t launch_permute(const DevCtx& d, const double* in, double* out, int d
 // `sys` is a device array of SysDesc; items list (system, subdomain) for the
 // apply and (system, dot tile) for the others. Systems whose solve is done are
 // skipped. `grid` blocks loop over the items (persistent launch). Every
-// system of one launch has block dimension `bs` (3 or 1).
+// system of one launch has block dimension `bs` (3 or 1) and the same
+// row-thread flag (SysDesc.row_thread).
 cudaError_t launch_apply_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int mode,
-                                 int factor_prec, int bs, int threads, size_t smem, int grid, cudaStream_t s);
+                                 int factor_prec, int bs, int row_thread, int threads, size_t smem, int grid,
+                                 cudaStream_t s);
 cudaError_t launch_spmv_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int kind, int bs,
                                 int grid, cudaStream_t s);
 cudaError_t launch_update_batched(const SysDesc* sys, const BatchItem* items, int64_t nitems, int bs, int grid,
@@ -124,7 +129,7 @@ cudaError_t launch_permute_batched(const SysDesc* sys, const BatchItem* items, i
 cudaError_t launch_gather_status(const SysDesc* sys, int32_t nsys, SolverScalars* out, cudaStream_t s);
 
 // Blocks per SM of the batched kernels (for persistent grids).
-int apply_blocks_per_sm(int factor_prec, int bs, int threads, size_t smem);
+int apply_blocks_per_sm(int factor_prec, int bs, int row_thread, int threads, size_t smem);
 int tile_blocks_per_sm(int bs);
 
 }  // namespace ilu0dd

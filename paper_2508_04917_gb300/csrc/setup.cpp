@@ -200,11 +200,6 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   Plan& p = *P;
   p = Plan();
   p.bs = bs;
-  // 3x3 blocks: FP64 and float-pair factors take three threads per row (ten
-  // rows per warp), FP32 and BF16 factors one thread per row (the row-thread
-  // layout); scalar rows one
-  p.row_thread = bs == 3 && (o->factor_prec == ILU0DD_F32 || o->factor_prec == ILU0DD_BF16);
-  p.rows_per_warp = bs == 3 && !p.row_thread ? kRowsPerWarp : 32;
   // per-phase wall times (opts.trace)
   double tprev = wall_seconds();
   std::string tlog;
@@ -379,6 +374,29 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
     *why = "the edge-centric traversal has no float-pair form (no atomic add on pairs)";
     return ILU0DD_ERR_INVALID;
   }
+  // blocks on each side of the diagonal per row (the jagged-diagonal sort key)
+  std::vector<int32_t> nlo(N), nup(N);
+  parallel_for(N, [&](int64_t i) {
+    int32_t lo = 0, up = 0;
+    for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1]; ++q) {
+      lo += p.dd_col[q] < i;
+      up += p.dd_col[q] > i;
+    }
+    nlo[i] = lo;
+    nup[i] = up;
+  });
+  int32_t side_max = 0;
+  for (int64_t i = 0; i < N; ++i) side_max = std::max(side_max, std::max(nlo[i], nup[i]));
+  // 3x3 blocks: FP64 and float-pair factors take three threads per row (ten
+  // rows per warp); FP32 and BF16 factors one thread per row (the row-thread
+  // layout) when no row has more than kDescSlots blocks on either side (all
+  // of a row's blocks then load ahead of the level wait; rows with more, as
+  // in 27-point patterns, take the three-thread mapping, which loads their
+  // further slots in groups: measured on GB300, unstructured 128^3 apply
+  // with one thread per row / three: FP32 0.574 / 0.336 ms, BF16 0.407 /
+  // 0.336); scalar rows one thread per row
+  p.row_thread = bs == 3 && (fp == ILU0DD_F32 || fp == ILU0DD_BF16) && side_max <= kDescSlots;
+  p.rows_per_warp = bs == 3 && !p.row_thread ? kRowsPerWarp : 32;
   p.factor_elem = (fp == ILU0DD_F64 || fp == ILU0DD_DF64) ? 8 : fp == ILU0DD_F32 ? 4 : 2;
   p.vec_elem = (fp == ILU0DD_F64 || fp == ILU0DD_DF64) ? 8 : 4;
   // shared-memory bytes per row of the subdomain vector: FP32 arithmetic in the
@@ -421,7 +439,7 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   p.threads = o->threads_per_cta > 0 ? o->threads_per_cta : std::min(max_threads, 32 * warps);
   if (p.threads % 32 || p.threads > max_threads || p.threads < 32) {
     *why = "threads_per_cta must be a multiple of 32 in [32, " + std::to_string(max_threads) +
-           "] (256 with 3x3 FP32 or BF16 factors, else 384)";
+           "] (256 with 3x3 FP32 or BF16 factors in the row-thread mapping, else 384)";
     return ILU0DD_ERR_INVALID;
   }
   // default L2 prefetch distance: 32 KiB of stream, 16 KiB for BF16 whose
@@ -438,17 +456,6 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   // ---- pieces: per subdomain, L levels 1.. then U levels 0.., rows of a level
   // sorted by block count (longest first), split by the block's row capacity
   p.cta.resize(p.nsub);
-  // blocks on each side of the diagonal per row (the jagged-diagonal sort key)
-  std::vector<int32_t> nlo(N), nup(N);
-  parallel_for(N, [&](int64_t i) {
-    int32_t lo = 0, up = 0;
-    for (int64_t q = p.dd_rp[i]; q < p.dd_rp[i + 1]; ++q) {
-      lo += p.dd_col[q] < i;
-      up += p.dd_col[q] > i;
-    }
-    nlo[i] = lo;
-    nup[i] = up;
-  });
   std::vector<std::vector<int32_t>> sub_rows(p.nsub);  // local rows, piece after piece
   std::vector<std::vector<PieceDesc>> sub_desc(p.nsub);
   std::vector<int64_t> sub_len(p.nsub, 0);

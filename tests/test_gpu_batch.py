@@ -93,6 +93,36 @@ def test_batch_rejects_mixed_precision():
         g.Batch([c0, c1])
 
 
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+def test_batched_three_thread_mapping(prec):
+    """FP32/BF16 systems with rows of more than three blocks a side (27-point
+    unstructured patterns, graph partitions) take the three-thread mapping;
+    their batch gives each system's single-solve bits. A batch that mixes them
+    with row-thread systems is refused (one mapping per batched launch)."""
+    ctxs = []
+    for grid, k, seed in [((10, 9, 8), 64, 31), ((16, 12, 10), 256, 32), ((12, 8, 6), 128, 33)]:
+        s = synth.unstructured(*grid, seed)
+        part, nparts = g.partition_bfs(s.row_ptr, s.col, k)
+        ctxs.append((g.Ilu0DD(s.row_ptr, s.col, s.val, part_id=part, nparts=nparts, factor_prec=prec), s))
+    assert all(c.query("row_thread") == 0 for c, _ in ctxs)
+    bs = [torch.from_numpy(s.b).cuda() for _, s in ctxs]
+    singles = [c.solve(b) for (c, _), b in zip(ctxs, bs)]
+    batch = g.Batch([c for c, _ in ctxs])
+    xs, infos = batch.solve(bs)
+    for (x1, i1), x2, i2 in zip(singles, xs, infos):
+        assert i1["status"] == i2["status"] == 0 and i1["iterations"] == i2["iterations"]
+        assert torch.equal(x1, x2)
+    batch.close()
+    grid, sub, s7 = _systems(SPECS[:1])[0]
+    narrow = g.Ilu0DD(s7.row_ptr, s7.col, s7.val, grid, sub, factor_prec=prec)
+    assert narrow.query("row_thread") == 1
+    with pytest.raises(g.Ilu0DDError):
+        g.Batch([narrow, ctxs[0][0]])
+    narrow.close()
+    for c, _ in ctxs:
+        c.close()
+
+
 def test_benchmark_batch_workload():
     """The benchmark's batched workload in full: 64 laplace systems with sides
     drawn from 24..96 (synth.ragged_batch), FP32 factors, 8x8x8 boxes at 160

@@ -49,6 +49,58 @@ def test_partitioned_decomposition_apply_and_solve(grid, k):
         ctx.close()
 
 
+@pytest.mark.parametrize("grid,k", CASES, ids=IDS)
+def test_partitioned_fp64_bitwise_vs_oracle_ildu0(grid, k):
+    """Rows of up to 13 blocks a side: the library's ILDU0 factors (Algorithm 7,
+    Section 4.3), its fused apply and its BiCGSTAB solve are the oracle's
+    ILDU0-form results bit for bit (the slots beyond the descriptor's three are
+    multiply-added in ascending column order, as the oracle's row sweep does)."""
+    s = synth.unstructured(*grid, 23)
+    part, nparts = g.partition_bfs(s.row_ptr, s.col, k)
+    d = oracle.decompose_labeled(s.row_ptr, s.col, s.val, part, nparts)
+    M = d.ildu()
+    ctx = g.Ilu0DD(s.row_ptr, s.col, s.val, part_id=part, nparts=nparts, keep_host=1)
+    try:
+        kept = d.Add.nnzb
+        rows = np.repeat(np.arange(s.n), np.diff(d.Add.row_ptr))
+        lower, upper = d.Add.col < rows, d.Add.col > rows
+        assert np.array_equal(ctx.export(B.X_L).reshape(kept, 3, 3)[lower], M.F.val[lower])
+        assert np.array_equal(ctx.export(B.X_UT).reshape(kept, 3, 3)[upper], M.F.val[upper])
+        assert np.array_equal(ctx.export(B.X_INVD).reshape(-1, 3, 3), M.inv_d)
+        r = np.random.default_rng(4).uniform(-1, 1, 3 * s.n)
+        assert np.array_equal(ctx.apply(torch.from_numpy(r).cuda()).cpu().numpy(), oracle.apply_ildu0(M, r))
+        x, info = ctx.solve(torch.from_numpy(s.b).cuda())
+        ref = oracle.bicgstab(d.Ap, M, s.b.reshape(-1, 3)[d.perm].reshape(-1))
+        assert info["status"] == ref.status == 0
+        assert info["iterations"] == ref.iterations and info["restarts"] == ref.restarts
+        assert np.array_equal(ctx.history(info["iterations"] + 1), ref.history)
+        assert np.array_equal(x.cpu().numpy(), ref.x.reshape(-1, 3)[d.iperm].reshape(-1))
+    finally:
+        ctx.close()
+
+
+def test_row_thread_mapping_only_for_narrow_rows():
+    """FP32/BF16 factors take one thread per row only when no row has more than
+    three blocks on either side (7-point patterns); the 27-point pattern takes
+    the three-thread mapping, as FP64 factors always do."""
+    s = synth.unstructured(10, 9, 8, 23)
+    part, nparts = g.partition_bfs(s.row_ptr, s.col, 64)
+    seven = synth.system(12, 12, 12, 1)
+    for prec in ("f32", "bf16"):
+        wide = g.Ilu0DD(s.row_ptr, s.col, s.val, part_id=part, nparts=nparts, factor_prec=prec)
+        narrow = g.Ilu0DD(seven.row_ptr, seven.col, seven.val, (12, 12, 12), (4, 4, 4), factor_prec=prec)
+        try:
+            assert wide.query("row_thread") == 0 and narrow.query("row_thread") == 1
+        finally:
+            wide.close()
+            narrow.close()
+    f64 = g.Ilu0DD(s.row_ptr, s.col, s.val, part_id=part, nparts=nparts)
+    try:
+        assert f64.query("row_thread") == 0
+    finally:
+        f64.close()
+
+
 @pytest.mark.parametrize("prec,tol", [("df64", 1e-12), ("f32", 1e-5), ("bf16", 5e-2)])
 def test_partitioned_precisions(prec, tol):
     s = synth.unstructured(16, 12, 10, 29)
