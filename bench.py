@@ -766,9 +766,10 @@ def run_unstructured(dev, cells=(128, 128, 128), part_rows=2048, reps=20):
     """Matrices without a grid (Section 3.1's graph-partition path): the seeded
     unstructured system (irregular 27-point block pattern, cells renumbered at
     random) split by the breadth-first partition into parts of part_rows rows;
-    FP64 and DF64 apply GB/s, dropped blocks, BiCGSTAB iterations and time to
-    1e-8. For contrast, the same system cut into contiguous chunks of its
-    (scrambled) row order."""
+    apply GB/s in every factor precision (FP32/BF16 in the three-thread
+    mapping: rows of up to 13 blocks a side), dropped blocks, BiCGSTAB
+    iterations and time to 1e-8. For contrast, the same system cut into
+    contiguous chunks of its (scrambled) row order."""
     import torch
 
     import paper_2508_04917_gb300 as pkg
@@ -782,7 +783,7 @@ def run_unstructured(dev, cells=(128, 128, 128), part_rows=2048, reps=20):
     z = torch.empty_like(r)
     out = {"cells": s.n, "blocks": s.nnzb, "part_rows": part_rows, "parts": nparts, "partition_s": round(part_s, 3)}
     for name, labels in (("bfs", part), ("chunks", (np.arange(s.n) // part_rows).astype(np.int32))):
-        for prec in (("f64", "df64") if name == "bfs" else ("f64",)):
+        for prec in (("f64", "df64", "f32", "bf16") if name == "bfs" else ("f64",)):
             t0 = time.perf_counter()
             ctx = pkg.Ilu0DD(s.row_ptr, s.col, s.val, part_id=labels, nparts=nparts, factor_prec=prec)
             torch.cuda.synchronize()
@@ -795,6 +796,7 @@ def run_unstructured(dev, cells=(128, 128, 128), part_rows=2048, reps=20):
                 "setup_s": round(su, 3),
                 "dropped_blocks_pct": round(100.0 * (1 - ctx.query("kept") / ctx.query("nnzb")), 2),
                 "max_levels": ctx.query("max_levels"), "pieces": ctx.query("pieces"),
+                "row_thread": ctx.query("row_thread"), "threads": ctx.query("threads"),
                 "apply_ms": round(ams, 5), "apply_rowsync_ms": round(rms, 5), "apply_bytes": ctx.query("apply_bytes"),
                 "apply_gbs": round(ctx.query("apply_bytes") / ams / 1e6, 1), "iterations": info["iterations"],
                 "solve_s": round(sec, 5), "status": info["status"],
