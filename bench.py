@@ -477,7 +477,21 @@ def run_batched(args, dev):
     bt_best, bt_trials = tune_batch_threads(systems, boxes, factor_prec="f32")
     tune_s = time.perf_counter() - t0
     classes2, choice2 = autotune_batch(systems, factor_prec="f32")
-    bt_best2, _ = tune_batch_threads(systems, [c[0] for c in choice2], factor_prec="f32")
+    bt_best2, bt_trials2 = tune_batch_threads(systems, [c[0] for c in choice2], factor_prec="f32")
+
+    def equivalent(trials_a, trials_b, best_a, best_b, key, tie=0.05):
+        # each run's choice is, in the other's choice's run, within the tie rule of it
+        ta = {key(t): t["seconds"] for t in trials_a}
+        tb = {key(t): t["seconds"] for t in trials_b}
+        ka, kb = key(best_a), key(best_b)
+        return (ka == kb or (kb in ta and ta[kb] <= (1 + tie) * ta[ka] and ka in tb and tb[ka] <= (1 + tie) * tb[kb]))
+
+    def box_key(t):
+        return (tuple(t["sub"]), t["threads_per_cta"])
+
+    classes_equivalent = [equivalent(c1["trials"], c2["trials"], c1["best"], c2["best"], box_key)
+                          for c1, c2 in zip(classes, classes2)]
+    threads_equivalent = equivalent(bt_trials, bt_trials2, bt_best, bt_best2, lambda t: t["threads_per_cta"])
     thr = bt_best["threads_per_cta"]
     t0 = time.perf_counter()
     ctxs = [pkg.Ilu0DD(s.row_ptr, s.col, s.val, (s.nx, s.ny, s.nz), boxes[i], factor_prec="f32",
@@ -520,6 +534,10 @@ def run_batched(args, dev):
            "second_tuning": {"subs": [list(c["best"]["sub"]) for c in classes2],
                              "batch_threads_per_cta": bt_best2["threads_per_cta"]},
            "tuning_stable": [c[0] for c in choice] == [c[0] for c in choice2] and thr == bt_best2["threads_per_cta"],
+           # where the two runs chose differently: whether each choice is within the tie rule of
+           # the other in both runs' own measurements (near-equal candidates)
+           "tuning_choices_equivalent": all(classes_equivalent) and threads_equivalent,
+           "tuning_classes_equivalent": classes_equivalent,
            "setup_s": round(setup_s, 2), "batched_s": round(batched_s, 5),
            "systems_per_s": round(n / batched_s, 2), "sequential_s": round(seq_s, 5),
            "sequential_systems_per_s": round(n / seq_s, 2), "all_converged": ok,

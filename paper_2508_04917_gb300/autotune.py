@@ -9,9 +9,13 @@ measures time to solution through the library:
 * candidates are (subdomain box, threads per block) pairs; those whose plan
   does not fit (shared memory, block size) are dropped by the library's
   host-side structural plan (``workspace_size``) before any device work;
-* each remaining candidate gets a context, one warm-up solve (CUDA-graph
-  capture) and ``repeats`` (5) timed solves; its time is the median, with the
-  minimum and maximum kept as its spread;
+* each remaining candidate gets a context and one warm-up solve (CUDA-graph
+  capture); then ``repeats`` (5) rounds each time one solve of every
+  candidate, the order rotated by one from round to round, so that drift over
+  the tuning run (clocks, other work on the machine) falls on all candidates
+  alike; a candidate's time is its median, with the minimum and maximum kept
+  as its spread (all candidate contexts are alive at once: their device
+  memory adds up);
 * the choice is the first candidate (in candidate order) whose median lies
   within ``tie`` (5 %) of the fastest one, so that near-equal candidates do
   not swap places from run to run on timer noise (solves of the smallest
@@ -63,37 +67,44 @@ def autotune(system, subs=DEFAULT_SUBS, threads=DEFAULT_THREADS, factor_prec="f3
              **opts):
     """Return (best, trials) for a synth.System-like object (row_ptr, col, val,
     nx, ny, nz, b). Each trial: sub, threads_per_cta (as resolved by the
-    library), seconds (median of `repeats` timed solves), seconds_min,
-    seconds_max, iterations. best = pick(trials, tie)."""
+    library), seconds (median of `repeats` timed solves, one per round over
+    all candidates), seconds_min, seconds_max, iterations. best = pick(trials,
+    tie)."""
     import torch
 
     grid = (system.nx, system.ny, system.nz)
     b = torch.from_numpy(system.b).cuda()
-    trials, seen = [], set()
-    for sub, thr in candidates(system, subs, threads, factor_prec, **opts):
-        try:
-            ctx = Ilu0DD(system.row_ptr, system.col, system.val, grid, sub, factor_prec=factor_prec,
-                         threads_per_cta=thr, **opts)
-        except Ilu0DDError:
-            continue
-        try:
+    live, seen = [], set()
+    try:
+        for sub, thr in candidates(system, subs, threads, factor_prec, **opts):
+            try:
+                ctx = Ilu0DD(system.row_ptr, system.col, system.val, grid, sub, factor_prec=factor_prec,
+                             threads_per_cta=thr, **opts)
+            except Ilu0DDError:
+                continue
             key = (sub, ctx.query("threads"))
             if key in seen:  # threads_per_cta = 0 resolved to a block size already timed
+                ctx.close()
                 continue
             seen.add(key)
+            live.append((key, ctx))
             ctx.solve(b)  # warm-up: graph capture
-            torch.cuda.synchronize()
-            times, info = [], None
-            for _ in range(repeats):
+        torch.cuda.synchronize()
+        times = {key: [] for key, _ in live}
+        infos = {}
+        for rnd in range(repeats):
+            k = rnd % max(1, len(live))
+            for key, ctx in live[k:] + live[:k]:
                 t0 = time.perf_counter()
-                _, info = ctx.solve(b, check=False)
+                _, infos[key] = ctx.solve(b, check=False)
                 torch.cuda.synchronize()
-                times.append(time.perf_counter() - t0)
-            if info["status"] == 0:
-                trials.append(dict(sub=sub, threads_per_cta=key[1], seconds=float(np.median(times)),
-                                   seconds_min=min(times), seconds_max=max(times),
-                                   iterations=info["iterations"]))
-        finally:
+                times[key].append(time.perf_counter() - t0)
+        trials = [dict(sub=key[0], threads_per_cta=key[1], seconds=float(np.median(times[key])),
+                       seconds_min=min(times[key]), seconds_max=max(times[key]),
+                       iterations=infos[key]["iterations"])
+                  for key, _ in live if infos[key]["status"] == 0]
+    finally:
+        for _, ctx in live:
             ctx.close()
     if not trials:
         raise RuntimeError("no autotuning candidate solved the system")

@@ -69,3 +69,10 @@ def test_autotune_size_classes_and_pruning():
     cand = candidates(s, subs=((8, 8, 8), (40, 40, 40)), threads=(0, 128), factor_prec="f64")
     # a 40^3 box (64,000 rows) does not fit one block's shared memory
     assert cand == [((8, 8, 8), 0), ((8, 8, 8), 128)]
+
+
+def test_autotune_pick_prefers_the_first_near_tie():
+    from paper_2508_04917_gb300.autotune import pick
+    trials = [dict(seconds=1.04), dict(seconds=1.00), dict(seconds=1.2)]
+    assert pick(trials, tie=0.05) is trials[0]
+    assert pick(trials, tie=0.01) is trials[1]
