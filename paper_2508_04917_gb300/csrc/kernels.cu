@@ -75,9 +75,12 @@ __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 // the double-float arithmetic is the bound; FP32 and BF16 factors one thread
 // per row computing all three components (32 rows per warp, the row-thread
 // layout: apply_block_rt), which issues a third of the instructions of the
-// three-thread mapping; scalar rows take one thread each (apply_block with
-// BS = 1). Both compute each output component with the same operations in
-// the same order, so the mappings give the same bits.
+// three-thread mapping, when no row has more than kDescSlots blocks on either
+// side (else they too take three threads per row, whose general-pattern path
+// loads wider rows' slots in groups); scalar rows take one thread each
+// (apply_block with BS = 1). On rows of up to kDescSlots blocks a side both
+// 3x3 mappings compute each output component with the same operations in the
+// same order, so they give the same bits.
 // In the DF64 mode the vector is held as float pairs, scaled by a power of two
 // per block (exact, and the apply is linear and local to the block) so that
 // the FP32 exponent range never limits it.

@@ -76,3 +76,13 @@ def test_autotune_pick_prefers_the_first_near_tie():
     trials = [dict(seconds=1.04), dict(seconds=1.00), dict(seconds=1.2)]
     assert pick(trials, tie=0.05) is trials[0]
     assert pick(trials, tie=0.01) is trials[1]
+
+
+def test_source_hash_ignores_comments_only():
+    import bench
+    a = 'int f(int x) { // one\n  return x + 1; /* two */ }\nconst char* s = "a // b /* c */";\n'
+    b = '/* header */\nint f(int x) {\n  return x + 1;   // other words\n}\nconst char* s = "a // b /* c */";'
+    c = 'int f(int x) { return x + 2; }\nconst char* s = "a // b /* c */";'
+    assert bench.strip_comments(a) == bench.strip_comments(b)
+    assert bench.strip_comments(a) != bench.strip_comments(c)
+    assert '"a // b /* c */"' in bench.strip_comments(a)
