@@ -76,7 +76,7 @@ def test_subdomain_shared_memory_limit():
     """Section 4 sizes subdomains so their vector fits in shared memory. On sm_103a
     (227 KiB per block) an FP64 subdomain of 9472 block rows (16x16x37 cells,
     222 KiB) fits; one more z-layer does not. FP32-factor contexts keep an FP32
-    vector, so twice the rows fit."""
+    vector (16 bytes a row in the row-thread layout), so more rows fit."""
     grid = (16, 16, 38)
     rp, col = synth.pattern(*grid)
     val = np.zeros((len(col), 3, 3))

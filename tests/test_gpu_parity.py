@@ -331,6 +331,29 @@ def test_largest_subdomain_fits_shared_memory():
     assert ctx.query("smem") <= 232448
 
 
+@pytest.mark.parametrize("prec,z,tol", [("f64", 37, 0.0), ("df64", 37, 1e-12), ("f32", 55, 1e-5), ("bf16", 55, 5e-2)])
+def test_maximum_subdomain_per_precision(prec, z, tol):
+    """The largest box subdomain whose vector fits the 227 KiB of shared memory
+    per block: 16x16x37 cells (9,472 block rows, 24 bytes a row) with FP64 or
+    float-pair factors, 16x16x55 (14,080 rows, 16 bytes a row in the row-thread
+    layout) with FP32 or BF16 factors; one z-layer more is refused (CPU test).
+    The apply against the oracle's ILDU0 form (FP64: bit for bit) and a solve to
+    1e-8."""
+    grid = sub = (16, 16, z)
+    s, d, ctx = case(grid, sub, seed=12, model=synth.MODEL_LAYERED, factor_prec=prec)
+    assert ctx.query("n") == 256 * z and ctx.query("nsub") == 1
+    r = np.random.default_rng(13).uniform(-1, 1, 3 * s.n)
+    z_gpu = host(ctx.apply(cu(r)))
+    ref = oracle.apply_ildu0(d.ildu(), r)
+    if tol == 0.0:
+        assert np.array_equal(z_gpu, ref)
+    else:
+        assert nrel(z_gpu, ref) <= tol
+    _, info = ctx.solve(cu(s.b))
+    assert info["status"] == 0 and info["rel_res_true"] < 1e-8
+    assert ctx.query("smem") <= 232448
+
+
 def test_zero_pivot_reported():
     """A zero diagonal block on the first row of a subdomain is a zero pivot of ILU0."""
     s = synth.system(4, 4, 4, 1)
