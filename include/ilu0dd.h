@@ -72,6 +72,10 @@ extern "C" {
  * (strictly ascending per row, diagonal block present), val[bs*bs*nnzb]
  * (row-major bs x bs blocks). block_dim = bs: 3 (also 0) for 3x3 blocks, 1
  * for a scalar CSR matrix; vectors then hold bs*n_brows doubles.
+ * n_brows = 0 (an empty system) is accepted on the partitioned path
+ * (ilu0dd_plan_create_partitioned, any nparts >= 0; the grid path needs
+ * positive sides): nothing is launched, vector pointers may be null, a solve
+ * returns ILU0DD_OK after no iteration, alone or in a batch.
  * Each array may be in host memory or in device memory of the current device
  * (the library tells them apart with cudaPointerGetAttributes). The
  * structural setup runs on the host, so device-resident row_ptr and col_idx

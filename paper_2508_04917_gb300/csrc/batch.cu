@@ -217,7 +217,7 @@ int bicgstab_solve_batched(ilu0dd_batch* b, const double* const* d_b, double* co
                            void* stream) {
   if (!b || !d_b || !d_x) return ILU0DD_ERR_INVALID;
   for (int32_t i = 0; i < b->nsys; ++i)
-    if (!d_b[i] || !d_x[i]) return ILU0DD_ERR_INVALID;
+    if (b->ctxs[i]->plan.N > 0 && (!d_b[i] || !d_x[i])) return ILU0DD_ERR_INVALID;
   const double t0 = wall_seconds();
   const int32_t n = b->nsys;
   std::vector<const double*> ptrs(2 * (size_t)n);
@@ -228,6 +228,15 @@ int bicgstab_solve_batched(ilu0dd_batch* b, const double* const* d_b, double* co
   std::vector<int32_t> restarts(n, 0), flags(n, 0);
   auto fail = [&](cudaError_t) { return ILU0DD_ERR_CUDA; };
   cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+  // A system with no rows has no work items, so no kernel ever sets its
+  // scalars: it is finished from the start (x empty, residual 0), as
+  // bicgstab_solve reports it.
+  SolverScalars empty{};
+  empty.done = 1;
+  empty.converged = 1;
+  for (int32_t i = 0; i < n && e == cudaSuccess; ++i)
+    if (b->ctxs[i]->plan.N == 0)
+      e = cudaMemcpyAsync(b->ctxs[i]->dev.sd.scal, &empty, sizeof empty, cudaMemcpyHostToDevice, b->own);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->d_ptrs, ptrs.data(), sizeof(double*) * ptrs.size(), cudaMemcpyHostToDevice, b->own);
   if (e == cudaSuccess) e = launch_permute_batched(b->d_sys, b->d_tile_items, b->n_tile, b->d_ptrs, 0, b->bs, b->grid_tile,

@@ -547,7 +547,7 @@ int ilu0_dd_apply_unfused(const ilu0dd_ctx* ctx, const double* d_r, double* d_z,
 }
 
 int ilu0_dd_spmv(const ilu0dd_ctx* ctx, const double* d_x, double* d_y, void* stream) {
-  if (!ctx || (ctx->plan.N > 0 && (!d_x || !d_y)) || d_x == d_y) return ILU0DD_ERR_INVALID;
+  if (!ctx || (ctx->plan.N > 0 && (!d_x || !d_y || d_x == d_y))) return ILU0DD_ERR_INVALID;
   cudaError_t e = launch_spmv(ctx->dev, 0, d_x, d_y, reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(const_cast<ilu0dd_ctx*>(ctx), e, "spmv launch");
   return ILU0DD_OK;
@@ -561,7 +561,7 @@ int ilu0_dd_dot(const ilu0dd_ctx* ctx, const double* d_x, const double* d_y, dou
 }
 
 int ilu0_dd_permute(const ilu0dd_ctx* ctx, const double* d_in, double* d_out, int dir, void* stream) {
-  if (!ctx || (dir != 0 && dir != 1) || (ctx->plan.N > 0 && (!d_in || !d_out)) || d_in == d_out)
+  if (!ctx || (dir != 0 && dir != 1) || (ctx->plan.N > 0 && (!d_in || !d_out || d_in == d_out)))
     return ILU0DD_ERR_INVALID;
   cudaError_t e = launch_permute(ctx->dev, d_in, d_out, dir, reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(const_cast<ilu0dd_ctx*>(ctx), e, "permute launch");
