@@ -382,6 +382,12 @@ def run_ours(args):
             ems = time_apply_warm(c, r, zp, 20, c.apply_edge) if prec != "df64" else None
             # shared-memory ablation: the subdomain vector in global memory (FP64 only)
             gms = time_apply_warm(c, r, zp, 20, c.apply_global_vector) if prec == "f64" else None
+            # mapping ablation (FP32 / BF16): three threads per row instead of the row-thread layout
+            tms = None
+            if c.query("row_thread") == 1:
+                c3 = pkg.Ilu0DD(s.row_ptr, s.col, s.val, grid, sub, factor_prec=prec, apply_mapping=1)
+                tms = time_apply_warm(c3, r, zp, 20)
+                c3.close()
             err_orc = None
             if z_orc is not None:
                 c.apply(r, zp)
@@ -394,6 +400,7 @@ def run_ours(args):
                             "fusion_speedup": round(ums / ams, 3), "apply_rowsync_ms": round(rms, 5),
                             "apply_edge_ms": None if ems is None else round(ems, 5),
                             "apply_vector_in_global_ms": None if gms is None else round(gms, 5),
+                            "apply_three_thread_ms": None if tms is None else round(tms, 5),
                             "apply_bytes": c.query("apply_bytes"),
                             "apply_gbs": round(c.query("apply_bytes") / ams / 1e6, 1)}
             c.close()

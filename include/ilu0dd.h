@@ -122,6 +122,12 @@ typedef struct {
                                MI210; its rounding order, hence the iteration count, may vary).
                                1 is not available with ILU0DD_DF64 (ILU0DD_ERR_INVALID); batched
                                solves always use 0. */
+  int32_t apply_mapping;    /* threads per 3x3 block row in the apply: 0 = automatic (default: one
+                               thread per row, the row-thread layout, for FP32 / BF16 factors when
+                               no row has more than three blocks on either side; else three);
+                               1 = three threads per row always (the row-thread layout's ablation:
+                               the same bits where both apply). Any other value: ILU0DD_ERR_INVALID.
+                               ILU0DD_Q_ROW_THREAD reports the mapping taken. */
 } ilu0dd_opts;
 
 typedef struct {

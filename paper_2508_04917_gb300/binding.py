@@ -51,7 +51,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("factor_prec", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
                 ("prefetch_bytes", ctypes.c_int32), ("maxit", ctypes.c_int32), ("rtol", ctypes.c_double),
                 ("check_every", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
-                ("keep_host", ctypes.c_int32), ("trace", ctypes.c_int32), ("traversal", ctypes.c_int32)]
+                ("keep_host", ctypes.c_int32), ("trace", ctypes.c_int32), ("traversal", ctypes.c_int32),
+                ("apply_mapping", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -150,7 +151,10 @@ def strerror(code: int) -> str:
 def default_opts(**kw) -> Opts:
     o = Opts()
     load().ilu0dd_default_opts(ctypes.byref(o))
+    names = {f[0] for f in Opts._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown option {k!r}")
         if k == "factor_prec" and isinstance(v, str):
             v = PRECISIONS[v]
         setattr(o, k, v)

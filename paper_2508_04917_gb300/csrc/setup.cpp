@@ -395,7 +395,11 @@ int make_plan(const ilu0dd_bsr* A, const ilu0dd_geom* g, const ilu0dd_opts* o, i
   // further slots in groups: measured on GB300, unstructured 128^3 apply
   // with one thread per row / three: FP32 0.574 / 0.336 ms, BF16 0.407 /
   // 0.336); scalar rows one thread per row
-  p.row_thread = bs == 3 && (fp == ILU0DD_F32 || fp == ILU0DD_BF16) && side_max <= kDescSlots;
+  if (o->apply_mapping != 0 && o->apply_mapping != 1) {
+    *why = "apply_mapping must be 0 (automatic) or 1 (three threads per 3x3 row)";
+    return ILU0DD_ERR_INVALID;
+  }
+  p.row_thread = bs == 3 && (fp == ILU0DD_F32 || fp == ILU0DD_BF16) && side_max <= kDescSlots && o->apply_mapping == 0;
   p.rows_per_warp = bs == 3 && !p.row_thread ? kRowsPerWarp : 32;
   p.factor_elem = (fp == ILU0DD_F64 || fp == ILU0DD_DF64) ? 8 : fp == ILU0DD_F32 ? 4 : 2;
   p.vec_elem = (fp == ILU0DD_F64 || fp == ILU0DD_DF64) ? 8 : 4;

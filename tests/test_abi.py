@@ -70,6 +70,11 @@ def test_rejects_bad_patterns():
     with pytest.raises(g.Ilu0DDError) as e:
         g.workspace_size(s.row_ptr, s.col, s.val, (8, 8, 8), (4, 4, 4), threads_per_cta=48)
     assert e.value.code == 1
+    with pytest.raises(g.Ilu0DDError) as e:
+        g.workspace_size(s.row_ptr, s.col, s.val, (8, 8, 8), (4, 4, 4), apply_mapping=2)
+    assert e.value.code == 1
+    with pytest.raises(TypeError):
+        g.workspace_size(s.row_ptr, s.col, s.val, (8, 8, 8), (4, 4, 4), no_such_option=1)
 
 
 def test_subdomain_shared_memory_limit():

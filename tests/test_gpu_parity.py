@@ -354,6 +354,30 @@ def test_maximum_subdomain_per_precision(prec, z, tol):
     assert ctx.query("smem") <= 232448
 
 
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+def test_row_thread_and_three_thread_mappings_same_bits(prec):
+    """FP32 / BF16 factors on 7-point rows: the row-thread apply (one thread per
+    row, the default here) and the three-thread apply (apply_mapping = 1) form
+    each output component with the same operations in the same order, so the
+    fused, unfused and row-flag applies and whole solves agree bit for bit."""
+    grid, sub = (33, 17, 9), (16, 16, 8)
+    s = synth.system(*grid, 3, model=synth.MODEL_LAYERED)
+    rt = g.Ilu0DD(s.row_ptr, s.col, s.val, grid, sub, factor_prec=prec)
+    tt = g.Ilu0DD(s.row_ptr, s.col, s.val, grid, sub, factor_prec=prec, apply_mapping=1)
+    try:
+        assert rt.query("row_thread") == 1 and tt.query("row_thread") == 0
+        r = cu(np.random.default_rng(14).uniform(-1, 1, 3 * s.n))
+        for name in ("apply", "apply_unfused", "apply_rowsync"):
+            assert torch.equal(getattr(rt, name)(r), getattr(tt, name)(r)), name
+        xa, ia = rt.solve(cu(s.b))
+        xb, ib = tt.solve(cu(s.b))
+        assert ia["status"] == ib["status"] == 0 and ia["iterations"] == ib["iterations"]
+        assert torch.equal(xa, xb)
+    finally:
+        rt.close()
+        tt.close()
+
+
 def test_zero_pivot_reported():
     """A zero diagonal block on the first row of a subdomain is a zero pivot of ILU0."""
     s = synth.system(4, 4, 4, 1)
