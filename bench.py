@@ -670,9 +670,9 @@ def run_edge_solve(dev, s160, repeats=10):
 def run_table4_shapes(dev, reps=20):
     """The grid shapes of the paper's Table 4 (laplacian1: 128^3 cells,
     laplacian2: 128x128x256, 3x3 blocks, 2,048-row subdomains = 16x16x8
-    boxes) with this build's seeded laplace values (the paper's are not
+    boxes) with the generator's seeded laplace values (the paper's are not
     published): the dropped share (Table 5: 6.52 % / 6.62 %), and the FP64
-    apply in each of the paper's kernel forms that this build has (fused
+    apply in each of the paper's kernel forms that the library has (fused
     row-wise, unfused, edge-centric), milliseconds. The paper's MI210 times
     for the same shapes are context, not targets."""
     import torch
